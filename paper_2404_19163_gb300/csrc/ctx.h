@@ -1,0 +1,44 @@
+// The library context (opaque to callers through zfact.h) and the internal
+// host helpers shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+
+#include "common.cuh"
+
+struct DevBuf {
+  void* ptr;
+  size_t bytes;
+};
+
+struct zfact_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int cc_major = 0, cc_minor = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::map<std::string, DevBuf> bufs;  // named device workspace, grown on demand
+  zf::IterState* st_dev = nullptr;     // device iteration state
+  zf::IterState* st_host = nullptr;    // pinned host mirror
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double* mixed_result = nullptr;      // device FP64 Z produced by the mixed driver
+  char err[512];
+};
+
+int ctx_fail(zfact_ctx* c, int code, const char* fmt, ...);
+int ctx_cuda(zfact_ctx* c, cudaError_t e, const char* what);
+void* ctx_buf(zfact_ctx* c, const char* name, size_t bytes, int* status);
+bool is_device_ptr(const void* p);
+int ctx_read_state(zfact_ctx* c);
+
+// FP64 building blocks (capi.cu)
+int f64_residual(zfact_ctx* c, const double* S, const double* Z, double* A, double* D, int n, int idx, int rule,
+                 double tol, int check_stop);
+int f64_poly(zfact_ctx* c, const double* D, double* Q, double* P, double* P2, int n, int m);
+int f64_update(zfact_ctx* c, const double* Z, const double* Q, double* Zn, int n);
+
+// Mixed-precision driver (mixed.cu): bulk tensor-core iterations, then Algorithm 3's refinement.
+int mixed_refine(zfact_ctx* c, const double* S, double* Za, double* Zb, int n, int order, int precision,
+                 const zfact_opts& o, int* iters, int* ridx, zfact_info* inf);

@@ -1,0 +1,238 @@
+// Element-wise steps and reductions of the recursion: the Gershgorin start
+// Z0 = I / sqrt(max_i sum_j |S_ij|) (Sec. 3: ||X0 - I||_2 < 1), the
+// deterministic Frobenius-norm finish Err = ||I - X||_F, and the stop test of
+// Algorithm 2 (Sec. 4.1, Eq. stopL2) evaluated on the device in FP64.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace zf {
+namespace {
+
+__global__ void k_rowabs_max(const double* __restrict__ S, int n, IterState* st) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = S + (size_t)warp * n;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += fabs(row[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  // non-negative doubles order like their bit patterns
+  if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(&st->amax[0]), __double_as_longlong(s));
+}
+
+__global__ void k_gscale(IterState* st) { st->gscale = 1.0 / sqrt(st->amax[0]); }
+
+__global__ void k_scaled_identity_f64(double* Z, int n, const IterState* st) {
+  const size_t total = (size_t)n * n;
+  const double s = st->gscale;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / n, j = e % n;
+    Z[e] = (i == j) ? s : 0.0;
+  }
+}
+
+__global__ void k_finish_err(const double* __restrict__ partials, int np, IterState* st, int idx, int rule,
+                             double tol, int n, int check_stop) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) s += partials[p];  // fixed order per thread
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double err = sqrt(red[0]);
+    if (idx < kHistMax) st->hist[idx] = err;
+    st->hist_len = idx + 1;
+    if (!isfinite(err)) {
+      st->nonfinite = 1;
+      st->stop = 1;
+    } else if (check_stop) {
+      const double prev = st->prev_err;
+      if (rule == 1) {
+        if (err / sqrt((double)n) <= tol) st->stop = 1;
+      } else if (err > prev * prev * prev || err >= prev) {
+        st->stop = 1;
+      }
+    }
+    st->prev_err = err;
+  }
+}
+
+__device__ __forceinline__ uint16_t r16(float x, bool bf16) {
+  return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(x)) : __half_as_ushort(__float2half_rn(x));
+}
+__device__ __forceinline__ float f16v(uint16_t h, bool bf16) {
+  return bf16 ? __bfloat162float(__ushort_as_bfloat16(h)) : __half2float(__ushort_as_half(h));
+}
+
+// 32 x 32 tiles through shared memory so that both the read and the (possibly transposed)
+// write are coalesced.
+template <typename T>
+__global__ void k_cvt16(const T* __restrict__ src, int n, int ld_src, uint16_t* __restrict__ hi,
+                        uint16_t* __restrict__ lo, int ld16, double scale, const float* scale_ptr, int transpose,
+                        int bf16) {
+  __shared__ uint16_t th[32][33], tl[32][33];
+  const double sc = scale_ptr ? (double)*scale_ptr : scale;
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = bi + r, j = bj + threadIdx.x;
+    uint16_t h = 0, l = 0;
+    if (i < n && j < n) {
+      const float x = (float)((double)src[(size_t)i * ld_src + j] * sc);
+      h = r16(x, bf16);
+      l = r16(x - f16v(h, bf16), bf16);
+    }
+    th[r][threadIdx.x] = h;
+    tl[r][threadIdx.x] = l;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int oi, oj;
+    uint16_t h, l;
+    if (transpose) {
+      oi = bj + r;
+      oj = bi + threadIdx.x;
+      h = th[threadIdx.x][r];
+      l = tl[threadIdx.x][r];
+    } else {
+      oi = bi + r;
+      oj = bj + threadIdx.x;
+      h = th[r][threadIdx.x];
+      l = tl[r][threadIdx.x];
+    }
+    if (oi < n && oj < n) {
+      hi[(size_t)oi * ld16 + oj] = h;
+      if (lo) lo[(size_t)oi * ld16 + oj] = l;
+    }
+  }
+}
+
+__global__ void k_split_flat(const double* __restrict__ A, int64_t n, double scale, uint16_t* hi, uint16_t* lo,
+                             int bf16) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const float x = (float)(A[e] * scale);
+    const uint16_t h = r16(x, bf16);
+    hi[e] = h;
+    lo[e] = r16(x - f16v(h, bf16), bf16);
+  }
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ src, int n, int ld64, float* dst, int ld32) {
+  const size_t total = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / n, j = e % n;
+    dst[i * ld32 + j] = (float)src[i * ld64 + j];
+  }
+}
+
+__global__ void k_f32_to_f64(const float* __restrict__ src, int n, int ld32, double* dst, int ld64) {
+  const size_t total = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / n, j = e % n;
+    dst[i * ld64 + j] = (double)src[i * ld32 + j];
+  }
+}
+
+__global__ void k_amax_f64(const double* __restrict__ A, size_t total, IterState* st, int slot) {
+  double m = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(A[e]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&st->amax[slot]), (unsigned long long)__double_as_longlong(m));
+}
+
+__device__ float pow2_for(double bound) {
+  // largest power of two s with bound * s <= 2^14 (FP16 max is 65504 ~ 2^16: two bits of headroom)
+  if (!(bound > 0.0) || !isfinite(bound)) return 1.0f;
+  int e;
+  frexp(bound, &e);  // bound in [2^(e-1), 2^e)
+  int p = 14 - e;
+  if (p > 60) p = 60;
+  if (p < -60) p = -60;
+  return ldexpf(1.0f, p);
+}
+
+__global__ void k_pow2_scales(IterState* st, int idx, float c1, float c2) {
+  const double ad = st->amax[1];
+  const double err = (idx >= 0 && idx < kHistMax) ? st->hist[idx] : ad;
+  st->scale[0] = pow2_for(ad);
+  st->scale[1] = pow2_for((double)c1 * ad + (double)c2 * err * err);
+  st->scale[2] = pow2_for(st->amax[2]);
+}
+
+}  // namespace
+
+cudaError_t launch_cvt16(const double* src, int n, int ld_src, uint16_t* hi, uint16_t* lo, int ld16, double scale,
+                         const float* scale_ptr, bool transpose, bool bf16, cudaStream_t s) {
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  k_cvt16<double><<<grid, block, 0, s>>>(src, n, ld_src, hi, lo, ld16, scale, scale_ptr, transpose, bf16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cvt16_f32(const float* src, int n, int ld_src, uint16_t* hi, uint16_t* lo, int ld16,
+                             bool transpose, bool bf16, cudaStream_t s) {
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  k_cvt16<float><<<grid, block, 0, s>>>(src, n, ld_src, hi, lo, ld16, 1.0, nullptr, transpose, bf16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_flat(const double* A, int64_t n, double scale, uint16_t* hi, uint16_t* lo, bool bf16,
+                              cudaStream_t s) {
+  const int blocks = (int)((n + 255) / 256 < 8192 ? (n + 255) / 256 : 8192);
+  k_split_flat<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(A, n, scale, hi, lo, bf16);
+  return cudaGetLastError();
+}
+
+static int grid_for(size_t total) { return (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192); }
+
+cudaError_t launch_f64_to_f32(const double* src, int n, int ld64, float* dst, int ld32, cudaStream_t s) {
+  k_f64_to_f32<<<grid_for((size_t)n * n), 256, 0, s>>>(src, n, ld64, dst, ld32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float* src, int n, int ld32, double* dst, int ld64, cudaStream_t s) {
+  k_f32_to_f64<<<grid_for((size_t)n * n), 256, 0, s>>>(src, n, ld32, dst, ld64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amax_f64(const double* A, int n, IterState* st, int slot, cudaStream_t s) {
+  cudaMemsetAsync(&st->amax[slot], 0, sizeof(double), s);
+  const size_t total = (size_t)n * n;
+  k_amax_f64<<<grid_for(total) < 1024 ? grid_for(total) : 1024, 256, 0, s>>>(A, total, st, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pow2_scales(IterState* st, int idx, float c1, float c2, cudaStream_t s) {
+  k_pow2_scales<<<1, 1, 0, s>>>(st, idx, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gershgorin(const double* S, int n, IterState* st, cudaStream_t s) {
+  cudaMemsetAsync(&st->amax[0], 0, sizeof(double), s);
+  const int warps_per_block = 8;
+  k_rowabs_max<<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(S, n, st);
+  k_gscale<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scaled_identity_f64(double* Z, int n, const IterState* st, cudaStream_t s) {
+  const size_t total = (size_t)n * n;
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  k_scaled_identity_f64<<<blocks, 256, 0, s>>>(Z, n, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_err(const double* partials, int nparts, IterState* st, int idx, int rule, double tol,
+                              int n, int check_stop, cudaStream_t s) {
+  k_finish_err<<<1, 256, 0, s>>>(partials, nparts, st, idx, rule, tol, n, check_stop);
+  return cudaGetLastError();
+}
+
+}  // namespace zf

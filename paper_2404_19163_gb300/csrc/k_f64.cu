@@ -1,0 +1,138 @@
+// FP64 CUDA-core products of the recursion (the paper's "double", Table I),
+// with the element-wise steps fused into the epilogues:
+//   residual   d = I - Z^T (S Z), symmetric, upper tiles only   (Eq. np1, Algorithm 2's Err)
+//   polynomial Q = c1 d + c2 d^2 (+ c_k d^k chains)               (delta-form of Eq. np1)
+//   update     Z' = Z + Z Q                                       (Z_{n+1} = Z_n p(d_n))
+// GB300's FP64 pipe is ~1.1 TFLOP/s (about 2 DFMA per SM per clock), so these
+// kernels are bound by FP64 issue for every N of interest; a 64x64 tile with a
+// 4x4 register micro-tile keeps the operand traffic far below that bound.
+#include "kernels.h"
+
+namespace zf {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__device__ __forceinline__ void sym_tile_of(int b, int T, int& bi, int& bj) {
+  // b-th tile of the upper triangle, row-major over (bi, bj >= bi)
+  int row = 0, rem = b;
+  while (rem >= T - row) {
+    rem -= T - row;
+    ++row;
+  }
+  bi = row;
+  bj = row + rem;
+}
+
+__global__ void __launch_bounds__(NT) k64_gemm(F64Gemm g) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  __shared__ double red[NT / 32];
+  const int n = g.n;
+  const int T = (n + BM - 1) / BM;
+  int bi, bj;
+  if (g.sym) {
+    sym_tile_of(blockIdx.x, T, bi, bj);
+  } else {
+    bi = blockIdx.y;
+    bj = blockIdx.x;
+  }
+  const int i0 = bi * BM, j0 = bj * BN;
+  const int t = threadIdx.x;
+  const int ty = t / 16, tx = t % 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < n; k0 += BK) {
+#pragma unroll
+    for (int e = 0; e < (BM * BK) / NT; ++e) {
+      const int idx = t + e * NT;
+      int ii, kk;
+      double v = 0.0;
+      if (g.transA) {
+        kk = idx / BM;
+        ii = idx % BM;
+        const int gi = i0 + ii, gk = k0 + kk;
+        if (gi < n && gk < n) v = g.A[(size_t)gk * n + gi];
+      } else {
+        ii = idx / BK;
+        kk = idx % BK;
+        const int gi = i0 + ii, gk = k0 + kk;
+        if (gi < n && gk < n) v = g.A[(size_t)gi * n + gk];
+      }
+      As[kk][ii] = v;
+    }
+#pragma unroll
+    for (int e = 0; e < (BK * BN) / NT; ++e) {
+      const int idx = t + e * NT;
+      const int kk = idx / BN, jj = idx % BN;
+      const int gk = k0 + kk, gj = j0 + jj;
+      Bs[kk][jj] = (gk < n && gj < n) ? g.B[(size_t)gk * n + gj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  double ss = 0.0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty * 4 + r;
+    if (i >= n) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx * 4 + c;
+      if (j >= n) continue;
+      if (g.sym && j < i) continue;  // the (j, i) entry is written by the tile that owns it
+      double v;
+      if (g.resid) {
+        v = (i == j ? 1.0 : 0.0) - acc[r][c];
+        ss += (i == j ? 1.0 : 2.0) * v * v;
+      } else {
+        v = g.beta * acc[r][c];
+        if (g.Add) v = fma(g.alpha, g.Add[(size_t)i * n + j], v);
+        if (g.P) {
+          g.P[(size_t)i * n + j] = acc[r][c];
+          if (g.sym && j != i) g.P[(size_t)j * n + i] = acc[r][c];
+        }
+      }
+      g.C[(size_t)i * n + j] = v;
+      if (g.sym && j != i) g.C[(size_t)j * n + i] = v;
+    }
+  }
+  if (g.resid) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((t & 31) == 0) red[t >> 5] = ss;
+    __syncthreads();
+    if (t == 0) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += red[w];
+      g.partials[blockIdx.x] = s;
+    }
+  }
+}
+
+}  // namespace
+
+int f64_num_blocks(int n, bool sym) {
+  const int T = (n + BM - 1) / BM;
+  return sym ? T * (T + 1) / 2 : T * T;
+}
+
+cudaError_t launch_f64_gemm(const F64Gemm& g, cudaStream_t s) {
+  const int T = (g.n + BM - 1) / BM;
+  dim3 grid = g.sym ? dim3(T * (T + 1) / 2) : dim3(T, T);
+  k64_gemm<<<grid, NT, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+}  // namespace zf

@@ -1,0 +1,466 @@
+// tcgen05 GEMM engine for the recursion's products on GB300 (sm_103a).
+//
+// One persistent CTA per SM walks a list of output tiles (128 x BN).  Warp 0
+// streams K-blocks of the operands into a ring of shared-memory stages with
+// TMA (128-byte swizzle); one thread of warp 1 issues tcgen05.mma (kind::f16,
+// FP32 accumulation in tensor memory) and releases each stage with
+// tcgen05.commit; warps 2-5 read the accumulator back with tcgen05.ld and run
+// the fused epilogue while the next tile accumulates in the other half of the
+// tensor memory (two accumulator buffers).
+//
+// A product may consist of up to four K-concatenated segments accumulated
+// into one accumulator: the split scheme (h)(h)+(h)(l)+(l)(h) of Sec. 3.2
+// (Eqs. SZn, Xn, Xsq) is three segments.  Symmetric products (X = Z^T S Z and
+// the powers of d) form only the tiles that touch the upper triangle and
+// write every entry (i, j), i <= j, to both (i, j) and (j, i).
+//
+// Every wait on an mbarrier is bounded; a wait that gives up raises a flag in
+// the device state and the CTA winds down (no trap).
+#include <stdio.h>
+
+#include "tc_gemm.h"
+
+namespace zf {
+namespace {
+
+constexpr int BM = 128, BK = 64, UK = 16, NTHREADS = 192;
+
+template <int BN>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int STAGES = BN == 256 ? 4 : 6;
+  static constexpr int TMEM_COLS = 2 * BN;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+__host__ __device__ inline int units_of(int M, int N, int sym, int bn_size) {
+  const int tm = (M + BM - 1) / BM, tn = (N + bn_size - 1) / bn_size;
+  if (!sym) return tm * tn;
+  int total = 0;
+  for (int r = 0; r < tm; ++r) total += tn - (r * BM) / bn_size;
+  return total;
+}
+
+__device__ __forceinline__ void decode_unit(int u, const TcArgs& a, int bn_size, int& bm, int& bn) {
+  const int tm = (a.M + BM - 1) / BM, tn = (a.N + bn_size - 1) / bn_size;
+  if (!a.sym) {
+    bm = u % tm;
+    bn = u / tm;
+    return;
+  }
+  for (int r = 0; r < tm; ++r) {
+    const int first = (r * BM) / bn_size, cnt = tn - first;
+    if (u < cnt) {
+      bm = r;
+      bn = first + u;
+      return;
+    }
+    u -= cnt;
+  }
+  bm = tm;
+  bn = tn;
+}
+
+__device__ __forceinline__ uint16_t to16(float x, int bf16) {
+  return bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(x)) : __half_as_ushort(__float2half_rn(x));
+}
+__device__ __forceinline__ float from16(uint16_t h, int bf16) {
+  return bf16 ? __bfloat162float(__ushort_as_bfloat16(h)) : __half2float(__ushort_as_half(h));
+}
+
+// Store 32 16-bit values of row i starting at column col0; entries with j >= n, or
+// j < i when `upper`, are skipped.  Mirror: also write (j, i) for i < j.
+__device__ __forceinline__ void put16(uint16_t* base, int ld, int i, int col0, int n, bool upper, bool mirror,
+                                      const uint16_t (&h)[32]) {
+  if (!base) return;
+  const bool full = (col0 + 32 <= n) && (!upper || col0 >= i);
+  if (full) {
+    uint4* dst = reinterpret_cast<uint4*>(base + (size_t)i * ld + col0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint4 w;
+      w.x = (uint32_t)h[q * 8 + 0] | ((uint32_t)h[q * 8 + 1] << 16);
+      w.y = (uint32_t)h[q * 8 + 2] | ((uint32_t)h[q * 8 + 3] << 16);
+      w.z = (uint32_t)h[q * 8 + 4] | ((uint32_t)h[q * 8 + 5] << 16);
+      w.w = (uint32_t)h[q * 8 + 6] | ((uint32_t)h[q * 8 + 7] << 16);
+      dst[q] = w;
+    }
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = col0 + jj;
+      if (j < n && (!upper || j >= i)) base[(size_t)i * ld + j] = h[jj];
+    }
+  }
+  if (mirror) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = col0 + jj;
+      if (j < n && j > i) base[(size_t)j * ld + i] = h[jj];
+    }
+  }
+}
+
+__device__ __forceinline__ void put32(float* base, int ld, int i, int col0, int n, bool upper, bool mirror,
+                                      const float (&x)[32]) {
+  const bool full = (col0 + 32 <= n) && (!upper || col0 >= i);
+  if (full) {
+    float4* dst = reinterpret_cast<float4*>(base + (size_t)i * ld + col0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = col0 + jj;
+      if (j < n && (!upper || j >= i)) base[(size_t)i * ld + j] = x[jj];
+    }
+  }
+  if (mirror) {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = col0 + jj;
+      if (j < n && j > i) base[(size_t)j * ld + i] = x[jj];
+    }
+  }
+}
+
+// Transposed store of 32 values of row i: element j goes to (j, i).  Coalesced across the warp.
+__device__ __forceinline__ void put16_t(uint16_t* base, int ld, int i, int col0, int n, const uint16_t (&h)[32]) {
+  if (!base) return;
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj) {
+    const int j = col0 + jj;
+    if (j < n) base[(size_t)j * ld + i] = h[jj];
+  }
+}
+
+__device__ __forceinline__ void split32(const float (&x)[32], float sc, int bf16, bool want_lo, uint16_t (&h)[32],
+                                        uint16_t (&l)[32]) {
+#pragma unroll
+  for (int jj = 0; jj < 32; ++jj) {
+    const float y = x[jj] * sc;
+    h[jj] = to16(y, bf16);
+    l[jj] = want_lo ? to16(y - from16(h[jj], bf16), bf16) : (uint16_t)0;
+  }
+}
+
+__device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, float (&v)[32], double& ss, float& amax,
+                                          float osc, float us) {
+  const int n = a.N;
+  if (i >= a.M) return;
+  const bool lo = a.split_out != 0;
+  uint16_t h[32], l[32];
+  switch (a.epi) {
+    case kEpiStore16: {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) v[jj] *= us;
+      split32(v, osc, a.bf16, lo, h, l);
+      put16(a.o16h, a.ld16, i, col0, n, false, false, h);
+      if (lo) put16(a.o16l, a.ld16, i, col0, n, false, false, l);
+      break;
+    }
+    case kEpiResid: {
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = col0 + jj;
+        const float d = (i == j ? 1.0f : 0.0f) - v[jj] * us;
+        v[jj] = d;
+        if (j < n && j >= i) {
+          const double dd = (double)d;
+          ss += (i == j ? 1.0 : 2.0) * dd * dd;
+          amax = fmaxf(amax, fabsf(d));
+        }
+      }
+      put32(a.f32, a.ld32, i, col0, n, true, true, v);
+      split32(v, osc, a.bf16, lo, h, l);
+      put16(a.o16h, a.ld16, i, col0, n, true, true, h);
+      if (lo) put16(a.o16l, a.ld16, i, col0, n, true, true, l);
+      break;
+    }
+    case kEpiPoly: {
+      // r = c1 * f32_in + c2 * v: the running sum of c_k d^k.  Outputs: the running sum in
+      // FP32 (f32), its 16-bit copy (o16, the final Q), and the raw power v (t16, P_k for
+      // the next product of the chain), all at (i, j) and (j, i).
+      const float* drow = a.f32_in + (size_t)i * a.ld32;
+      float r[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = col0 + jj;
+        const float d = (j < n) ? drow[j] : 0.0f;
+        v[jj] *= us;
+        r[jj] = a.c1 * d + a.c2 * v[jj];
+      }
+      if (a.f32) put32(a.f32, a.ld32, i, col0, n, true, true, r);
+      if (a.o16h) {
+        split32(r, osc, a.bf16, lo, h, l);
+        put16(a.o16h, a.ld16, i, col0, n, true, true, h);
+        if (lo) put16(a.o16l, a.ld16, i, col0, n, true, true, l);
+      }
+      if (a.t16h) {
+        split32(v, a.p_scale ? *a.p_scale : 1.0f, a.bf16, lo, h, l);
+        put16(a.t16h, a.ld16, i, col0, n, true, true, h);
+        if (lo) put16(a.t16l, a.ld16, i, col0, n, true, true, l);
+      }
+      break;
+    }
+    case kEpiZupd: {
+      float* zrow = a.f32 + (size_t)i * a.ld32;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = col0 + jj;
+        if (j < n) {
+          const float z = zrow[j] + v[jj] * us;
+          zrow[j] = z;
+          v[jj] = z;
+          amax = fmaxf(amax, fabsf(z));
+        } else {
+          v[jj] = 0.0f;
+        }
+      }
+      split32(v, osc, a.bf16, lo, h, l);
+      put16(a.o16h, a.ld16, i, col0, n, false, false, h);
+      if (lo) put16(a.o16l, a.ld16, i, col0, n, false, false, l);
+      put16_t(a.t16h, a.ld16, i, col0, n, h);
+      if (lo) put16_t(a.t16l, a.ld16, i, col0, n, l);
+      break;
+    }
+    case kEpiF64: {
+      double* crow = a.f64 + (size_t)i * a.ld64;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = col0 + jj;
+        if (j < n) crow[j] = (double)v[jj] * (double)us;
+      }
+      break;
+    }
+    case kEpiZupd64: {
+      double* zrow = a.f64 + (size_t)i * a.ld64;
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int j = col0 + jj;
+        if (j < n) {
+          const double z = zrow[j] + (double)v[jj] * (double)us;
+          zrow[j] = z;
+          v[jj] = (float)z;
+          amax = fmaxf(amax, fabsf((float)z));
+        } else {
+          v[jj] = 0.0f;
+        }
+      }
+      if (a.o16h) {
+        split32(v, osc, a.bf16, lo, h, l);
+        put16(a.o16h, a.ld16, i, col0, n, false, false, h);
+        if (lo) put16(a.o16l, a.ld16, i, col0, n, false, false, l);
+        put16_t(a.t16h, a.ld16, i, col0, n, h);
+        if (lo) put16_t(a.t16l, a.ld16, i, col0, n, l);
+      }
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__ TcMaps maps, const TcArgs a) {
+  using C = Cfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = align1024(smem_raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* tfull = empty + C::STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* done_bar = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int units = units_of(a.M, a.N, a.sym, BN);
+  const int kblocks = (a.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(done_bar, 1);
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    for (int s = 0; s < a.nseg; ++s) {
+      tma_prefetch_desc(&maps.a[s]);
+      tma_prefetch_desc(&maps.b[s]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        int bm, bn;
+        decode_unit(u, a, BN, bm, bn);
+        for (int s = 0; s < a.nseg && ok; ++s) {
+          for (int kb = 0; kb < kblocks; ++kb, ++it) {
+            const int st = it % C::STAGES;
+            const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+            if (!mbar_wait(&empty[st], ph ^ 1u, a.err_flag, 1)) {
+              ok = false;
+              break;
+            }
+            uint8_t* sa = smem + st * C::STAGE;
+            mbar_arrive_expect_tx(&full[st], C::STAGE);
+            tma_load_2d(sa, &maps.a[s], kb * BK, bm * BM, &full[st]);
+            tma_load_2d(sa + C::A_BYTES, &maps.b[s], kb * BK, bn * BN, &full[st]);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(BM, BN, a.bf16 != 0);
+      int it = 0, ui = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
+        const int buf = ui & 1;
+        const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
+        if (!mbar_wait(&tempty[buf], uph ^ 1u, a.err_flag, 2)) break;
+        tc_fence_after();
+        const uint32_t dtm = tmem_base + (uint32_t)(buf * BN);
+        uint32_t acc = 0;
+        for (int s = 0; s < a.nseg && ok; ++s) {
+          for (int kb = 0; kb < kblocks; ++kb, ++it) {
+            const int st = it % C::STAGES;
+            const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+            if (!mbar_wait(&full[st], ph, a.err_flag, 3)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + st * C::STAGE);
+            const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sa + C::A_BYTES);
+#pragma unroll
+            for (int k = 0; k < BK / UK; ++k) {
+              // advance the start address by k * 16 elements * 2 bytes inside the swizzle atom
+              tc_mma_f16(dtm, da + (uint64_t)((k * UK * 2) >> 4), db + (uint64_t)((k * UK * 2) >> 4), idesc, acc);
+              acc = 1;
+            }
+            tc_commit(&empty[st]);
+          }
+        }
+        if (ok) tc_commit(&tfull[buf]);
+      }
+      tc_commit(done_bar);
+      mbar_wait(done_bar, 0, a.err_flag, 4);
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    int ui = 0;
+    const float osc = a.out_scale ? *a.out_scale : 1.0f;
+    float us = a.unscale;
+    if (a.sa_ptr) us /= *a.sa_ptr;
+    if (a.sb_ptr) us /= *a.sb_ptr;
+    float amax = 0.0f;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++ui) {
+      const int buf = ui & 1;
+      const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
+      if (!mbar_wait(&tfull[buf], uph, a.err_flag, 5)) break;
+      tc_fence_after();
+      int bm, bn;
+      decode_unit(u, a, BN, bm, bn);
+      const int i = bm * BM + q * 32 + lane;
+      double ss = 0.0;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        float v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
+        const int col0 = bn * BN + c * 32;
+        if (a.sym && col0 + 31 < bm * BM) continue;  // chunk entirely below the diagonal block
+        epi_chunk(a, i, col0, v, ss, amax, osc, us);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      if (a.epi == kEpiResid) {
+        // fixed-order warp reduction; one partial per (tile, quadrant), summed in order later
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) a.partials[(size_t)u * 4 + q] = ss;
+      }
+    }
+    if (a.amax_bits) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if (lane == 0) atomicMax(a.amax_bits, __float_as_uint(amax));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, C::TMEM_COLS);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+}  // namespace
+
+int tc_make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows, bool bf16) {
+  if ((ld % 8) != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return -1;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = cuTensorMapEncodeTiled(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                                      const_cast<void*>(base), dims, strides, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : (int)r;
+}
+
+int tc_num_units(const TcArgs& a, int bn) { return units_of(a.M, a.N, a.sym, bn); }
+
+template <int BN>
+static cudaError_t launch_bn(const TcArgs& a, const TcMaps& maps, int num_sms, cudaStream_t s) {
+  static bool attr_set = false;
+  using C = Cfg<BN>;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int units = units_of(a.M, a.N, a.sym, BN);
+  const int grid = units < num_sms ? units : num_sms;
+  if (grid <= 0) return cudaSuccess;
+  k_tc_gemm<BN><<<grid, NTHREADS, C::SMEM, s>>>(maps, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(const TcArgs& a, const TcMaps& maps, int bn, int num_sms, cudaStream_t s) {
+  if (a.nseg < 1 || a.nseg > kTcMaxSeg) return cudaErrorInvalidValue;
+  if (bn == 256) return launch_bn<256>(a, maps, num_sms, s);
+  if (bn == 128) return launch_bn<128>(a, maps, num_sms, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace zf

@@ -1,0 +1,64 @@
+// Host-side launchers of libzfact's kernels (C++ linkage, internal to the library).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace zf {
+
+// ----------------------------------------------------------------- FP64 CUDA-core products (k_f64.cu)
+// acc = op(A) B for N x N row-major FP64 matrices, op(A) = A or A^T.
+// Epilogue:  C = alpha * Add + beta * acc   (Add == nullptr: C = beta * acc),
+//            P = acc when P != nullptr (raw product, for power chains),
+//            sym: only tiles with row-block <= col-block are formed; entry (i,j), i <= j,
+//                 is written to (i,j) and (j,i).
+// Residual epilogue (resid == true, requires sym and op(A) = A^T):
+//            C = I - acc, and partials[block] = sum of C_ij^2 over the entries the block owns
+//            (off-diagonal entries count twice), to be reduced by launch_finish_err.
+struct F64Gemm {
+  const double* A;
+  const double* B;
+  double* C;
+  const double* Add;
+  double* P;
+  double alpha, beta;
+  double* partials;
+  int n;
+  bool transA, sym, resid;
+};
+int f64_num_blocks(int n, bool sym);
+cudaError_t launch_f64_gemm(const F64Gemm& g, cudaStream_t s);
+
+// ----------------------------------------------------------------- elementwise / reductions (k_elem.cu)
+// st->gscale = 1/sqrt(max_i sum_j |S_ij|) (st->amax[0] is used as scratch).
+cudaError_t launch_gershgorin(const double* S, int n, IterState* st, cudaStream_t s);
+// Z = st->gscale * I (FP64, N x N).
+cudaError_t launch_scaled_identity_f64(double* Z, int n, const IterState* st, cudaStream_t s);
+// Err = sqrt(sum of partials in a fixed order) -> st->hist[idx]; if check_stop, evaluate the stop
+// rule against st->hist[idx-1] (rule 0: Algorithm 2 with guards; rule 1: Err/sqrt(N) <= tol).
+cudaError_t launch_finish_err(const double* partials, int nparts, IterState* st, int idx, int rule,
+                              double tol, int n, int check_stop, cudaStream_t s);
+
+// 16-bit operand copies of an FP64 matrix (Eq. splitStyle): x = FP32[scale * src_ij],
+// hi = R16(x), lo = R16(x - hi) (lo skipped when lo == nullptr), written at (i, j), or at
+// (j, i) when transpose.  scale = *scale_ptr when scale_ptr != nullptr, else `scale`.
+cudaError_t launch_cvt16(const double* src, int n, int ld_src, uint16_t* hi, uint16_t* lo, int ld16, double scale,
+                         const float* scale_ptr, bool transpose, bool bf16, cudaStream_t s);
+// The same from an FP32 source.
+cudaError_t launch_cvt16_f32(const float* src, int n, int ld_src, uint16_t* hi, uint16_t* lo, int ld16,
+                             bool transpose, bool bf16, cudaStream_t s);
+// Flat split of n values (zfact_split).
+cudaError_t launch_split_flat(const double* A, int64_t n, double scale, uint16_t* hi, uint16_t* lo, bool bf16,
+                              cudaStream_t s);
+// dst32 = (float) src64 (n x n, leading dimensions ld64 / ld32) and back.
+cudaError_t launch_f64_to_f32(const double* src, int n, int ld64, float* dst, int ld32, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float* src, int n, int ld32, double* dst, int ld64, cudaStream_t s);
+// st->amax[slot] = max |A_ij| (FP64 bits, non-negative ordering).
+cudaError_t launch_amax_f64(const double* A, int n, IterState* st, int slot, cudaStream_t s);
+// Power-of-two scales for FP16 operands: st->scale[k] = 2^e with bound_k * 2^e in (2^13, 2^14],
+// bound_0 = amax[1] (d), bound_1 = c1*amax[1] + c2*hist[idx]^2 (Q), bound_2 = amax[2] (Z).
+cudaError_t launch_pow2_scales(IterState* st, int idx, float c1, float c2, cudaStream_t s);
+
+}  // namespace zf

@@ -1,0 +1,299 @@
+// Mixed-precision driver: bulk iterations of Eq. np1 on the tensor cores in the
+// schemes of Table I ((h)(h) with 16-bit operands and FP32 accumulation, or
+// the split (h)(h)+(h)(l)+(l)(h) of Sec. 3.2), stopped by Algorithm 2, then
+// Algorithm 3's refinement with d formed in FP64 accuracy.
+//
+// Per bulk iteration (all products tcgen05, FP32 accumulation in TMEM):
+//   K3  Q  = c1 d + c2 d^2 (+ c_k d^k)       symmetric tiles, fused polynomial epilogue
+//   K4  Z' = Z + Z Q                          FP32 master update + 16-bit Z and Z^T copies
+//   K1  A^T = Z^T S                           16-bit A^T for the next product
+//   K2  d  = I - Z^T A, Err = ||d||_F         symmetric tiles, fused residual epilogue
+// Z^T S is formed instead of S Z because S is symmetric: both operands of every
+// product are then K-major (row-major) 16-bit matrices, which is what a TMA
+// box and a tcgen05 shared-memory descriptor read directly.
+#include <math.h>
+#include <string.h>
+
+#include <utility>
+
+#include "ctx.h"
+#include "kernels.h"
+#include "tc_gemm.h"
+
+using namespace zf;
+
+namespace {
+
+struct Mat16 {
+  uint16_t* h = nullptr;
+  uint16_t* l = nullptr;
+};
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+int alloc16(zfact_ctx* c, const char* name, int n, int ld, bool split, Mat16* m) {
+  int st = ZFACT_OK;
+  const size_t bytes = (size_t)n * ld * sizeof(uint16_t);
+  std::string nh = std::string(name) + ".h", nl = std::string(name) + ".l";
+  m->h = (uint16_t*)ctx_buf(c, nh.c_str(), bytes, &st);
+  if (!m->h) return st;
+  if (split) {
+    m->l = (uint16_t*)ctx_buf(c, nl.c_str(), bytes, &st);
+    if (!m->l) return st;
+  } else {
+    m->l = nullptr;
+  }
+  return ZFACT_OK;
+}
+
+}  // namespace
+
+// A tensor-core product D = sum_s A_s B_s^T (B_s given N x K, i.e. the row-major matrix whose
+// rows are the columns of the right factor), with the split segments of Sec. 3.2 when
+// A.l / B.l are present: (h)(h) + (h)(l) + (l)(h).
+int tc_product(zfact_ctx* c, TcArgs& a, const Mat16& A, const Mat16& B, int ld, int bn) {
+  TcMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  const uint16_t* as[3] = {A.h, A.h, A.l};
+  const uint16_t* bs[3] = {B.h, B.l, B.h};
+  int nseg = 1;
+  if (A.l && B.l) nseg = 3;
+  for (int s = 0; s < nseg; ++s) {
+    int r1 = tc_make_map(&maps.a[s], as[s], a.M, a.K, ld, 128, a.bf16 != 0);
+    int r2 = tc_make_map(&maps.b[s], bs[s], a.N, a.K, ld, bn, a.bf16 != 0);
+    if (r1 || r2) return ctx_fail(c, ZFACT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d, %d)", r1, r2);
+  }
+  a.nseg = nseg;
+  a.err_flag = &c->st_dev->error;
+  return ctx_cuda(c, launch_tc_gemm(a, maps, bn, c->num_sms, c->stream), "tcgen05 gemm");
+}
+
+int tc_product_public(zfact_ctx* c, TcArgs& a, const uint16_t* Ah, const uint16_t* Al, const uint16_t* Bh,
+                      const uint16_t* Bl, int ld, int bn) {
+  Mat16 A, B;
+  A.h = const_cast<uint16_t*>(Ah);
+  A.l = const_cast<uint16_t*>(Al);
+  B.h = const_cast<uint16_t*>(Bh);
+  B.l = const_cast<uint16_t*>(Bl);
+  return tc_product(c, a, A, B, ld, bn);
+}
+
+static TcArgs tc_args(int n, bool bf16) {
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.M = a.N = a.K = n;
+  a.bf16 = bf16 ? 1 : 0;
+  a.unscale = 1.0f;
+  return a;
+}
+
+int pick_bn(int n) { return n <= 128 ? 128 : 256; }
+
+int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int n, int order, int precision,
+                 const zfact_opts& o, int* iters_out, int* ridx_out, zfact_info* inf) {
+  const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
+  const bool split = (precision == ZFACT_P_FP16_SPLIT || precision == ZFACT_P_BF16_SPLIT);
+  if (!bf16) return ctx_fail(c, ZFACT_ERR_UNSUPPORTED, "FP16 bulk precisions are not available yet");
+  const int ld = round_up(n, 64);
+  const int bn = pick_bn(n);
+  int st = ZFACT_OK;
+  double coef[8];
+  coef[0] = 1.0;
+  for (int k = 1; k <= order; ++k) coef[k] = coef[k - 1] * (2.0 * k - 1.0) / (2.0 * k);
+
+  // ---- workspace
+  Mat16 S16, Za, Zta, Zb, Ztb, At, D16, Q16, Pa, Pb;
+  if ((st = alloc16(c, "S16", n, ld, split, &S16))) return st;
+  if ((st = alloc16(c, "Z16a", n, ld, split, &Za))) return st;
+  if ((st = alloc16(c, "Zt16a", n, ld, split, &Zta))) return st;
+  if ((st = alloc16(c, "Z16b", n, ld, split, &Zb))) return st;
+  if ((st = alloc16(c, "Zt16b", n, ld, split, &Ztb))) return st;
+  if ((st = alloc16(c, "At16", n, ld, split, &At))) return st;
+  if ((st = alloc16(c, "D16", n, ld, split, &D16))) return st;
+  if ((st = alloc16(c, "Q16", n, ld, split, &Q16))) return st;
+  if (order > 2) {
+    if ((st = alloc16(c, "P16a", n, ld, split, &Pa))) return st;
+    if ((st = alloc16(c, "P16b", n, ld, split, &Pb))) return st;
+  }
+  float* Zm = (float*)ctx_buf(c, "Zm32", sizeof(float) * (size_t)n * ld, &st);
+  if (!Zm) return st;
+  float* D32 = (float*)ctx_buf(c, "D32", sizeof(float) * (size_t)n * ld, &st);
+  if (!D32) return st;
+  float* Q32 = nullptr;
+  if (order > 2) {
+    Q32 = (float*)ctx_buf(c, "Q32", sizeof(float) * (size_t)n * ld, &st);
+    if (!Q32) return st;
+  }
+  const int max_units = tc_num_units(tc_args(n, bf16), 128) + 16;
+  double* partials = (double*)ctx_buf(c, "tc_partials", sizeof(double) * 4 * (size_t)max_units, &st);
+  if (!partials) return st;
+
+  // ---- set-up: 16-bit S (once), FP32 master Z and its 16-bit copies
+  if ((st = ctx_cuda(c, launch_cvt16(S, n, n, S16.h, S16.l, ld, 1.0, nullptr, false, bf16, c->stream), "S16")))
+    return st;
+  if ((st = ctx_cuda(c, launch_f64_to_f32(Za64, n, n, Zm, ld, c->stream), "Z master"))) return st;
+  if ((st = ctx_cuda(c, launch_cvt16(Za64, n, n, Za.h, Za.l, ld, 1.0, nullptr, false, bf16, c->stream), "Z16")))
+    return st;
+  if ((st = ctx_cuda(c, launch_cvt16(Za64, n, n, Zta.h, Zta.l, ld, 1.0, nullptr, true, bf16, c->stream), "Zt16")))
+    return st;
+
+  Mat16* Zc = &Za;
+  Mat16* Ztc = &Zta;
+  Mat16* Zn = &Zb;
+  Mat16* Ztn = &Ztb;
+
+  // d = I - Z^T S Z from the current 16-bit Z; Err -> hist[idx]
+  auto residual = [&](int idx, int check_stop) -> int {
+    int s2;
+    TcArgs k1 = tc_args(n, bf16);
+    k1.epi = kEpiStore16;
+    k1.split_out = split;
+    k1.o16h = At.h;
+    k1.o16l = At.l;
+    k1.ld16 = ld;
+    if ((s2 = tc_product(c, k1, *Ztc, S16, ld, bn))) return s2;
+    TcArgs k2 = tc_args(n, bf16);
+    k2.epi = kEpiResid;
+    k2.sym = 1;
+    k2.split_out = split;
+    k2.f32 = D32;
+    k2.ld32 = ld;
+    k2.o16h = D16.h;
+    k2.o16l = D16.l;
+    k2.ld16 = ld;
+    k2.partials = partials;
+    k2.amax_bits = &c->st_dev->amaxf[1];
+    if ((s2 = tc_product(c, k2, *Ztc, At, ld, bn))) return s2;
+    const int np = 4 * tc_num_units(k2, bn);
+    return ctx_cuda(c, launch_finish_err(partials, np, c->st_dev, idx, o.stop_rule, o.tol, n, check_stop, c->stream),
+                    "finish err");
+  };
+
+  // Q = sum_k c_k d^k (products of commuting symmetric matrices: symmetric tiles)
+  auto polynomial = [&]() -> int {
+    int s2;
+    Mat16* Pin = &D16;
+    Mat16* Pout = &Pa;
+    for (int k = 2; k <= order; ++k) {
+      TcArgs kp = tc_args(n, bf16);
+      kp.epi = kEpiPoly;
+      kp.sym = 1;
+      kp.split_out = split;
+      kp.f32_in = (k == 2) ? D32 : Q32;
+      kp.ld32 = ld;
+      kp.c1 = (k == 2) ? (float)coef[1] : 1.0f;
+      kp.c2 = (float)coef[k];
+      kp.ld16 = ld;
+      if (k == order) {
+        kp.o16h = Q16.h;
+        kp.o16l = Q16.l;
+      } else {
+        kp.f32 = Q32;
+        kp.t16h = Pout->h;
+        kp.t16l = Pout->l;
+      }
+      if ((s2 = tc_product(c, kp, *Pin, D16, ld, bn))) return s2;
+      Pin = Pout;
+      Pout = (Pout == &Pa) ? &Pb : &Pa;
+    }
+    return ZFACT_OK;
+  };
+
+  // ---- bulk phase (Algorithm 2)
+  if ((st = residual(0, 0))) return st;
+  if ((st = ctx_read_state(c))) return st;
+  const double err0 = c->st_host->hist[0];
+  if (!(err0 < 1.0)) inf->warn = ZFACT_WARN_NONCONTRACTIVE;
+  bool done = c->st_host->nonfinite || (o.fixed_iters <= 0 && o.stop_rule == 1 && err0 / sqrt((double)n) <= o.tol);
+  const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.nmax;
+  int iters = 0;
+  while (!done && iters < limit && iters + 1 + o.refine_steps + 1 < kHistMax) {
+    if ((st = polynomial())) return st;
+    TcArgs k4 = tc_args(n, bf16);
+    k4.epi = kEpiZupd;
+    k4.split_out = split;
+    k4.f32 = Zm;
+    k4.ld32 = ld;
+    k4.o16h = Zn->h;
+    k4.o16l = Zn->l;
+    k4.t16h = Ztn->h;
+    k4.t16l = Ztn->l;
+    k4.ld16 = ld;
+    if ((st = tc_product(c, k4, *Zc, Q16, ld, bn))) return st;
+    std::swap(Zc, Zn);
+    std::swap(Ztc, Ztn);
+    ++iters;
+    if ((st = residual(iters, o.fixed_iters <= 0 ? 1 : 0))) return st;
+    if ((st = ctx_read_state(c))) return st;
+    done = c->st_host->nonfinite || c->st_host->stop;
+  }
+  *iters_out = iters;
+  if (c->st_host->nonfinite) {
+    c->mixed_result = Za64;
+    return ZFACT_OK;
+  }
+
+  // ---- refinement (Algorithm 3): Z = FP64[Z]; X = Z^T S Z in FP64; Z = Z p(X)
+  if ((st = ctx_cuda(c, launch_f32_to_f64(Zm, n, ld, Za64, n, c->stream), "Z to FP64"))) return st;
+  double* Z64 = Za64;
+  double* A64 = (double*)ctx_buf(c, "A64", sizeof(double) * (size_t)n * n, &st);
+  if (!A64) return st;
+  double* D64 = (double*)ctx_buf(c, "D64", sizeof(double) * (size_t)n * n, &st);
+  if (!D64) return st;
+  // FP16 hi/lo operands with power-of-two scales for the refinement products
+  Mat16 Dr, Qr, Zr;
+  if ((st = alloc16(c, "D16r", n, ld, true, &Dr))) return st;
+  if ((st = alloc16(c, "Q16r", n, ld, true, &Qr))) return st;
+  if ((st = alloc16(c, "Z16r", n, ld, true, &Zr))) return st;
+  int ridx = 0;
+  int idx = iters;
+  for (int r = 0; r <= o.refine_steps; ++r) {
+    ++idx;
+    if ((st = f64_residual(c, S, Z64, A64, D64, n, idx, o.stop_rule, o.tol, 0))) return st;
+    if ((st = ctx_read_state(c))) return st;
+    const double err = c->st_host->hist[idx];
+    inf->resid_f = err;
+    if (c->st_host->nonfinite) break;
+    if (r == o.refine_steps) break;
+    if (o.tol > 0 && err / sqrt((double)n) <= o.tol) break;
+    // Q = c1 d + c2 d^2 with d in FP64 (FP16 hi/lo products for the quadratic term)
+    if ((st = ctx_cuda(c, launch_amax_f64(D64, n, c->st_dev, 1, c->stream), "amax d"))) return st;
+    if ((st = ctx_cuda(c, launch_amax_f64(Z64, n, c->st_dev, 2, c->stream), "amax Z"))) return st;
+    if ((st = ctx_cuda(c, launch_pow2_scales(c->st_dev, idx, (float)coef[1], (float)coef[2], c->stream), "scales")))
+      return st;
+    if ((st = ctx_cuda(c, launch_f64_to_f32(D64, n, n, D32, ld, c->stream), "d to FP32"))) return st;
+    if ((st = ctx_cuda(c, launch_cvt16(D64, n, n, Dr.h, Dr.l, ld, 1.0, &c->st_dev->scale[0], false, false, c->stream),
+                       "d16")))
+      return st;
+    TcArgs kq = tc_args(n, false);
+    kq.epi = kEpiPoly;
+    kq.sym = 1;
+    kq.split_out = 1;
+    kq.f32_in = D32;
+    kq.ld32 = ld;
+    kq.c1 = (float)coef[1];
+    kq.c2 = (float)coef[2];
+    kq.sa_ptr = &c->st_dev->scale[0];
+    kq.sb_ptr = &c->st_dev->scale[0];
+    kq.out_scale = &c->st_dev->scale[1];
+    kq.o16h = Qr.h;
+    kq.o16l = Qr.l;
+    kq.ld16 = ld;
+    if ((st = tc_product(c, kq, Dr, Dr, ld, bn))) return st;
+    // Z += Z Q with an FP64 master
+    if ((st = ctx_cuda(c, launch_cvt16(Z64, n, n, Zr.h, Zr.l, ld, 1.0, &c->st_dev->scale[2], false, false, c->stream),
+                       "Z16 refine")))
+      return st;
+    TcArgs ku = tc_args(n, false);
+    ku.epi = kEpiZupd64;
+    ku.f64 = Z64;
+    ku.ld64 = n;
+    ku.sa_ptr = &c->st_dev->scale[2];
+    ku.sb_ptr = &c->st_dev->scale[1];
+    if ((st = tc_product(c, ku, Zr, Qr, ld, bn))) return st;
+    ++ridx;
+  }
+  *ridx_out = ridx;
+  c->mixed_result = Z64;
+  return ZFACT_OK;
+}

@@ -1,0 +1,103 @@
+// Single steps of the recursion exposed through the C ABI for step-level
+// parity tests: a tensor-core product of 16-bit-rounded operands (Sec. 3.2,
+// Table I), the hi/lo split of Eq. splitStyle, and d = I - Z^T S Z.
+#include <math.h>
+#include <string.h>
+
+#include "ctx.h"
+#include "kernels.h"
+#include "tc_gemm.h"
+
+using namespace zf;
+
+int tc_product_public(zfact_ctx* c, TcArgs& a, const uint16_t* Ah, const uint16_t* Al, const uint16_t* Bh,
+                      const uint16_t* Bl, int ld, int bn);
+
+extern "C" int zfact_gemm(zfact_ctx* c, int precision, int64_t N, const double* A, double scale_a, const double* B,
+                          double scale_b, double* C) {
+  if (!c) return ZFACT_ERR_ARG;
+  if (!A || !B || !C) return ctx_fail(c, ZFACT_ERR_ARG, "null matrix");
+  if (N < 1 || N > 65536) return ctx_fail(c, ZFACT_ERR_ARG, "N out of range");
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C))
+    return ctx_fail(c, ZFACT_ERR_ARG, "zfact_gemm takes device pointers");
+  if (!(scale_a > 0) || !(scale_b > 0)) return ctx_fail(c, ZFACT_ERR_ARG, "scales must be positive");
+  cudaSetDevice(c->device);
+  const int n = (int)N;
+  int st = ZFACT_OK;
+  cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
+  if (precision == ZFACT_P_FP64) {
+    F64Gemm g{A, B, C, nullptr, nullptr, 0.0, 1.0, nullptr, n, false, false, false};
+    if ((st = ctx_cuda(c, launch_f64_gemm(g, c->stream), "f64 gemm"))) return st;
+    return ctx_read_state(c);
+  }
+  const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
+  const bool split = (precision == ZFACT_P_FP16_SPLIT || precision == ZFACT_P_BF16_SPLIT);
+  if (!bf16 && precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT)
+    return ctx_fail(c, ZFACT_ERR_ARG, "unknown precision %d", precision);
+  const int ld = (n + 63) / 64 * 64;
+  const size_t bytes = (size_t)n * ld * sizeof(uint16_t);
+  uint16_t* Ah = (uint16_t*)ctx_buf(c, "g.Ah", bytes, &st);
+  if (!Ah) return st;
+  uint16_t* Bh = (uint16_t*)ctx_buf(c, "g.Bh", bytes, &st);
+  if (!Bh) return st;
+  uint16_t *Al = nullptr, *Bl = nullptr;
+  if (split) {
+    Al = (uint16_t*)ctx_buf(c, "g.Al", bytes, &st);
+    if (!Al) return st;
+    Bl = (uint16_t*)ctx_buf(c, "g.Bl", bytes, &st);
+    if (!Bl) return st;
+  }
+  if ((st = ctx_cuda(c, launch_cvt16(A, n, n, Ah, Al, ld, scale_a, nullptr, false, bf16, c->stream), "A16")))
+    return st;
+  // the right factor is read as B^T (row-major N x K)
+  if ((st = ctx_cuda(c, launch_cvt16(B, n, n, Bh, Bl, ld, scale_b, nullptr, true, bf16, c->stream), "B16")))
+    return st;
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.M = a.N = a.K = n;
+  a.bf16 = bf16;
+  a.epi = kEpiF64;
+  a.unscale = (float)(1.0 / (scale_a * scale_b));
+  a.f64 = C;
+  a.ld64 = n;
+  const int bn = n <= 128 ? 128 : 256;
+  if ((st = tc_product_public(c, a, Ah, Al, Bh, Bl, ld, bn))) return st;
+  return ctx_read_state(c);
+}
+
+extern "C" int zfact_split(zfact_ctx* c, int precision, const double* A, int64_t n, double scale, uint16_t* hi,
+                           uint16_t* lo) {
+  if (!c) return ZFACT_ERR_ARG;
+  if (!A || !hi || !lo || n < 0) return ctx_fail(c, ZFACT_ERR_ARG, "bad arguments");
+  if (n == 0) return ZFACT_OK;
+  const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
+  if (!bf16 && precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT)
+    return ctx_fail(c, ZFACT_ERR_ARG, "split needs a 16-bit precision");
+  cudaSetDevice(c->device);
+  int st = ctx_cuda(c, launch_split_flat(A, n, scale, hi, lo, bf16, c->stream), "split");
+  if (st) return st;
+  return ctx_cuda(c, cudaStreamSynchronize(c->stream), "split sync");
+}
+
+extern "C" int zfact_residual(zfact_ctx* c, int mode, const double* S, const double* Z, int64_t N, double* D,
+                              double* err) {
+  if (!c) return ZFACT_ERR_ARG;
+  if (!S || !Z || !err) return ctx_fail(c, ZFACT_ERR_ARG, "null argument");
+  if (N < 1 || N > 65536) return ctx_fail(c, ZFACT_ERR_ARG, "N out of range");
+  if (mode != ZFACT_R_NATIVE) return ctx_fail(c, ZFACT_ERR_UNSUPPORTED, "refine mode %d not available", mode);
+  cudaSetDevice(c->device);
+  const int n = (int)N;
+  int st = ZFACT_OK;
+  double* A64 = (double*)ctx_buf(c, "A64", sizeof(double) * (size_t)n * n, &st);
+  if (!A64) return st;
+  double* Dw = D;
+  if (!Dw) {
+    Dw = (double*)ctx_buf(c, "D64", sizeof(double) * (size_t)n * n, &st);
+    if (!Dw) return st;
+  }
+  cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
+  if ((st = f64_residual(c, S, Z, A64, Dw, n, 0, 0, 0.0, 0))) return st;
+  if ((st = ctx_read_state(c))) return st;
+  *err = c->st_host->hist[0];
+  return ZFACT_OK;
+}

@@ -1,0 +1,62 @@
+// Host interface of the tcgen05 GEMM engine (k_tc.cu).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace zf {
+
+constexpr int kTcMaxSeg = 4;
+
+// Epilogue of a tensor-core product (acc = sum over segments of A_s B_s^T, FP32).
+// v = acc * unscale is the product in true units.
+enum TcEpi : int {
+  kEpiStore16 = 0,  // o16 (hi[, lo]) = R16(v * out_scale), row-major
+  kEpiResid = 1,    // sym: d = I - v; f32 (d) + o16 (d, hi[, lo]) at (i,j) and (j,i); Err partials; amax
+  kEpiPoly = 2,     // sym: r = c1 * f32_in + c2 * v -> f32 (r), o16 (r); t16 (v, raw power); mirrored
+  kEpiZupd = 3,     // f32_io += v; o16 = R16(f32_io * out_scale) row-major and t16 transposed
+  kEpiF64 = 4,      // f64_out = v (double), row-major
+  kEpiZupd64 = 5,   // f64_io += v (double); o16/t16 as kEpiZupd from the updated FP64 value
+};
+
+struct TcArgs {
+  int M, N, K;        // logical sizes of the product (rows of A, rows of B, reduction length)
+  int nseg;           // segments accumulated into one accumulator (K-concatenation)
+  int sym;            // upper-triangle tiles only; mirrored writes
+  int epi;            // TcEpi
+  int bf16;           // operand/output 16-bit format: 1 = BF16, 0 = FP16
+  int split_out;      // write the lo part of 16-bit outputs too
+  float unscale;      // 1 / (scale_A * scale_B), a power of two
+  const float* sa_ptr;     // device: extra A scale (unscale /= *sa_ptr), nullptr = none
+  const float* sb_ptr;     // device: extra B scale
+  const float* out_scale;  // device: scale applied before rounding 16-bit outputs (nullptr = 1)
+  const float* p_scale;    // device: scale of the raw-power output of kEpiPoly (nullptr = 1)
+  // epilogue operands (row-major, leading dimensions in elements)
+  float* f32;  int ld32;        // kEpiResid out (d), kEpiZupd in/out (Z master)
+  const float* f32_in;          // kEpiPoly: d in FP32
+  double* f64; int ld64;        // kEpiF64 out / kEpiZupd64 in-out
+  uint16_t* o16h; uint16_t* o16l; int ld16;
+  uint16_t* t16h; uint16_t* t16l;  // kEpiZupd: transposed copy
+  float c1, c2;
+  double* partials;             // kEpiResid: 4 per tile (one per TMEM lane quadrant)
+  unsigned int* amax_bits;      // kEpiResid: max |d| as FP32 bits; kEpiZupd: max |Z|
+  int* err_flag;
+};
+
+// Tensor maps of the operands: A segment s is a_maps[s] (M x K, K-major = row-major),
+// B segment s is b_maps[s] (N x K, row-major).
+struct TcMaps {
+  CUtensorMap a[kTcMaxSeg];
+  CUtensorMap b[kTcMaxSeg];
+};
+
+// Encode a tensor map of a row-major 16-bit matrix (rows x cols, leading dimension ld
+// elements, ld % 8 == 0) with a 64-column x box_rows box and 128-byte swizzle.
+int tc_make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows, bool bf16);
+
+int tc_num_units(const TcArgs& a, int bn);
+cudaError_t launch_tc_gemm(const TcArgs& a, const TcMaps& maps, int bn, int num_sms, cudaStream_t s);
+
+}  // namespace zf

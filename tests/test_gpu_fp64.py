@@ -1,0 +1,121 @@
+"""FP64 GPU path (the paper's "double") against the FP64 CPU oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_19163_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2404_19163_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_workload1_fixed_iters_parity(ctx):
+    S, Q, lam = synth.householder_spd(256, seed=0)
+    Zo, ho, it = oracle.refine(S, None, m=2, nmax=50)
+    r = ctx.refine(dev(S), None, order=2, precision="fp64", fixed_iters=it)
+    assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
+    assert np.allclose(r.hist[:it + 1], ho[:it + 1], rtol=1e-9, atol=1e-14)
+    assert r.info["iters"] == it
+
+
+def test_workload1_stop_rule(ctx):
+    S, Q, lam = synth.householder_spd(256, seed=0)
+    Zo, ho, it = oracle.refine(S, None, m=2, nmax=50)
+    r = ctx.refine(dev(S), None, order=2, precision="fp64")
+    # the stop fires at the FP64 noise floor; the count may differ by one there
+    assert abs(r.info["iters"] - it) <= 1
+    assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
+    R = (Q * lam ** -0.5) @ Q.T
+    assert rel(r.Z.cpu().numpy(), R) <= 1e-13
+    assert r.info["resid_f"] / 16.0 < 1e-14
+
+
+@pytest.mark.parametrize("n", [1, 7, 63, 65, 130, 300])
+def test_ragged_sizes(ctx, n):
+    S, Q, lam = synth.householder_spd(n, seed=n)
+    Zo, ho, it = oracle.refine(S, None, m=2, nmax=50, fixed_iters=4)
+    r = ctx.refine(dev(S), None, order=2, precision="fp64", fixed_iters=4)
+    assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
+
+
+@pytest.mark.parametrize("m", [3, 4, 5])
+def test_higher_orders(ctx, m):
+    S, Q, lam = synth.householder_spd(200, seed=m)
+    Zo, ho, it = oracle.refine(S, None, m=m, nmax=50, fixed_iters=3)
+    r = ctx.refine(dev(S), None, order=m, precision="fp64", fixed_iters=3)
+    assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
+    assert np.allclose(r.hist, ho, rtol=1e-9, atol=1e-14)
+
+
+def test_warm_start_general_z0(ctx):
+    g = np.random.default_rng(5)
+    S, Q, lam = synth.householder_spd(150, seed=9)
+    Z0 = (Q * lam ** -0.5) @ Q.T + 0.01 * g.standard_normal((150, 150))
+    Zo, ho, it = oracle.refine(S, Z0, m=2, nmax=50, fixed_iters=3)
+    r = ctx.refine(dev(S), dev(Z0), order=2, precision="fp64", fixed_iters=3)
+    assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
+
+
+def test_host_pointers(ctx):
+    S, Q, lam = synth.householder_spd(100, seed=11)
+    Zo, ho, it = oracle.refine(S, None, m=2, nmax=50, fixed_iters=3)
+    r = ctx.refine(np.ascontiguousarray(S), None, order=2, precision="fp64", fixed_iters=3)
+    assert isinstance(r.Z, np.ndarray)
+    assert rel(r.Z, Zo) <= 1e-12
+
+
+def test_tolerance_rule(ctx):
+    S, Q, lam = synth.householder_spd(128, seed=12)
+    Zo, ho, it = oracle.refine(S, None, m=2, nmax=50, rule=1, tol=1e-8)
+    r = ctx.refine(dev(S), None, order=2, precision="fp64", stop_rule=1, tol=1e-8)
+    assert r.info["iters"] == it
+    assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
+
+
+def test_errors(ctx):
+    import torch
+    from paper_2404_19163_gb300 import ZfactError
+    S = dev(np.eye(8))
+    with pytest.raises(ZfactError) as e:
+        ctx.refine(S, None, order=7)
+    assert e.value.code == 1
+    Sn = np.eye(8)
+    Sn[2, 3] = Sn[3, 2] = np.nan
+    with pytest.raises(ZfactError) as e:
+        ctx.refine(dev(Sn), None, order=2, precision="fp64")
+    assert e.value.code == 4
+    # a non-contractive start is reported as a warning with a result
+    r = ctx.refine(dev(np.eye(8) * 4.0), dev(np.eye(8)), order=2, precision="fp64", fixed_iters=1,
+                   raise_on_error=False)
+    assert r.status == 100
+
+
+def test_workload2_full_size_against_oracle(ctx):
+    """N = 4096 cubic Gaussian overlap, the launch configuration the benchmark times."""
+    S = synth.cubic_overlap()
+    n = S.shape[0]
+    r = ctx.refine(dev(S), None, order=2, precision="fp64")
+    it = r.info["iters"]
+    Zo, ho, ito = oracle.refine(S, None, m=2, nmax=50, fixed_iters=it)
+    assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
+    assert r.info["resid_f"] / math.sqrt(n) < 1e-13
