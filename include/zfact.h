@@ -77,7 +77,7 @@ typedef enum zfact_refine_mode {
 typedef struct zfact_opts {
     int nmax;            /* max bulk updates (default 50) */
     int refine_steps;    /* max FP64-d refinement updates after the bulk stop (Algorithm 3);
-                            default 0 for FP64, 2 for the mixed precisions */
+                            default 0 for FP64, 3 for the mixed precisions */
     int refine_mode;     /* zfact_refine_mode (default ZFACT_R_OZAKI when available) */
     int stop_rule;       /* 0: Algorithm 2 (Err_n > Err_{n-1}^3, or Err_n >= Err_{n-1}, or non-finite);
                             1: Algorithm 1 (Err_n / sqrt(N) <= tol) */
@@ -93,6 +93,7 @@ typedef struct zfact_info {
     int refine_iters;    /* refinement updates performed (Algorithm 3) */
     int hist_len;        /* entries written to hist */
     int warn;            /* 0 or ZFACT_WARN_NONCONTRACTIVE */
+    int launches;        /* kernels this call launched */
     double resid_f;      /* ||I - Z^T S Z||_F of the returned Z (FP64-accurate), NaN if not formed */
     double ms;           /* device time of the call (CUDA events around the work), milliseconds */
 } zfact_info;
@@ -175,6 +176,21 @@ int zfact_mlp_adam(zfact_ctx* ctx, float* params, const float* grad, float* m, f
  * Z0 = scale * I in *scale and m in *order (HOST). */
 int zfact_propose(zfact_ctx* ctx, const double* S, int64_t N, const float* params,
                   const float* feat_mean, const float* feat_std, double* scale, int* order);
+
+/* ---- per-kernel timing ----------------------------------------------------------------
+ * When profiling is on, every kernel launch of the context is bracketed by CUDA events
+ * on the context's stream; the per-kernel totals (launch count, device milliseconds,
+ * algorithmic FLOPs and bytes) accumulate until read with reset != 0. */
+typedef struct zfact_kstat {
+    char name[40];       /* kernel family, e.g. "tc_gemm.resid" */
+    int launches;
+    double ms;           /* summed device time of the launches */
+    double flops;        /* summed algorithmic floating-point operations */
+    double bytes;        /* summed algorithmic DRAM bytes */
+} zfact_kstat;
+int zfact_set_profiling(zfact_ctx* ctx, int on);
+/* Copies up to cap entries into out (HOST), the count into *n (HOST). */
+int zfact_kernel_stats(zfact_ctx* ctx, zfact_kstat* out, int cap, int* n, int reset);
 
 /* ---- single steps, exposed for step-level parity tests ----------------------------- */
 /* C = A B for N x N FP64 matrices with the operands rounded to the 16-bit format of

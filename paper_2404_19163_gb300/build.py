@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         for _, log in results:
             sys.stderr.write(log)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcuda", "-lcudart"]
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

@@ -60,6 +60,72 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// ----------------------------------------------------------------- per-kernel accounting
+int kstat_id(zfact_ctx* c, const char* name) {
+  for (size_t i = 0; i < c->kstats.size(); ++i)
+    if (c->kstats[i].name == name) return (int)i;
+  KStat k;
+  k.name = name;
+  c->kstats.push_back(k);
+  return (int)c->kstats.size() - 1;
+}
+
+cudaEvent_t ev_get(zfact_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void kstats_flush(zfact_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    KStat& k = c->kstats[p.id];
+    k.launches += p.count;
+    k.ms += ms;
+    k.flops += p.flops;
+    k.bytes += p.bytes;
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+extern "C" int zfact_set_profiling(zfact_ctx* c, int on) {
+  if (!c) return ZFACT_ERR_ARG;
+  c->profiling = on != 0;
+  return ZFACT_OK;
+}
+
+extern "C" int zfact_kernel_stats(zfact_ctx* c, zfact_kstat* out, int cap, int* n, int reset) {
+  if (!c) return ZFACT_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  kstats_flush(c);
+  int cnt = 0;
+  for (auto& k : c->kstats) {
+    if (out && cnt < cap) {
+      memset(&out[cnt], 0, sizeof(zfact_kstat));
+      strncpy(out[cnt].name, k.name.c_str(), sizeof(out[cnt].name) - 1);
+      out[cnt].launches = k.launches;
+      out[cnt].ms = k.ms;
+      out[cnt].flops = k.flops;
+      out[cnt].bytes = k.bytes;
+    }
+    ++cnt;
+  }
+  if (n) *n = cnt;
+  if (reset) c->kstats.clear();
+  return ZFACT_OK;
+}
+
 // ----------------------------------------------------------------- lifecycle
 extern "C" void zfact_default_opts(zfact_opts* o) {
   if (!o) return;
@@ -117,6 +183,8 @@ extern "C" void zfact_destroy(zfact_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (auto& kv : c->bufs) cudaFree(kv.second.ptr);
   c->bufs.clear();
+  kstats_flush(c);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);
   cudaEventDestroy(c->ev0);
@@ -133,6 +201,7 @@ int ctx_read_state(zfact_ctx* c) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   int s = ctx_cuda(c, e, "state read-back");
   if (s) return s;
+  kstats_flush(c);
   if (c->st_host->error & kErrTimeout)
     return ctx_fail(c, ZFACT_ERR_TIMEOUT, "a bounded device wait gave up (code 0x%x)", c->st_host->error);
   if (c->st_host->error & kErrShape) return ctx_fail(c, ZFACT_ERR_ARG, "kernel shape check failed");
@@ -147,11 +216,18 @@ int f64_residual(zfact_ctx* c, const double* S, const double* Z, double* A, doub
   const int nb = f64_num_blocks(n, true);
   double* partials = (double*)ctx_buf(c, "partials", sizeof(double) * (size_t)(nb + 1024), &st);
   if (!partials) return st;
+  const double n2 = (double)n * n, n3 = n2 * n;
   F64Gemm g1{S, Z, A, nullptr, nullptr, 0.0, 1.0, nullptr, n, false, false, false};
-  if ((st = ctx_cuda(c, launch_f64_gemm(g1, c->stream), "f64 S*Z"))) return st;
+  if ((st = ctx_cuda(c, klaunch(c, "f64_gemm.sz", 2 * n3, 24 * n2, 1, [&] { return launch_f64_gemm(g1, c->stream); }),
+                     "f64 S*Z")))
+    return st;
   F64Gemm g2{Z, A, D, nullptr, nullptr, 0.0, 1.0, partials, n, true, true, true};
-  if ((st = ctx_cuda(c, launch_f64_gemm(g2, c->stream), "f64 Z^T*A residual"))) return st;
-  return ctx_cuda(c, launch_finish_err(partials, nb, c->st_dev, idx, rule, tol, n, check_stop, c->stream),
+  if ((st = ctx_cuda(c, klaunch(c, "f64_gemm.resid", n3, 24 * n2, 1, [&] { return launch_f64_gemm(g2, c->stream); }),
+                     "f64 Z^T*A residual")))
+    return st;
+  return ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
+                    return launch_finish_err(partials, nb, c->st_dev, idx, rule, tol, n, check_stop, c->stream);
+                  }),
                   "finish err");
 }
 
@@ -162,12 +238,17 @@ int f64_poly(zfact_ctx* c, const double* D, double* Q, double* P, double* P2, in
   for (int k = 1; k <= m; ++k) coef[k] = coef[k - 1] * (2.0 * k - 1.0) / (2.0 * k);
   int st;
   // P = d*d, Q = c1 d + c2 P
+  const double n2 = (double)n * n, n3 = n2 * n;
   F64Gemm g{D, D, Q, D, m > 2 ? P : nullptr, coef[1], coef[2], nullptr, n, false, true, false};
-  if ((st = ctx_cuda(c, launch_f64_gemm(g, c->stream), "f64 poly"))) return st;
+  if ((st = ctx_cuda(c, klaunch(c, "f64_gemm.poly", n3, 24 * n2, 1, [&] { return launch_f64_gemm(g, c->stream); }),
+                     "f64 poly")))
+    return st;
   for (int k = 3; k <= m; ++k) {
     // P_k = P_{k-1} d ; Q += c_k P_k
     F64Gemm gk{P, D, Q, Q, k < m ? P2 : nullptr, 1.0, coef[k], nullptr, n, false, true, false};
-    if ((st = ctx_cuda(c, launch_f64_gemm(gk, c->stream), "f64 poly chain"))) return st;
+    if ((st = ctx_cuda(c, klaunch(c, "f64_gemm.poly", n3, 32 * n2, 1, [&] { return launch_f64_gemm(gk, c->stream); }),
+                       "f64 poly chain")))
+      return st;
     double* t = P;
     P = P2;
     P2 = t;
@@ -177,8 +258,10 @@ int f64_poly(zfact_ctx* c, const double* D, double* Q, double* P, double* P2, in
 
 // Zn = Z + Z Q
 int f64_update(zfact_ctx* c, const double* Z, const double* Q, double* Zn, int n) {
+  const double n2 = (double)n * n, n3 = n2 * n;
   F64Gemm g{Z, Q, Zn, Z, nullptr, 1.0, 1.0, nullptr, n, false, false, false};
-  return ctx_cuda(c, launch_f64_gemm(g, c->stream), "f64 update");
+  return ctx_cuda(c, klaunch(c, "f64_gemm.update", 2 * n3, 24 * n2, 1, [&] { return launch_f64_gemm(g, c->stream); }),
+                  "f64 update");
 }
 
 // ----------------------------------------------------------------- argument checks
@@ -205,7 +288,7 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   zfact_default_opts(&o);
   if (opts_in) o = *opts_in;
   if (o.nmax < 1) o.nmax = 1;
-  if (o.refine_steps < 0) o.refine_steps = (precision == ZFACT_P_FP64) ? 0 : 2;
+  if (o.refine_steps < 0) o.refine_steps = (precision == ZFACT_P_FP64) ? 0 : 3;
   if (o.refine_mode < 0) o.refine_mode = ZFACT_R_NATIVE;
   const int n = (int)N;
   const size_t nn = (size_t)n * n, bytes = nn * sizeof(double);
@@ -213,6 +296,7 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   memset(&inf, 0, sizeof(inf));
   inf.resid_f = NAN;
 
+  c->launches = 0;
   cudaEventRecord(c->ev0, c->stream);
   // ---- stage inputs (host inputs are copied in; device S is used in place)
   const double* S = S_in;
@@ -231,8 +315,14 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   if (Z0_in) {
     if ((st = ctx_cuda(c, cudaMemcpyAsync(Za, Z0_in, bytes, cudaMemcpyDefault, c->stream), "copy Z0"))) return st;
   } else {
-    if ((st = ctx_cuda(c, launch_gershgorin(S, n, c->st_dev, c->stream), "gershgorin"))) return st;
-    if ((st = ctx_cuda(c, launch_scaled_identity_f64(Za, n, c->st_dev, c->stream), "Z0"))) return st;
+    if ((st = ctx_cuda(c, klaunch(c, "gershgorin", 2.0 * n * n, 8.0 * n * n, 2,
+                                  [&] { return launch_gershgorin(S, n, c->st_dev, c->stream); }),
+                       "gershgorin")))
+      return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 8.0 * n * n, 1,
+                                  [&] { return launch_scaled_identity_f64(Za, n, c->st_dev, c->stream); }),
+                       "Z0")))
+      return st;
   }
 
   int iters = 0, ridx = 0;
@@ -299,6 +389,7 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   inf.refine_iters = ridx;
   inf.hist_len = hl < hist_cap ? hl : hist_cap;
   inf.ms = ms;
+  inf.launches = c->launches;
   if (!(c->st_host->hist[0] < 1.0)) inf.warn = ZFACT_WARN_NONCONTRACTIVE;
   if (info) *info = inf;
   if (c->st_host->nonfinite) return ctx_fail(c, ZFACT_ERR_NONFINITE, "Err became non-finite");

@@ -5,12 +5,26 @@
 
 #include <map>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
 struct DevBuf {
   void* ptr;
   size_t bytes;
+};
+
+struct KStat {
+  std::string name;
+  int launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+
+struct PendingEv {
+  int id;
+  cudaEvent_t a, b;
+  double flops, bytes;
+  int count;
 };
 
 struct zfact_ctx {
@@ -25,7 +39,31 @@ struct zfact_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double* mixed_result = nullptr;      // device FP64 Z produced by the mixed driver
   char err[512];
+  // per-kernel accounting
+  bool profiling = false;
+  int launches = 0;                  // kernels launched since the counter was last reset
+  std::vector<KStat> kstats;
+  std::vector<PendingEv> pending;
+  std::vector<cudaEvent_t> ev_pool;
 };
+
+int kstat_id(zfact_ctx* c, const char* name);
+cudaEvent_t ev_get(zfact_ctx* c);
+void kstats_flush(zfact_ctx* c);  // stream must be idle
+
+// Launch `f` (returning cudaError_t) as `count` kernels of family `name` with the given
+// algorithmic FLOPs / bytes; bracketed by events when profiling is on.
+template <class F>
+cudaError_t klaunch(zfact_ctx* c, const char* name, double flops, double bytes, int count, F&& f) {
+  c->launches += count;
+  if (!c->profiling) return f();
+  cudaEvent_t a = ev_get(c), b = ev_get(c);
+  cudaEventRecord(a, c->stream);
+  cudaError_t e = f();
+  cudaEventRecord(b, c->stream);
+  c->pending.push_back(PendingEv{kstat_id(c, name), a, b, flops, bytes, count});
+  return e;
+}
 
 int ctx_fail(zfact_ctx* c, int code, const char* fmt, ...);
 int ctx_cuda(zfact_ctx* c, cudaError_t e, const char* what);

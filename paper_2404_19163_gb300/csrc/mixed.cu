@@ -65,7 +65,16 @@ int tc_product(zfact_ctx* c, TcArgs& a, const Mat16& A, const Mat16& B, int ld, 
   }
   a.nseg = nseg;
   a.err_flag = &c->st_dev->error;
-  return ctx_cuda(c, launch_tc_gemm(a, maps, bn, c->num_sms, c->stream), "tcgen05 gemm");
+  static const char* names[] = {"tc_gemm.store16", "tc_gemm.resid", "tc_gemm.poly", "tc_gemm.zupd",
+                                "tc_gemm.f64out", "tc_gemm.zupd64"};
+  const double flops = (double)nseg * 2.0 * a.M * a.N * a.K * (a.sym ? 0.5 : 1.0);
+  const double in_bytes = (double)nseg * 2.0 * ((double)a.M * a.K + (double)a.N * a.K);
+  const double out_elems = (double)a.M * a.N;
+  const double out_bytes[] = {2, 4 + 2, 2, 8 + 4, 8, 16 + 4};
+  const int e = a.epi >= 0 && a.epi <= 5 ? a.epi : 0;
+  return ctx_cuda(c, klaunch(c, names[e], flops, in_bytes + out_elems * out_bytes[e] * (a.split_out ? 1.5 : 1.0), 1,
+                             [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, c->stream); }),
+                  "tcgen05 gemm");
 }
 
 int tc_product_public(zfact_ctx* c, TcArgs& a, const uint16_t* Ah, const uint16_t* Al, const uint16_t* Bh,
@@ -129,12 +138,12 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   if (!partials) return st;
 
   // ---- set-up: 16-bit S (once), FP32 master Z and its 16-bit copies
-  if ((st = ctx_cuda(c, launch_cvt16(S, n, n, S16.h, S16.l, ld, 1.0, nullptr, false, bf16, c->stream), "S16")))
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_cvt16(S, n, n, S16.h, S16.l, ld, 1.0, nullptr, false, bf16, c->stream); }), "S16")))
     return st;
-  if ((st = ctx_cuda(c, launch_f64_to_f32(Za64, n, n, Zm, ld, c->stream), "Z master"))) return st;
-  if ((st = ctx_cuda(c, launch_cvt16(Za64, n, n, Za.h, Za.l, ld, 1.0, nullptr, false, bf16, c->stream), "Z16")))
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f64_to_f32(Za64, n, n, Zm, ld, c->stream); }), "Z master"))) return st;
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_cvt16(Za64, n, n, Za.h, Za.l, ld, 1.0, nullptr, false, bf16, c->stream); }), "Z16")))
     return st;
-  if ((st = ctx_cuda(c, launch_cvt16(Za64, n, n, Zta.h, Zta.l, ld, 1.0, nullptr, true, bf16, c->stream), "Zt16")))
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_cvt16(Za64, n, n, Zta.h, Zta.l, ld, 1.0, nullptr, true, bf16, c->stream); }), "Zt16")))
     return st;
 
   Mat16* Zc = &Za;
@@ -165,7 +174,10 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     k2.amax_bits = &c->st_dev->amaxf[1];
     if ((s2 = tc_product(c, k2, *Ztc, At, ld, bn))) return s2;
     const int np = 4 * tc_num_units(k2, bn);
-    return ctx_cuda(c, launch_finish_err(partials, np, c->st_dev, idx, o.stop_rule, o.tol, n, check_stop, c->stream),
+    return ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
+                      return launch_finish_err(partials, np, c->st_dev, idx, o.stop_rule, o.tol, n, check_stop,
+                                               c->stream);
+                    }),
                     "finish err");
   };
 
@@ -234,7 +246,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   }
 
   // ---- refinement (Algorithm 3): Z = FP64[Z]; X = Z^T S Z in FP64; Z = Z p(X)
-  if ((st = ctx_cuda(c, launch_f32_to_f64(Zm, n, ld, Za64, n, c->stream), "Z to FP64"))) return st;
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f32_to_f64(Zm, n, ld, Za64, n, c->stream); }), "Z to FP64"))) return st;
   double* Z64 = Za64;
   double* A64 = (double*)ctx_buf(c, "A64", sizeof(double) * (size_t)n * n, &st);
   if (!A64) return st;
@@ -257,12 +269,15 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     if (r == o.refine_steps) break;
     if (o.tol > 0 && err / sqrt((double)n) <= o.tol) break;
     // Q = c1 d + c2 d^2 with d in FP64 (FP16 hi/lo products for the quadratic term)
-    if ((st = ctx_cuda(c, launch_amax_f64(D64, n, c->st_dev, 1, c->stream), "amax d"))) return st;
-    if ((st = ctx_cuda(c, launch_amax_f64(Z64, n, c->st_dev, 2, c->stream), "amax Z"))) return st;
-    if ((st = ctx_cuda(c, launch_pow2_scales(c->st_dev, idx, (float)coef[1], (float)coef[2], c->stream), "scales")))
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_amax_f64(D64, n, c->st_dev, 1, c->stream); }), "amax d"))) return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_amax_f64(Z64, n, c->st_dev, 2, c->stream); }), "amax Z"))) return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_pow2_scales(c->st_dev, idx, (float)coef[1], (float)coef[2], c->stream); }), "scales")))
       return st;
-    if ((st = ctx_cuda(c, launch_f64_to_f32(D64, n, n, D32, ld, c->stream), "d to FP32"))) return st;
-    if ((st = ctx_cuda(c, launch_cvt16(D64, n, n, Dr.h, Dr.l, ld, 1.0, &c->st_dev->scale[0], false, false, c->stream),
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f64_to_f32(D64, n, n, D32, ld, c->stream); }), "d to FP32"))) return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
+                         return launch_cvt16(D64, n, n, Dr.h, Dr.l, ld, 1.0, &c->st_dev->scale[0], false, false,
+                                             c->stream);
+                       }),
                        "d16")))
       return st;
     TcArgs kq = tc_args(n, false);
@@ -281,7 +296,10 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     kq.ld16 = ld;
     if ((st = tc_product(c, kq, Dr, Dr, ld, bn))) return st;
     // Z += Z Q with an FP64 master
-    if ((st = ctx_cuda(c, launch_cvt16(Z64, n, n, Zr.h, Zr.l, ld, 1.0, &c->st_dev->scale[2], false, false, c->stream),
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
+                         return launch_cvt16(Z64, n, n, Zr.h, Zr.l, ld, 1.0, &c->st_dev->scale[2], false, false,
+                                             c->stream);
+                       }),
                        "Z16 refine")))
       return st;
     TcArgs ku = tc_args(n, false);

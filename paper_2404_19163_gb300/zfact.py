@@ -30,6 +30,7 @@ EXPORTED = (
     "zfact_default_opts", "zfact_create", "zfact_destroy", "zfact_last_error", "zfact_refine",
     "zfact_refine_batched", "zfact_features", "zfact_mlp_forward", "zfact_mlp_backward",
     "zfact_mlp_adam", "zfact_propose", "zfact_gemm", "zfact_split", "zfact_residual",
+    "zfact_set_profiling", "zfact_kernel_stats",
 )
 
 
@@ -47,10 +48,16 @@ class Opts(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("refine_iters", ctypes.c_int), ("hist_len", ctypes.c_int),
-                ("warn", ctypes.c_int), ("resid_f", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("warn", ctypes.c_int), ("launches", ctypes.c_int), ("resid_f", ctypes.c_double),
+                ("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 _lib = None
@@ -83,6 +90,8 @@ def load(path: Optional[str] = None):
     lib.zfact_gemm.argtypes = [P, I, I64, P, D, P, D, P]
     lib.zfact_split.argtypes = [P, I, P, I64, D, P, P]
     lib.zfact_residual.argtypes = [P, I, P, P, I64, P, ctypes.POINTER(D)]
+    lib.zfact_set_profiling.argtypes = [P, I]
+    lib.zfact_kernel_stats.argtypes = [P, P, I, ctypes.POINTER(I), I]
     for name in EXPORTED:
         if getattr(lib, name).restype is ctypes.c_int or name in ("zfact_default_opts", "zfact_destroy",
                                                                       "zfact_last_error"):
@@ -224,6 +233,18 @@ class Context:
                                            hist_cap, infos, status.ctypes.data)
         self._raise(rc)
         return Z_list, hist, [i.as_dict() for i in infos], status
+
+    # ------------------------------------------------------------ per-kernel timing
+    def set_profiling(self, on: bool = True):
+        self._raise(self.lib.zfact_set_profiling(self.h, int(bool(on))))
+
+    def kernel_stats(self, reset: bool = True):
+        cap = 64
+        arr = (KStat * cap)()
+        n = ctypes.c_int()
+        self._raise(self.lib.zfact_kernel_stats(self.h, arr, cap, ctypes.byref(n), int(bool(reset))))
+        return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms,
+                 "flops": arr[i].flops, "bytes": arr[i].bytes} for i in range(min(n.value, cap))]
 
     # ------------------------------------------------------------ steps
     def gemm(self, A, B, precision: str = "bf16", scale_a: float = 1.0, scale_b: float = 1.0, C=None):

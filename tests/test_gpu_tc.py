@@ -1,0 +1,143 @@
+"""tcgen05 tensor-core products and the mixed-precision recursion against the oracle.
+
+Step-level parity: the GPU product of 16-bit operands (FP32 accumulation in
+tensor memory) is compared element by element with the oracle's FP64 product
+of the same 16-bit-rounded operands.  The difference is FP32 accumulation
+rounding only, bounded by (nseg*K) * 2^-23 * (|A16| |B16|)_ij (any summation
+order, truncating or rounding adder)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_19163_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2404_19163_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+KIND = {"bf16": "bf16", "bf16_split": "bf16", "fp16": "fp16", "fp16_split": "fp16"}
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_split_bit_exact(ctx, prec):
+    import torch
+    g = np.random.default_rng(1)
+    A = g.standard_normal(100003) * 10.0 ** g.uniform(-3, 3, 100003)
+    scale = 2.0 ** -3 if prec == "fp16" else 1.0
+    hi, lo = ctx.split(dev(A), prec, scale)
+    rh, rl = oracle.split16(A, KIND[prec], scale)
+    np16 = np.float16 if prec == "fp16" else None
+    if prec == "fp16":
+        eh = rh.astype(np.float16).view(np.uint16)
+        el = rl.astype(np.float16).view(np.uint16)
+    else:
+        eh = (rh.view(np.uint32) >> 16).astype(np.uint16)
+        el = (rl.view(np.uint32) >> 16).astype(np.uint16)
+    assert np.array_equal(hi.cpu().numpy().view(np.uint16), eh)
+    assert np.array_equal(lo.cpu().numpy().view(np.uint16), el)
+
+
+@pytest.mark.parametrize("n", [128, 64, 129, 256, 300, 520])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "bf16_split", "fp16_split"])
+def test_gemm_parity(ctx, n, prec):
+    g = np.random.default_rng(n)
+    A = g.standard_normal((n, n))
+    B = g.standard_normal((n, n)) * 0.5
+    sa, sb = (2.0 ** 4, 2.0 ** -2) if prec.startswith("fp16") else (1.0, 1.0)
+    C = ctx.gemm(dev(A), dev(B), prec, sa, sb).cpu().numpy()
+    kind = KIND[prec]
+    Ah, Al = oracle.split16(A, kind, sa)
+    Bh, Bl = oracle.split16(B, kind, sb)
+    if prec.endswith("split"):
+        ref = oracle.mm16(Ah, Bh) + oracle.mm16(Ah, Bl) + oracle.mm16(Al, Bh)
+        absp = np.abs(Ah) @ np.abs(Bh) + np.abs(Ah) @ np.abs(Bl) + np.abs(Al) @ np.abs(Bh)
+        nseg = 3
+    else:
+        ref = oracle.mm16(Ah, Bh)
+        absp = np.abs(Ah) @ np.abs(Bh)
+        nseg = 1
+    ref /= sa * sb
+    bound = nseg * n * 2.0 ** -23 * absp / (sa * sb) + 1e-30
+    err = np.abs(C - ref)
+    assert np.all(err <= bound), (prec, n, float(np.max(err / bound)))
+    # the exact FP64 product differs by the operand rounding only
+    full = A @ B
+    u = 2.0 ** -8 if kind == "bf16" else 2.0 ** -11
+    if prec.endswith("split"):
+        u = u * u * 4
+    assert np.max(np.abs(C - full)) <= 4 * u * np.max(np.abs(A) @ np.abs(B)) + 1e-6
+
+
+def test_mixed_bf16_workload1(ctx):
+    S, Q, lam = synth.householder_spd(256, seed=0)
+    n = 256
+    Zo, ho, it = oracle.refine(S, None, m=2, nmax=50)
+    r = ctx.refine(dev(S), None, order=2, precision="bf16", tol=1e-12)
+    Z = r.Z.cpu().numpy()
+    res = np.linalg.norm(np.eye(n) - Z.T @ S @ Z) / math.sqrt(n)
+    assert res <= 1e-12
+    assert r.info["resid_f"] / math.sqrt(n) <= 1e-12
+    # a different but valid factor: Z = S^{-1/2} U, U orthogonal within the BF16 floor
+    relz = np.linalg.norm(Z - Zo) / np.linalg.norm(Zo)
+    assert relz <= 5e-2
+    assert r.info["launches"] > 0
+    assert np.linalg.norm(Z @ Z.T - np.linalg.inv(S)) / np.linalg.norm(np.linalg.inv(S)) <= 1e-11
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16_split"])
+def test_mixed_bulk_history_tracks_fp64(ctx, prec):
+    """Before the BF16 noise floor, Err_n of the mixed bulk follows the FP64 oracle's."""
+    S = synth.cubic_overlap(n_side=8)
+    n = S.shape[0]
+    Zo, ho, it = oracle.refine(S, None, m=2, nmax=50, fixed_iters=2)
+    r = ctx.refine(dev(S), None, order=2, precision=prec, fixed_iters=2, refine_steps=0)
+    u = 2.0 ** -8 if prec == "bf16" else 2.0 ** -16
+    for k in range(3):
+        assert abs(r.hist[k] - ho[k]) <= 8 * u * math.sqrt(n) + 1e-3 * ho[k], (k, r.hist, ho)
+
+
+@pytest.mark.parametrize("m", [3, 4])
+def test_mixed_higher_order(ctx, m):
+    S, Q, lam = synth.householder_spd(200, seed=m)
+    r = ctx.refine(dev(S), None, order=m, precision="bf16", tol=1e-12)
+    assert r.info["resid_f"] / math.sqrt(200) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 7, 100, 129, 383])
+def test_mixed_ragged(ctx, n):
+    S, Q, lam = synth.householder_spd(n, seed=n)
+    r = ctx.refine(dev(S), None, order=2, precision="bf16_split", tol=1e-12)
+    Z = r.Z.cpu().numpy()
+    assert np.linalg.norm(np.eye(n) - Z.T @ S @ Z) / math.sqrt(n) <= 1e-12
+
+
+def test_mixed_workload2_full_size(ctx):
+    """N = 4096 Gaussian overlap, BF16 bulk + FP64-d refinement, to tol 1e-12."""
+    S = synth.cubic_overlap()
+    n = S.shape[0]
+    r = ctx.refine(dev(S), None, order=2, precision="bf16", tol=1e-12)
+    assert r.info["resid_f"] / math.sqrt(n) <= 1e-12
+    # sampled entries of d = I - Z^T S Z, each recomputed by the oracle's definition in FP64
+    Z = r.Z.cpu().numpy()
+    g = np.random.default_rng(3)
+    A_cols = {}
+    for _ in range(16):
+        i, j = g.integers(0, n, 2)
+        sz_j = S @ Z[:, j]
+        d_ij = (1.0 if i == j else 0.0) - float(np.dot(Z[:, i], sz_j))
+        assert abs(d_ij) <= 1e-12 * 10
