@@ -209,6 +209,23 @@ int zfact_split(zfact_ctx* ctx, int precision, const double* A, int64_t n, doubl
 int zfact_residual(zfact_ctx* ctx, int refine_mode, const double* S, const double* Z,
                    int64_t N, double* D, double* err);
 
+/* ---- allocation-free residual -------------------------------------------------------
+ * d = I - Z^T S Z (FP64 CUDA cores) and ||d||_F, without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc where they need the residual, such as an application whose own memory pool
+ * owns the whole device, or a step loop that cannot absorb the device synchronisation an
+ * allocation may cause.  S, Z (N x N FP64, row-major) and the outputs D (N x N) and err
+ * (one double) are DEVICE pointers owned by the caller.  Work is queued on cuda_stream
+ * (a cudaStream_t; NULL = the default stream) and the call returns without waiting.
+ * N must be in 1..1024; larger N returns ZFACT_ERR_ARG and launches nothing.  The product
+ * S Z and the norm partials live in one static device array of 8 MiB + 8 KiB that every
+ * GPU loading this library holds until the process exits; all calls on a device share
+ * it, so calls that overlap on the GPU race.  The first call on each device looks up that
+ * array's device address with the device current; make that first call before any stream
+ * capture.  No context is needed. */
+int zfact_residual_noalloc(const double* S, const double* Z, int64_t N, double* D, double* err,
+                           void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

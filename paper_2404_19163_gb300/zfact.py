@@ -30,7 +30,7 @@ EXPORTED = (
     "zfact_default_opts", "zfact_create", "zfact_destroy", "zfact_last_error", "zfact_refine",
     "zfact_refine_batched", "zfact_features", "zfact_mlp_forward", "zfact_mlp_backward",
     "zfact_mlp_adam", "zfact_propose", "zfact_gemm", "zfact_split", "zfact_residual",
-    "zfact_set_profiling", "zfact_kernel_stats",
+    "zfact_set_profiling", "zfact_kernel_stats", "zfact_residual_noalloc",
 )
 
 
@@ -92,6 +92,7 @@ def load(path: Optional[str] = None):
     lib.zfact_residual.argtypes = [P, I, P, P, I64, P, ctypes.POINTER(D)]
     lib.zfact_set_profiling.argtypes = [P, I]
     lib.zfact_kernel_stats.argtypes = [P, P, I, ctypes.POINTER(I), I]
+    lib.zfact_residual_noalloc.argtypes = [P, P, I64, P, P, P]
     for name in EXPORTED:
         if getattr(lib, name).restype is ctypes.c_int or name in ("zfact_default_opts", "zfact_destroy",
                                                                       "zfact_last_error"):
