@@ -289,7 +289,7 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   if (opts_in) o = *opts_in;
   if (o.nmax < 1) o.nmax = 1;
   if (o.refine_steps < 0) o.refine_steps = (precision == ZFACT_P_FP64) ? 0 : 3;
-  if (o.refine_mode < 0) o.refine_mode = ZFACT_R_NATIVE;
+  if (o.refine_mode < 0) o.refine_mode = ZFACT_R_OZAKI;
   const int n = (int)N;
   const size_t nn = (size_t)n * n, bytes = nn * sizeof(double);
   zfact_info inf;

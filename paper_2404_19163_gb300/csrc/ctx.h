@@ -77,6 +77,11 @@ int f64_residual(zfact_ctx* c, const double* S, const double* Z, double* A, doub
 int f64_poly(zfact_ctx* c, const double* D, double* Q, double* P, double* P2, int n, int m);
 int f64_update(zfact_ctx* c, const double* Z, const double* Q, double* Zn, int n);
 
+// FP64-accurate products by error-free slicing (ozaki.cu)
+int oz_prepare_S(zfact_ctx* c, const double* S, int n);
+int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop);
+int oz_update(zfact_ctx* c, double* Z, const double* Q, int n);
+
 // Mixed-precision driver (mixed.cu): bulk tensor-core iterations, then Algorithm 3's refinement.
 int mixed_refine(zfact_ctx* c, const double* S, double* Za, double* Zb, int n, int order, int precision,
                  const zfact_opts& o, int* iters, int* ridx, zfact_info* inf);

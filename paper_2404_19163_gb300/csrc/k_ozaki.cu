@@ -1,0 +1,220 @@
+// FP64-accurate products on the BF16 tensor cores by error-free slicing
+// (Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012).
+//
+// Every row r of an FP64 operand X is scaled by 2^-e_r (e_r: smallest power of two
+// bounding the row's largest magnitude) and peeled into s integer slices of b bits:
+//     x = 2^e_r * sum_p a_p 2^{-b(p+1)} + remainder,   a_0 in [-2^b, 2^b],
+//     a_p in [-2^{b-1}, 2^{b-1}] for p >= 1  (round to nearest at every step),
+// so every slice value is an integer that BF16 holds exactly.  The product of two
+// sliced operands is  C_ij = 2^{eA_i + eB_j} sum_{t} 2^{-b(t+2)} G_t,ij  with
+// G_t = sum_{p+q=t} A_p B_q^T; the terms p + q >= s are dropped (Ozaki's
+// truncation).  The tensor-core engine forms each G_t over K-chunks short enough
+// that every partial sum is an integer below 2^24, i.e. exact in FP32; the
+// combine kernels below add the groups in FP64.
+#include <math.h>
+
+#include "kernels.h"
+
+namespace zf {
+namespace {
+
+__device__ __forceinline__ int exp_bound(double v) {
+  // smallest-ish e with |v| <= 2^e (frexp: v = f 2^e, f in [0.5, 1))
+  int e;
+  frexp(v, &e);
+  return e;
+}
+
+// Row (COLS = false) or column (COLS = true) exponents of X (n x n, leading dimension ld).
+template <bool COLS>
+__global__ void k_oz_exp(const double* __restrict__ X, int n, int ld, int* __restrict__ e) {
+  __shared__ double red[8][33];
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  double cm = 0.0;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi + r, j = bj + tx;
+    const double v = (i < n && j < n) ? fabs(X[(size_t)i * ld + j]) : 0.0;
+    if (COLS) {
+      cm = fmax(cm, v);
+    } else {
+      double m = v;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (tx == 0 && i < n && m > 0.0) atomicMax(&e[i], exp_bound(m));
+    }
+  }
+  if (COLS) {
+    red[ty][tx] = cm;
+    __syncthreads();
+    if (ty == 0) {
+      double m = red[0][tx];
+      for (int y = 1; y < 8; ++y) m = fmax(m, red[y][tx]);
+      const int j = bj + tx;
+      if (j < n && m > 0.0) atomicMax(&e[j], exp_bound(m));
+    }
+  }
+}
+
+// Slices of X (TRANS = false: operand rows are rows of X) or of X^T (TRANS = true: operand
+// rows are columns of X).  Slice p, operand row r, column k -> out[(p * Rp + r) * ld16 + k].
+template <bool TRANS>
+__global__ void k_oz_slice(const double* __restrict__ X, int n, int ld, const int* __restrict__ e, int s, int b,
+                           uint16_t* __restrict__ out, int ld16, int Rp) {
+  __shared__ double tile[32][33];
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int i = bi + r, j = bj + tx;
+    tile[r][tx] = (i < n && j < n) ? X[(size_t)i * ld + j] : 0.0;
+  }
+  __syncthreads();
+  const double two_b = ldexp(1.0, b);
+  for (int r = ty; r < 32; r += 8) {
+    int row, col;
+    double x;
+    if (TRANS) {
+      row = bj + r;  // operand row = column of X
+      col = bi + tx;
+      x = tile[tx][r];
+    } else {
+      row = bi + r;
+      col = bj + tx;
+      x = tile[r][tx];
+    }
+    if (row >= n || col >= n) continue;
+    const int er = e[row];
+    x = (er > -1000) ? ldexp(x, -er) : 0.0;
+    for (int p = 0; p < s; ++p) {
+      const double t = x * two_b;
+      const double a = rint(t);
+      x = t - a;
+      out[((size_t)p * Rp + row) * ld16 + col] = __bfloat16_as_ushort(__double2bfloat16(a));
+    }
+  }
+}
+
+// Sum of the groups in FP64 with the scales: val = 2^{eA_i + eB_j} 2^{-2b} sum_t 2^{-bt} T_t,
+// T_t = sum_c G[t * nch + c] (Horner from the smallest weight).  mode 0: out = val,
+// mode 1: out += val.  sym: only i <= j formed, written to (i, j) and (j, i).
+__global__ void k_oz_combine(const float* __restrict__ G, size_t gstride, int ld32, int s, int nch, int b,
+                             const int* __restrict__ eA, const int* __restrict__ eB, int n, double* out, int ld64,
+                             int mode, int sym) {
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int i = blockIdx.y * 8 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  if (sym && j < i) return;
+  const size_t off = (size_t)i * ld32 + j;
+  const double wb = ldexp(1.0, -b);
+  double h = 0.0;
+  for (int t = s - 1; t >= 0; --t) {
+    double tt = 0.0;
+    for (int c = 0; c < nch; ++c) tt += (double)G[(size_t)(t * nch + c) * gstride + off];
+    h = h * wb + tt;
+  }
+  const int ea = eA[i], eb = eB[j];
+  const double val = (ea > -1000 && eb > -1000) ? ldexp(h, ea + eb - 2 * b) : 0.0;
+  double* o = out + (size_t)i * ld64 + j;
+  if (mode == 1) {
+    *o += val;
+    if (sym && j > i) out[(size_t)j * ld64 + i] += val;
+  } else {
+    *o = val;
+    if (sym && j > i) out[(size_t)j * ld64 + i] = val;
+  }
+}
+
+// d = I - X (X symmetric, FP64), partials[block] = sum over the block's entries of d^2.
+__global__ void k_resid_from_x(const double* __restrict__ X, double* __restrict__ D, int n, double* partials) {
+  __shared__ double red[256];
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int i = blockIdx.y * 8 + threadIdx.y;
+  double ss = 0.0;
+  if (i < n && j < n) {
+    const double d = (i == j ? 1.0 : 0.0) - X[(size_t)i * n + j];
+    D[(size_t)i * n + j] = d;
+    ss = d * d;
+  }
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  red[tid] = ss;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+}
+
+// out = a * X + b * Y (FP64, n x n contiguous)
+__global__ void k_axpby64(double* out, double a, const double* X, double b, const double* Y, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = a * X[e] + b * Y[e];
+}
+
+__global__ void k_pow2_slot(IterState* st, int amax_slot, int scale_slot) {
+  const double bound = st->amax[amax_slot];
+  float sc = 1.0f;
+  if (bound > 0.0 && isfinite(bound)) {
+    int e;
+    frexp(bound, &e);
+    int p = 14 - e;
+    p = p > 60 ? 60 : (p < -60 ? -60 : p);
+    sc = ldexpf(1.0f, p);
+  }
+  st->scale[scale_slot] = sc;
+}
+
+}  // namespace
+
+cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, cudaStream_t s) {
+  k_pow2_slot<<<1, 1, 0, s>>>(st, amax_slot, scale_slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_exp(const double* X, int n, int ld, bool cols, int* e, cudaStream_t s) {
+  cudaMemsetAsync(e, 0x80, sizeof(int) * (size_t)n, s);  // very negative: all-zero rows stay marked
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  if (cols)
+    k_oz_exp<true><<<grid, block, 0, s>>>(X, n, ld, e);
+  else
+    k_oz_exp<false><<<grid, block, 0, s>>>(X, n, ld, e);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_slice(const double* X, int n, int ld, bool trans, const int* e, int sl, int b, uint16_t* out,
+                            int ld16, int Rp, cudaStream_t s) {
+  for (int p = 0; p < sl; ++p)  // padding rows n..Rp-1 of every slice must read as zero
+    if (Rp > n) cudaMemsetAsync(out + ((size_t)p * Rp + n) * ld16, 0, sizeof(uint16_t) * (size_t)(Rp - n) * ld16, s);
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  if (trans)
+    k_oz_slice<true><<<grid, block, 0, s>>>(X, n, ld, e, sl, b, out, ld16, Rp);
+  else
+    k_oz_slice<false><<<grid, block, 0, s>>>(X, n, ld, e, sl, b, out, ld16, Rp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_combine(const float* G, size_t gstride, int ld32, int sl, int nch, int b, const int* eA,
+                              const int* eB, int n, double* out, int ld64, int mode, bool sym, cudaStream_t s) {
+  dim3 grid((n + 31) / 32, (n + 7) / 8), block(32, 8);
+  k_oz_combine<<<grid, block, 0, s>>>(G, gstride, ld32, sl, nch, b, eA, eB, n, out, ld64, mode, sym ? 1 : 0);
+  return cudaGetLastError();
+}
+
+int resid_from_x_blocks(int n) { return ((n + 31) / 32) * ((n + 7) / 8); }
+
+cudaError_t launch_resid_from_x(const double* X, double* D, int n, double* partials, cudaStream_t s) {
+  dim3 grid((n + 31) / 32, (n + 7) / 8), block(32, 8);
+  k_resid_from_x<<<grid, block, 0, s>>>(X, D, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby64(double* out, double a, const double* X, double b, const double* Y, size_t total,
+                           cudaStream_t s) {
+  const int blocks = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+  k_axpby64<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(out, a, X, b, Y, total);
+  return cudaGetLastError();
+}
+
+}  // namespace zf

@@ -35,12 +35,47 @@ struct Cfg {
   static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 
-__host__ __device__ inline int units_of(int M, int N, int sym, int bn_size) {
+__host__ __device__ inline int tiles_of(int M, int N, int sym, int bn_size) {
   const int tm = (M + BM - 1) / BM, tn = (N + bn_size - 1) / bn_size;
   if (!sym) return tm * tn;
   int total = 0;
   for (int r = 0; r < tm; ++r) total += tn - (r * BM) / bn_size;
   return total;
+}
+
+__host__ __device__ inline int units_of(const TcArgs& a, int bn_size) {
+  const int t = tiles_of(a.M, a.N, a.sym, bn_size);
+  return a.oz_s > 0 ? t * a.oz_s * a.oz_nch : t;
+}
+
+// Work of one unit: `npairs` operand pairs over K-blocks [kb0, kb1).
+struct UnitPlan {
+  int tile, group, npairs, p0, t, kb0, kb1;
+};
+
+__device__ __forceinline__ UnitPlan plan_unit(int u, const TcArgs& a, int kblocks) {
+  UnitPlan pl;
+  if (a.oz_s > 0) {
+    const int ng = a.oz_s * a.oz_nch;
+    pl.tile = u / ng;
+    pl.group = u % ng;
+    pl.t = pl.group / a.oz_nch;
+    const int c = pl.group % a.oz_nch;
+    pl.p0 = pl.t - (a.oz_s - 1) > 0 ? pl.t - (a.oz_s - 1) : 0;
+    const int p1 = pl.t < a.oz_s - 1 ? pl.t : a.oz_s - 1;
+    pl.npairs = p1 - pl.p0 + 1;
+    pl.kb0 = (a.oz_c0 + c) * a.oz_chunk_kb;
+    pl.kb1 = pl.kb0 + a.oz_chunk_kb < kblocks ? pl.kb0 + a.oz_chunk_kb : kblocks;
+  } else {
+    pl.tile = u;
+    pl.group = 0;
+    pl.t = 0;
+    pl.p0 = 0;
+    pl.npairs = a.nseg;
+    pl.kb0 = 0;
+    pl.kb1 = kblocks;
+  }
+  return pl;
 }
 
 __device__ __forceinline__ void decode_unit(int u, const TcArgs& a, int bn_size, int& bm, int& bn) {
@@ -147,7 +182,7 @@ __device__ __forceinline__ void split32(const float (&x)[32], float sc, int bf16
 }
 
 __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, float (&v)[32], double& ss, float& amax,
-                                          float osc, float us) {
+                                          float osc, float us, int group) {
   const int n = a.N;
   if (i >= a.M) return;
   const bool lo = a.split_out != 0;
@@ -231,8 +266,17 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int j = col0 + jj;
-        if (j < n) crow[j] = (double)v[jj] * (double)us;
+        if (j < n && (!a.sym || j >= i)) {
+          const double x = (double)v[jj] * (double)us;
+          crow[j] = x;
+          if (a.sym && j > i) a.f64[(size_t)j * a.ld64 + i] = x;
+        }
       }
+      break;
+    }
+    case kEpiG32: {
+      float* g = a.f32 + (size_t)group * a.g_stride;
+      put32(g, a.ld32, i, col0, n, a.sym != 0, false, v);
       break;
     }
     case kEpiZupd64: {
@@ -280,7 +324,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done_bar + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int units = units_of(a.M, a.N, a.sym, BN);
+  const int units = units_of(a, BN);
   const int kblocks = (a.K + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
@@ -315,10 +359,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       int it = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const UnitPlan pl = plan_unit(u, a, kblocks);
         int bm, bn;
-        decode_unit(u, a, BN, bm, bn);
-        for (int s = 0; s < a.nseg && ok; ++s) {
-          for (int kb = 0; kb < kblocks; ++kb, ++it) {
+        decode_unit(pl.tile, a, BN, bm, bn);
+        for (int pi = 0; pi < pl.npairs && ok; ++pi) {
+          int mi = pi, ya = bm * BM, yb = bn * BN;
+          if (a.oz_s > 0) {
+            const int p = pl.p0 + pi, q = pl.t - p;
+            mi = 0;
+            ya += p * a.oz_ra;
+            yb += q * a.oz_rb;
+          }
+          for (int kb = pl.kb0; kb < pl.kb1; ++kb, ++it) {
             const int st = it % C::STAGES;
             const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
             if (!mbar_wait(&empty[st], ph ^ 1u, a.err_flag, 1)) {
@@ -327,8 +379,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
             }
             uint8_t* sa = smem + st * C::STAGE;
             mbar_arrive_expect_tx(&full[st], C::STAGE);
-            tma_load_2d(sa, &maps.a[s], kb * BK, bm * BM, &full[st]);
-            tma_load_2d(sa + C::A_BYTES, &maps.b[s], kb * BK, bn * BN, &full[st]);
+            tma_load_2d(sa, &maps.a[mi], kb * BK, ya, &full[st]);
+            tma_load_2d(sa + C::A_BYTES, &maps.b[mi], kb * BK, yb, &full[st]);
           }
         }
       }
@@ -345,8 +397,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
         tc_fence_after();
         const uint32_t dtm = tmem_base + (uint32_t)(buf * BN);
         uint32_t acc = 0;
-        for (int s = 0; s < a.nseg && ok; ++s) {
-          for (int kb = 0; kb < kblocks; ++kb, ++it) {
+        const UnitPlan pl = plan_unit(u, a, kblocks);
+        for (int pi = 0; pi < pl.npairs && ok; ++pi) {
+          for (int kb = pl.kb0; kb < pl.kb1; ++kb, ++it) {
             const int st = it % C::STAGES;
             const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
             if (!mbar_wait(&full[st], ph, a.err_flag, 3)) {
@@ -383,8 +436,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
       if (!mbar_wait(&tfull[buf], uph, a.err_flag, 5)) break;
       tc_fence_after();
+      const UnitPlan pl = plan_unit(u, a, kblocks);
       int bm, bn;
-      decode_unit(u, a, BN, bm, bn);
+      decode_unit(pl.tile, a, BN, bm, bn);
       const int i = bm * BM + q * 32 + lane;
       double ss = 0.0;
 #pragma unroll 1
@@ -393,7 +447,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
         const int col0 = bn * BN + c * 32;
         if (a.sym && col0 + 31 < bm * BM) continue;  // chunk entirely below the diagonal block
-        epi_chunk(a, i, col0, v, ss, amax, osc, us);
+        epi_chunk(a, i, col0, v, ss, amax, osc, us, pl.group);
       }
       tc_fence_before();
       __syncwarp();
@@ -453,7 +507,7 @@ int tc_make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, in
   return r == CUDA_SUCCESS ? 0 : (int)r;
 }
 
-int tc_num_units(const TcArgs& a, int bn) { return units_of(a.M, a.N, a.sym, bn); }
+int tc_num_units(const TcArgs& a, int bn) { return units_of(a, bn); }
 
 template <int BN>
 static cudaError_t launch_bn(const TcArgs& a, const TcMaps& maps, int num_sms, cudaStream_t s) {
@@ -464,7 +518,7 @@ static cudaError_t launch_bn(const TcArgs& a, const TcMaps& maps, int num_sms, c
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int units = units_of(a.M, a.N, a.sym, BN);
+  const int units = units_of(a, BN);
   const int grid = units < num_sms ? units : num_sms;
   if (grid <= 0) return cudaSuccess;
   k_tc_gemm<BN><<<grid, NTHREADS, C::SMEM, s>>>(maps, a);
@@ -472,7 +526,7 @@ static cudaError_t launch_bn(const TcArgs& a, const TcMaps& maps, int num_sms, c
 }
 
 cudaError_t launch_tc_gemm(const TcArgs& a, const TcMaps& maps, int bn, int num_sms, cudaStream_t s) {
-  if (a.nseg < 1 || a.nseg > kTcMaxSeg) return cudaErrorInvalidValue;
+  if (a.oz_s <= 0 && (a.nseg < 1 || a.nseg > kTcMaxSeg)) return cudaErrorInvalidValue;
   if (bn == 256) return launch_bn<256>(a, maps, num_sms, s);
   if (bn == 128) return launch_bn<128>(a, maps, num_sms, s);
   return cudaErrorInvalidValue;

@@ -61,4 +61,22 @@ cudaError_t launch_amax_f64(const double* A, int n, IterState* st, int slot, cud
 // bound_0 = amax[1] (d), bound_1 = c1*amax[1] + c2*hist[idx]^2 (Q), bound_2 = amax[2] (Z).
 cudaError_t launch_pow2_scales(IterState* st, int idx, float c1, float c2, cudaStream_t s);
 
+// ---- error-free slicing (k_ozaki.cu)
+// e[r] = exponent bounding row r (cols = false) or column r (cols = true) of X.
+cudaError_t launch_oz_exp(const double* X, int n, int ld, bool cols, int* e, cudaStream_t s);
+// Integer slices (b bits each) of X's rows (trans = false) or columns (trans = true); slice p of
+// operand row r at out[(p * Rp + r) * ld16 + k]; rows n..Rp-1 of every slice are zeroed.
+cudaError_t launch_oz_slice(const double* X, int n, int ld, bool trans, const int* e, int sl, int b, uint16_t* out,
+                            int ld16, int Rp, cudaStream_t s);
+// out (=, or += when mode 1) 2^{eA_i + eB_j} sum_t 2^{-b(t+2)} sum_c G[t * nch + c]; sym: i <= j, mirrored.
+cudaError_t launch_oz_combine(const float* G, size_t gstride, int ld32, int sl, int nch, int b, const int* eA,
+                              const int* eB, int n, double* out, int ld64, int mode, bool sym, cudaStream_t s);
+int resid_from_x_blocks(int n);
+// st->scale[scale_slot] = power of two s with st->amax[amax_slot] * s <= 2^14.
+cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, cudaStream_t s);
+// D = I - X (FP64), per-block sums of D_ij^2 into partials.
+cudaError_t launch_resid_from_x(const double* X, double* D, int n, double* partials, cudaStream_t s);
+cudaError_t launch_axpby64(double* out, double a, const double* X, double b, const double* Y, size_t total,
+                           cudaStream_t s);
+
 }  // namespace zf

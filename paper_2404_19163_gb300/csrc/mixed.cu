@@ -98,6 +98,175 @@ static TcArgs tc_args(int n, bool bf16) {
 
 int pick_bn(int n) { return n <= 128 ? 128 : 256; }
 
+
+// Algorithm 3 with d formed by FP64 CUDA-core products; Q and Z Q by FP16 hi/lo tensor-core
+// products (FP32 accumulation) added to the FP64 master.
+static int refine_native(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o,
+                         int iters, int* ridx_out, zfact_info* inf, float* D32, int ld, int bn) {
+  int st = ZFACT_OK;
+  double coef[8];
+  coef[0] = 1.0;
+  for (int k = 1; k <= order; ++k) coef[k] = coef[k - 1] * (2.0 * k - 1.0) / (2.0 * k);
+  int ridx = 0;
+  double* A64 = (double*)ctx_buf(c, "A64", sizeof(double) * (size_t)n * n, &st);
+  if (!A64) return st;
+  double* D64 = (double*)ctx_buf(c, "D64", sizeof(double) * (size_t)n * n, &st);
+  if (!D64) return st;
+  // FP16 hi/lo operands with power-of-two scales for the refinement products
+  Mat16 Dr, Qr, Zr;
+  if ((st = alloc16(c, "D16r", n, ld, true, &Dr))) return st;
+  if ((st = alloc16(c, "Q16r", n, ld, true, &Qr))) return st;
+  if ((st = alloc16(c, "Z16r", n, ld, true, &Zr))) return st;
+  int idx = iters;
+  for (int r = 0; r <= o.refine_steps; ++r) {
+    ++idx;
+    if ((st = f64_residual(c, S, Z64, A64, D64, n, idx, o.stop_rule, o.tol, 0))) return st;
+    if ((st = ctx_read_state(c))) return st;
+    const double err = c->st_host->hist[idx];
+    inf->resid_f = err;
+    if (c->st_host->nonfinite) break;
+    if (r == o.refine_steps) break;
+    if (o.tol > 0 && err / sqrt((double)n) <= o.tol) break;
+    // Q = c1 d + c2 d^2 with d in FP64 (FP16 hi/lo products for the quadratic term)
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_amax_f64(D64, n, c->st_dev, 1, c->stream); }), "amax d"))) return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_amax_f64(Z64, n, c->st_dev, 2, c->stream); }), "amax Z"))) return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_pow2_scales(c->st_dev, idx, (float)coef[1], (float)coef[2], c->stream); }), "scales")))
+      return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f64_to_f32(D64, n, n, D32, ld, c->stream); }), "d to FP32"))) return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
+                         return launch_cvt16(D64, n, n, Dr.h, Dr.l, ld, 1.0, &c->st_dev->scale[0], false, false,
+                                             c->stream);
+                       }),
+                       "d16")))
+      return st;
+    TcArgs kq = tc_args(n, false);
+    kq.epi = kEpiPoly;
+    kq.sym = 1;
+    kq.split_out = 1;
+    kq.f32_in = D32;
+    kq.ld32 = ld;
+    kq.c1 = (float)coef[1];
+    kq.c2 = (float)coef[2];
+    kq.sa_ptr = &c->st_dev->scale[0];
+    kq.sb_ptr = &c->st_dev->scale[0];
+    kq.out_scale = &c->st_dev->scale[1];
+    kq.o16h = Qr.h;
+    kq.o16l = Qr.l;
+    kq.ld16 = ld;
+    if ((st = tc_product(c, kq, Dr, Dr, ld, bn))) return st;
+    // Z += Z Q with an FP64 master
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
+                         return launch_cvt16(Z64, n, n, Zr.h, Zr.l, ld, 1.0, &c->st_dev->scale[2], false, false,
+                                             c->stream);
+                       }),
+                       "Z16 refine")))
+      return st;
+    TcArgs ku = tc_args(n, false);
+    ku.epi = kEpiZupd64;
+    ku.f64 = Z64;
+    ku.ld64 = n;
+    ku.sa_ptr = &c->st_dev->scale[2];
+    ku.sb_ptr = &c->st_dev->scale[1];
+    if ((st = tc_product(c, ku, Zr, Qr, ld, bn))) return st;
+    ++ridx;
+  }
+  *ridx_out = ridx;
+  return ZFACT_OK;
+}
+
+// Algorithm 3 with d = I - Z^T S Z and Z + Z Q formed to FP64 accuracy by error-free slicing on
+// the BF16 tensor cores; the polynomial's powers d^k (k >= 2) by FP16 hi/lo products.
+static int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o,
+                        int iters, int* ridx_out, zfact_info* inf) {
+  int st = ZFACT_OK;
+  double coef[8];
+  coef[0] = 1.0;
+  for (int k = 1; k <= order; ++k) coef[k] = coef[k - 1] * (2.0 * k - 1.0) / (2.0 * k);
+  const int ld = round_up(n, 64);
+  const int bn = pick_bn(n);
+  const size_t nn = (size_t)n * n;
+  double* D64 = (double*)ctx_buf(c, "D64", sizeof(double) * nn, &st);
+  if (!D64) return st;
+  double* Q64 = (double*)ctx_buf(c, "Q64", sizeof(double) * nn, &st);
+  if (!Q64) return st;
+  double* P64 = (double*)ctx_buf(c, "P64", sizeof(double) * nn, &st);
+  if (!P64) return st;
+  Mat16 Dr, Pr;
+  if ((st = alloc16(c, "D16r", n, ld, true, &Dr))) return st;
+  if (order > 2 && (st = alloc16(c, "P16r", n, ld, true, &Pr))) return st;
+  if ((st = oz_prepare_S(c, S, n))) return st;
+  int ridx = 0, idx = iters;
+  for (int r = 0; r <= o.refine_steps; ++r) {
+    ++idx;
+    if ((st = oz_residual(c, Z64, D64, n, idx, o.stop_rule, o.tol, 0))) return st;
+    if ((st = ctx_read_state(c))) return st;
+    const double err = c->st_host->hist[idx];
+    inf->resid_f = err;
+    if (c->st_host->nonfinite || r == o.refine_steps) break;
+    if (o.tol > 0 && err / sqrt((double)n) <= o.tol) break;
+    // Q = c1 d + sum_{k>=2} c_k d^k: the linear term exact in FP64, the powers by FP16 hi/lo products
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 2, [&] {
+                         cudaError_t e = launch_amax_f64(D64, n, c->st_dev, 1, c->stream);
+                         if (e != cudaSuccess) return e;
+                         return launch_pow2_slot(c->st_dev, 1, 0, c->stream);
+                       }),
+                       "scale d")))
+      return st;
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
+                         return launch_cvt16(D64, n, n, Dr.h, Dr.l, ld, 1.0, &c->st_dev->scale[0], false, false,
+                                             c->stream);
+                       }),
+                       "d16")))
+      return st;
+    const double* Pprev = D64;
+    for (int k = 2; k <= order; ++k) {
+      Mat16 A = Dr;
+      if (k > 2) {
+        // 16-bit hi/lo copy of the previous power with its own scale
+        if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 3, [&] {
+                             cudaError_t e = launch_amax_f64(Pprev, n, c->st_dev, 4, c->stream);
+                             if (e != cudaSuccess) return e;
+                             e = launch_pow2_slot(c->st_dev, 4, 4, c->stream);
+                             if (e != cudaSuccess) return e;
+                             return launch_cvt16(Pprev, n, n, Pr.h, Pr.l, ld, 1.0, &c->st_dev->scale[4], false, false,
+                                                 c->stream);
+                           }),
+                           "power16")))
+          return st;
+        A = Pr;
+      }
+      TcArgs kp = tc_args(n, false);
+      kp.epi = kEpiF64;
+      kp.sym = 1;
+      kp.f64 = P64;
+      kp.ld64 = n;
+      kp.sa_ptr = &c->st_dev->scale[k > 2 ? 4 : 0];
+      kp.sb_ptr = &c->st_dev->scale[0];
+      if ((st = tc_product(c, kp, A, Dr, ld, bn))) return st;
+      const double* first = (k == 2) ? D64 : Q64;
+      const double a1 = (k == 2) ? coef[1] : 1.0;
+      if ((st = ctx_cuda(c, klaunch(c, "elementwise", 3.0 * nn, 24.0 * nn, 1, [&] {
+                           return launch_axpby64(Q64, a1, first, coef[k], P64, nn, c->stream);
+                         }),
+                         "Q")))
+        return st;
+      if (k < order) {
+        // keep the power for the next product (P64 is overwritten by it)
+        double* keep = (double*)ctx_buf(c, "P64keep", sizeof(double) * nn, &st);
+        if (!keep) return st;
+        if ((st = ctx_cuda(c, cudaMemcpyAsync(keep, P64, sizeof(double) * nn, cudaMemcpyDeviceToDevice, c->stream),
+                           "keep power")))
+          return st;
+        Pprev = keep;
+      }
+    }
+    if ((st = oz_update(c, Z64, Q64, n))) return st;
+    ++ridx;
+  }
+  *ridx_out = ridx;
+  return ZFACT_OK;
+}
+
 int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int n, int order, int precision,
                  const zfact_opts& o, int* iters_out, int* ridx_out, zfact_info* inf) {
   const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
@@ -248,68 +417,11 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   // ---- refinement (Algorithm 3): Z = FP64[Z]; X = Z^T S Z in FP64; Z = Z p(X)
   if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f32_to_f64(Zm, n, ld, Za64, n, c->stream); }), "Z to FP64"))) return st;
   double* Z64 = Za64;
-  double* A64 = (double*)ctx_buf(c, "A64", sizeof(double) * (size_t)n * n, &st);
-  if (!A64) return st;
-  double* D64 = (double*)ctx_buf(c, "D64", sizeof(double) * (size_t)n * n, &st);
-  if (!D64) return st;
-  // FP16 hi/lo operands with power-of-two scales for the refinement products
-  Mat16 Dr, Qr, Zr;
-  if ((st = alloc16(c, "D16r", n, ld, true, &Dr))) return st;
-  if ((st = alloc16(c, "Q16r", n, ld, true, &Qr))) return st;
-  if ((st = alloc16(c, "Z16r", n, ld, true, &Zr))) return st;
   int ridx = 0;
-  int idx = iters;
-  for (int r = 0; r <= o.refine_steps; ++r) {
-    ++idx;
-    if ((st = f64_residual(c, S, Z64, A64, D64, n, idx, o.stop_rule, o.tol, 0))) return st;
-    if ((st = ctx_read_state(c))) return st;
-    const double err = c->st_host->hist[idx];
-    inf->resid_f = err;
-    if (c->st_host->nonfinite) break;
-    if (r == o.refine_steps) break;
-    if (o.tol > 0 && err / sqrt((double)n) <= o.tol) break;
-    // Q = c1 d + c2 d^2 with d in FP64 (FP16 hi/lo products for the quadratic term)
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_amax_f64(D64, n, c->st_dev, 1, c->stream); }), "amax d"))) return st;
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_amax_f64(Z64, n, c->st_dev, 2, c->stream); }), "amax Z"))) return st;
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_pow2_scales(c->st_dev, idx, (float)coef[1], (float)coef[2], c->stream); }), "scales")))
-      return st;
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f64_to_f32(D64, n, n, D32, ld, c->stream); }), "d to FP32"))) return st;
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
-                         return launch_cvt16(D64, n, n, Dr.h, Dr.l, ld, 1.0, &c->st_dev->scale[0], false, false,
-                                             c->stream);
-                       }),
-                       "d16")))
-      return st;
-    TcArgs kq = tc_args(n, false);
-    kq.epi = kEpiPoly;
-    kq.sym = 1;
-    kq.split_out = 1;
-    kq.f32_in = D32;
-    kq.ld32 = ld;
-    kq.c1 = (float)coef[1];
-    kq.c2 = (float)coef[2];
-    kq.sa_ptr = &c->st_dev->scale[0];
-    kq.sb_ptr = &c->st_dev->scale[0];
-    kq.out_scale = &c->st_dev->scale[1];
-    kq.o16h = Qr.h;
-    kq.o16l = Qr.l;
-    kq.ld16 = ld;
-    if ((st = tc_product(c, kq, Dr, Dr, ld, bn))) return st;
-    // Z += Z Q with an FP64 master
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
-                         return launch_cvt16(Z64, n, n, Zr.h, Zr.l, ld, 1.0, &c->st_dev->scale[2], false, false,
-                                             c->stream);
-                       }),
-                       "Z16 refine")))
-      return st;
-    TcArgs ku = tc_args(n, false);
-    ku.epi = kEpiZupd64;
-    ku.f64 = Z64;
-    ku.ld64 = n;
-    ku.sa_ptr = &c->st_dev->scale[2];
-    ku.sb_ptr = &c->st_dev->scale[1];
-    if ((st = tc_product(c, ku, Zr, Qr, ld, bn))) return st;
-    ++ridx;
+  if (o.refine_mode == ZFACT_R_OZAKI) {
+    if ((st = refine_ozaki(c, S, Z64, n, order, o, iters, &ridx, inf))) return st;
+  } else {
+    if ((st = refine_native(c, S, Z64, n, order, o, iters, &ridx, inf, D32, ld, bn))) return st;
   }
   *ridx_out = ridx;
   c->mixed_result = Z64;

@@ -1,0 +1,169 @@
+// Host driver of the FP64-accurate products (error-free slicing, k_ozaki.cu) used
+// by the refinement of Algorithm 3: d = I - Z^T S Z and Z <- Z + Z Q formed to
+// FP64 accuracy on the BF16 tensor cores instead of GB300's ~1.1 TFLOP/s FP64 pipe.
+#include <math.h>
+#include <string.h>
+
+#include <string>
+
+#include "ctx.h"
+#include "kernels.h"
+#include "tc_gemm.h"
+
+using namespace zf;
+
+namespace {
+
+constexpr int kOzBits = 6;             // bits per slice
+constexpr int kOzSlicesResid = 9;      // 54 bits: residual products
+constexpr int kOzSlicesUpdate = 8;     // 48 bits: Z Q (its result is a small correction)
+constexpr size_t kOzGBudget = (size_t)6 << 30;  // bytes of FP32 group partials per launch
+
+struct OzOperand {
+  uint16_t* sl = nullptr;
+  int* e = nullptr;
+  int Rp = 0, s = 0;
+};
+
+int ld16_of(int n) { return (n + 63) / 64 * 64; }
+int rp_of(int n) { return (n + 255) / 256 * 256; }
+
+// K-blocks per chunk: every group sum stays an integer below 2^24.  A group t holds
+// pairs with |a_0| <= 2^b, |a_p| <= 2^(b-1) (p >= 1), so its sum over K terms is at
+// most K 2^(2b) (1 + (t-1)/4) for t >= 1 and K 2^(2b) for t = 0.
+int chunk_kb(int s) {
+  const double worst = 1.0 + (s - 2) / 4.0;
+  const double kmax = ldexp(1.0, 24 - 2 * kOzBits) / (worst > 1.0 ? worst : 1.0);
+  int kb = (int)floor(kmax / 64.0);
+  return kb < 1 ? 1 : kb;
+}
+
+int oz_make(zfact_ctx* c, const char* name, const double* X, int n, int ldx, bool trans, int s, OzOperand* op) {
+  int st = ZFACT_OK;
+  const int ld16 = ld16_of(n), Rp = rp_of(n);
+  std::string ns = std::string("oz.") + name + ".sl", ne = std::string("oz.") + name + ".e";
+  op->sl = (uint16_t*)ctx_buf(c, ns.c_str(), sizeof(uint16_t) * (size_t)s * Rp * ld16, &st);
+  if (!op->sl) return st;
+  op->e = (int*)ctx_buf(c, ne.c_str(), sizeof(int) * (size_t)n, &st);
+  if (!op->e) return st;
+  op->Rp = Rp;
+  op->s = s;
+  if ((st = ctx_cuda(c, klaunch(c, "oz_slice", 0, 8.0 * n * n * 2 + 2.0 * s * n * n, 2, [&] {
+                       cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, c->stream);
+                       if (e != cudaSuccess) return e;
+                       return launch_oz_slice(X, n, ldx, trans, op->e, s, kOzBits, op->sl, ld16, Rp, c->stream);
+                     }),
+                     "oz slice")))
+    return st;
+  return ZFACT_OK;
+}
+
+// out (mode 0: =, 1: +=) A B^T to FP64 accuracy, A and B given by their row slices.
+int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool sym, double* out, int ld64,
+               int mode) {
+  int st = ZFACT_OK;
+  const int s = A.s < B.s ? A.s : B.s;
+  const int ld = ld16_of(n);
+  const int ckb = chunk_kb(s);
+  const int kblocks = (n + 63) / 64;
+  const int nch_total = (kblocks + ckb - 1) / ckb;
+  const size_t slot_bytes = sizeof(float) * (size_t)n * ld;
+  int nch_b = (int)(kOzGBudget / (slot_bytes * s));
+  if (nch_b < 1) nch_b = 1;
+  if (nch_b > nch_total) nch_b = nch_total;
+  float* G = (float*)ctx_buf(c, "oz.G", slot_bytes * s * nch_b, &st);
+  if (!G) return st;
+  TcMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  const int bn = 256;
+  int r1 = tc_make_map(&maps.a[0], A.sl, A.s * A.Rp, n, ld, 128, true);
+  int r2 = tc_make_map(&maps.b[0], B.sl, B.s * B.Rp, n, ld, bn, true);
+  if (r1 || r2) return ctx_fail(c, ZFACT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d, %d)", r1, r2);
+  for (int c0 = 0; c0 < nch_total; c0 += nch_b) {
+    const int nch = (nch_total - c0) < nch_b ? (nch_total - c0) : nch_b;
+    TcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.M = a.N = a.K = n;
+    a.nseg = 1;
+    a.sym = sym ? 1 : 0;
+    a.epi = kEpiG32;
+    a.bf16 = 1;
+    a.unscale = 1.0f;
+    a.f32 = G;
+    a.ld32 = ld;
+    a.g_stride = (size_t)n * ld;
+    a.oz_s = s;
+    a.oz_nch = nch;
+    a.oz_chunk_kb = ckb;
+    a.oz_c0 = c0;
+    a.oz_ra = A.Rp;
+    a.oz_rb = B.Rp;
+    a.err_flag = &c->st_dev->error;
+    // algorithmic work: s(s+1)/2 slice pairs over this launch's share of K
+    const int kb_lo = c0 * ckb, kb_hi = (c0 + nch) * ckb < kblocks ? (c0 + nch) * ckb : kblocks;
+    const double kk = (double)(kb_hi - kb_lo) * 64.0 < n ? (double)(kb_hi - kb_lo) * 64.0 : (double)n;
+    const double pairs = s * (s + 1) / 2.0;
+    const double flops = pairs * 2.0 * n * n * kk * (sym ? 0.5 : 1.0);
+    const double bytes = pairs * 2.0 * 2.0 * n * kk + 4.0 * s * nch * (double)n * n;
+    if ((st = ctx_cuda(c, klaunch(c, "tc_gemm.ozaki", flops, bytes, 1,
+                                  [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, c->stream); }),
+                       "tcgen05 ozaki")))
+      return st;
+    const int md = (c0 == 0) ? mode : 1;
+    if ((st = ctx_cuda(c, klaunch(c, "oz_combine", 0, 4.0 * s * nch * n * (double)n + 16.0 * n * n, 1, [&] {
+                         return launch_oz_combine(G, (size_t)n * ld, ld, s, nch, kOzBits, A.e, B.e, n, out, ld64, md,
+                                                  sym, c->stream);
+                       }),
+                       "oz combine")))
+      return st;
+  }
+  return ZFACT_OK;
+}
+
+}  // namespace
+
+int oz_prepare_S(zfact_ctx* c, const double* S, int n) {
+  OzOperand op;
+  return oz_make(c, "S", S, n, n, false, kOzSlicesResid, &op);
+}
+
+// d = I - Z^T S Z to FP64 accuracy; Err -> hist[idx].  oz_prepare_S must have run for this S.
+int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop) {
+  int st = ZFACT_OK;
+  OzOperand Sop, Zt, At;
+  Sop.sl = (uint16_t*)ctx_buf(c, "oz.S.sl", 0, &st);
+  Sop.e = (int*)ctx_buf(c, "oz.S.e", 0, &st);
+  Sop.Rp = rp_of(n);
+  Sop.s = kOzSlicesResid;
+  double* A64 = (double*)ctx_buf(c, "oz.At64", sizeof(double) * (size_t)n * n, &st);
+  if (!A64) return st;
+  double* X64 = (double*)ctx_buf(c, "oz.X64", sizeof(double) * (size_t)n * n, &st);
+  if (!X64) return st;
+  const int nb = resid_from_x_blocks(n);
+  double* partials = (double*)ctx_buf(c, "oz.partials", sizeof(double) * (size_t)nb, &st);
+  if (!partials) return st;
+  // rows of Z^T = columns of Z
+  if ((st = oz_make(c, "Zt", Z, n, n, true, kOzSlicesResid, &Zt))) return st;
+  // A^T = Z^T S  (S symmetric: B operand rows are rows of S)
+  if ((st = oz_product(c, Zt, Sop, n, false, A64, n, 0))) return st;
+  if ((st = oz_make(c, "At", A64, n, n, false, kOzSlicesResid, &At))) return st;
+  // X = Z^T A = Z^T (A^T)^T, symmetric tiles
+  if ((st = oz_product(c, Zt, At, n, true, X64, n, 0))) return st;
+  if ((st = ctx_cuda(c, klaunch(c, "resid_from_x", 2.0 * n * n, 16.0 * n * n, 1,
+                                [&] { return launch_resid_from_x(X64, D, n, partials, c->stream); }),
+                     "resid from X")))
+    return st;
+  return ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
+                    return launch_finish_err(partials, nb, c->st_dev, idx, rule, tol, n, check_stop, c->stream);
+                  }),
+                  "finish err");
+}
+
+// Z <- Z + Z Q to FP64 accuracy (Q symmetric: B operand rows are rows of Q).
+int oz_update(zfact_ctx* c, double* Z, const double* Q, int n) {
+  int st = ZFACT_OK;
+  OzOperand Zr, Qr;
+  if ((st = oz_make(c, "Zr", Z, n, n, false, kOzSlicesUpdate, &Zr))) return st;
+  if ((st = oz_make(c, "Qr", Q, n, n, false, kOzSlicesUpdate, &Qr))) return st;
+  return oz_product(c, Zr, Qr, n, false, Z, n, 1);
+}

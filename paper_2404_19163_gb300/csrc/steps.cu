@@ -84,7 +84,8 @@ extern "C" int zfact_residual(zfact_ctx* c, int mode, const double* S, const dou
   if (!c) return ZFACT_ERR_ARG;
   if (!S || !Z || !err) return ctx_fail(c, ZFACT_ERR_ARG, "null argument");
   if (N < 1 || N > 65536) return ctx_fail(c, ZFACT_ERR_ARG, "N out of range");
-  if (mode != ZFACT_R_NATIVE) return ctx_fail(c, ZFACT_ERR_UNSUPPORTED, "refine mode %d not available", mode);
+  if (mode != ZFACT_R_NATIVE && mode != ZFACT_R_OZAKI)
+    return ctx_fail(c, ZFACT_ERR_ARG, "unknown refine mode %d", mode);
   cudaSetDevice(c->device);
   const int n = (int)N;
   int st = ZFACT_OK;
@@ -96,7 +97,12 @@ extern "C" int zfact_residual(zfact_ctx* c, int mode, const double* S, const dou
     if (!Dw) return st;
   }
   cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
-  if ((st = f64_residual(c, S, Z, A64, Dw, n, 0, 0, 0.0, 0))) return st;
+  if (mode == ZFACT_R_OZAKI) {
+    if ((st = oz_prepare_S(c, S, n))) return st;
+    if ((st = oz_residual(c, Z, Dw, n, 0, 0, 0.0, 0))) return st;
+  } else if ((st = f64_residual(c, S, Z, A64, Dw, n, 0, 0, 0.0, 0))) {
+    return st;
+  }
   if ((st = ctx_read_state(c))) return st;
   *err = c->st_host->hist[0];
   return ZFACT_OK;

@@ -19,6 +19,7 @@ enum TcEpi : int {
   kEpiZupd = 3,     // f32_io += v; o16 = R16(f32_io * out_scale) row-major and t16 transposed
   kEpiF64 = 4,      // f64_out = v (double), row-major
   kEpiZupd64 = 5,   // f64_io += v (double); o16/t16 as kEpiZupd from the updated FP64 value
+  kEpiG32 = 6,      // f32 + slot * g_stride = raw accumulator (Ozaki group partial), upper only when sym
 };
 
 struct TcArgs {
@@ -43,6 +44,11 @@ struct TcArgs {
   double* partials;             // kEpiResid: 4 per tile (one per TMEM lane quadrant)
   unsigned int* amax_bits;      // kEpiResid: max |d| as FP32 bits; kEpiZupd: max |Z|
   int* err_flag;
+  // Ozaki mode (oz_s > 0): operands are integer slices stacked along rows (slice p of A at
+  // rows p * oz_ra, slice q of B at rows q * oz_rb, one tensor map each); a work unit is
+  // (tile, group g) with g = t * oz_nch + c: all slice pairs p + q = t over K-chunk c.
+  int oz_s, oz_nch, oz_chunk_kb, oz_ra, oz_rb, oz_c0;  // oz_c0: first K-chunk of this launch
+  size_t g_stride;              // kEpiG32: elements between group slots
 };
 
 // Tensor maps of the operands: A segment s is a_maps[s] (M x K, K-major = row-major),

@@ -1,0 +1,97 @@
+"""FP64-accurate residual d = I - Z^T S Z by error-free slicing on the BF16 tensor
+cores, against the FP64 oracle.  Row-scaled slicing is accurate normwise: the
+truncation error of an entry is bounded by 2^-54 K times the row maxima of the
+two factors, not by the entry's own |A||B|.  The bound used here,
+1e-13 * max(|Z|^T |S| |Z|), is six orders below what plain FP32 accumulation
+leaves (~1e-7), so it holds only if every slice-pair group is accumulated
+exactly and combined in FP64."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_19163_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2404_19163_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n", [5, 64, 200, 777, 1500, 3001])
+def test_ozaki_residual_matches_oracle(ctx, n):
+    import torch
+    g = np.random.default_rng(n)
+    if n <= 800:
+        S, Q, lam = synth.householder_spd(n, seed=n)
+        Z = (Q * lam ** -0.5) @ Q.T + 1e-3 * g.standard_normal((n, n))
+    else:
+        side = round(n ** (1 / 3)) + 1
+        S = synth.cubic_overlap(n_side=side)[:n, :n].copy()
+        Z = np.eye(n) / math.sqrt(np.abs(S).sum(axis=1).max()) + 1e-3 * g.standard_normal((n, n))
+    d_or, err_or = oracle.residual(S, Z)
+    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    err = ctx.residual(dev(S), dev(Z), "ozaki", D=D)
+    scale = np.max(np.abs(Z).T @ np.abs(S) @ np.abs(Z))
+    diff = np.abs(D.cpu().numpy() - d_or)
+    assert np.max(diff) <= 1e-13 * scale, float(np.max(diff) / scale)
+    assert abs(err - err_or) <= 1e-13 * scale * n
+    # and the FP64 CUDA-core residual agrees too
+    D2 = torch.empty_like(D)
+    err2 = ctx.residual(dev(S), dev(Z), "native", D=D2)
+    assert np.max(np.abs(D2.cpu().numpy() - d_or)) <= 1e-13 * scale
+
+
+def test_ozaki_residual_of_exact_factor_is_tiny(ctx):
+    """Z = S^{-1/2} from the generator's own factors: the FP64-accurate residual sits at the
+    FP64 noise floor, far below anything FP32 accumulation could resolve."""
+    n = 300
+    S, Q, lam = synth.householder_spd(n, seed=77)
+    Z = (Q * lam ** -0.5) @ Q.T
+    err = ctx.residual(dev(S), dev(Z), "ozaki")
+    _, err_or = oracle.residual(S, Z)
+    # FP32 accumulation could not resolve anything below ~1e-6 here; the slicing truncation
+    # (2^-54 normwise, s = 9 slices of 6 bits) leaves a floor within a few times FP64's
+    assert err < 1e-12 and abs(err - err_or) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16_split"])
+def test_mixed_ozaki_refinement(ctx, prec):
+    S, Q, lam = synth.householder_spd(256, seed=0)
+    r = ctx.refine(dev(S), None, order=2, precision=prec, tol=1e-12, refine_mode="ozaki")
+    Z = r.Z.cpu().numpy()
+    _, e = oracle.residual(S, Z)
+    assert e / 16.0 <= 1e-12
+    assert abs(r.info["resid_f"] - e) <= 1e-13
+    assert r.info["refine_iters"] >= 1
+
+
+@pytest.mark.parametrize("m", [3, 5])
+def test_mixed_ozaki_higher_order(ctx, m):
+    S, Q, lam = synth.householder_spd(190, seed=m)
+    r = ctx.refine(dev(S), None, order=m, precision="bf16", tol=1e-12, refine_mode="ozaki")
+    _, e = oracle.residual(S, r.Z.cpu().numpy())
+    assert e / math.sqrt(190) <= 1e-12
+
+
+def test_mixed_ozaki_workload2(ctx):
+    S = synth.cubic_overlap()
+    n = S.shape[0]
+    r = ctx.refine(dev(S), None, order=2, precision="bf16", tol=1e-12, refine_mode="ozaki")
+    assert r.info["resid_f"] / math.sqrt(n) <= 1e-12
+    # the FP64 CUDA-core residual of the returned Z confirms it
+    e = ctx.residual(dev(S), r.Z, "native")
+    assert e / math.sqrt(n) <= 1e-12
+    assert abs(e - r.info["resid_f"]) <= 1e-12 * math.sqrt(n)
