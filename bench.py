@@ -9,7 +9,9 @@ inputs resident on the device.  Prints ONE JSON line (rank 0).
 
 Workload (default): N = 4096 Gaussian overlap, s-type sites exp(-r^2/2) on a
 jittered 16^3 cubic lattice (spacing 2.5, jitter 0.1), cold start Z0 = I/sqrt(g_hi),
-m = 2, BF16 tensor-core bulk with FP32 accumulation, FP64-d refinement.
+m = 2, BF16 tensor-core bulk with FP32 accumulation in the paper's split scheme
+(h)(h)+(h)(l)+(l)(h) with BF16 hi/lo operands, then Algorithm 3's refinement with
+d and Z + Z Q formed to FP64 accuracy by error-free slicing on the tensor cores.
 The single-instance path does not shard: with --gpus N every rank runs its own
 replica (weak scaling) and value = max-over-ranks time / factorizations done.
 """
@@ -293,7 +295,7 @@ def run_ours(args, rank, ws, local):
         out = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16" if prec.startswith("bf16") else prec, "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16" if prec.startswith("bf16") else ("fp16" if prec.startswith("fp16") else prec), "data": "synthetic",
             "config": {"workload": "gaussian_overlap_cubic_N4096_cold_start", "N": n, "order": 2,
                        "precision": prec, "refine": "Algorithm 3, FP64 d (%s)" % (args.refine_mode or "default"),
                        "tol": TOL, "parallelism": "replicas" if ws > 1 else "single",
@@ -322,7 +324,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16")
+    ap.add_argument("--precision", default="bf16_split")
     ap.add_argument("--refine-mode", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

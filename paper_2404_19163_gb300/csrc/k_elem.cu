@@ -167,7 +167,37 @@ __global__ void k_pow2_scales(IterState* st, int idx, float c1, float c2) {
   st->scale[2] = pow2_for(st->amax[2]);
 }
 
+__device__ float pow2_head(double bound, int headroom_log2) {
+  if (!(bound > 0.0) || !isfinite(bound)) return 1.0f;
+  int e;
+  frexp(bound, &e);
+  int p = 14 - headroom_log2 - e;
+  if (p > 60) p = 60;
+  if (p < -60) p = -60;
+  return ldexpf(1.0f, p);
+}
+
+__global__ void k_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next) {
+  if (op == 0) {
+    const double ad = (double)__uint_as_float(st->amaxf[1]);
+    const double err = (idx >= 0 && idx < kHistMax) ? st->hist[idx] : ad;
+    st->scale[0] = pow2_head(ad, 0);
+    st->scale[1] = pow2_head((double)c1 * ad + (double)c2 * err * err, 0);
+  } else if (op == 1) {
+    st->scale[4] = pow2_head(st->amax[0] * st->amax[6], 0);
+  } else if (op == 2) {
+    st->scale[zslot_next] = pow2_head(st->amax[6], 4);
+  } else {
+    st->amax[6] = (double)__uint_as_float(st->amaxf[2]);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next, cudaStream_t s) {
+  k_fp16_scales<<<1, 1, 0, s>>>(st, op, idx, c1, c2, zslot_next);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cvt16(const double* src, int n, int ld_src, uint16_t* hi, uint16_t* lo, int ld16, double scale,
                          const float* scale_ptr, bool transpose, bool bf16, cudaStream_t s) {
@@ -177,9 +207,9 @@ cudaError_t launch_cvt16(const double* src, int n, int ld_src, uint16_t* hi, uin
 }
 
 cudaError_t launch_cvt16_f32(const float* src, int n, int ld_src, uint16_t* hi, uint16_t* lo, int ld16,
-                             bool transpose, bool bf16, cudaStream_t s) {
+                             bool transpose, bool bf16, const float* scale_ptr, cudaStream_t s) {
   dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-  k_cvt16<float><<<grid, block, 0, s>>>(src, n, ld_src, hi, lo, ld16, 1.0, nullptr, transpose, bf16);
+  k_cvt16<float><<<grid, block, 0, s>>>(src, n, ld_src, hi, lo, ld16, 1.0, scale_ptr, transpose, bf16);
   return cudaGetLastError();
 }
 

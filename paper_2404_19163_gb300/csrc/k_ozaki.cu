@@ -58,8 +58,36 @@ __global__ void k_oz_exp(const double* __restrict__ X, int n, int ld, int* __res
   }
 }
 
+// x * 2^(T - e) rounded to the nearest integer (|x| < 2^e, so the result is below 2^T in
+// magnitude), from the bits of x alone: integer operations only, since GB300's FP64 pipe
+// is far slower than its integer pipes.
+__device__ __forceinline__ long long fixed_point(double x, int e, int T) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  if (eb == 0 && m == 0) return 0;
+  int E;
+  if (eb == 0) {
+    E = -1074;
+  } else {
+    m |= 1ull << 52;
+    E = eb - 1075;
+  }
+  const int sh = E - e + T;  // value = m 2^E; want m 2^(E - e + T)
+  long long F;
+  if (sh >= 0)
+    F = (long long)(m << (sh < 11 ? sh : 11));
+  else if (sh > -63)
+    F = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else
+    F = 0;
+  return (bits >> 63) ? -F : F;
+}
+
 // Slices of X (TRANS = false: operand rows are rows of X) or of X^T (TRANS = true: operand
 // rows are columns of X).  Slice p, operand row r, column k -> out[(p * Rp + r) * ld16 + k].
+// The row is held as a fixed-point integer F of T = s*b bits; digit p is F's next b bits
+// rounded to nearest (a_0 in [-2^b, 2^b], later digits in [-2^(b-1), 2^(b-1)]).
 template <bool TRANS>
 __global__ void k_oz_slice(const double* __restrict__ X, int n, int ld, const int* __restrict__ e, int s, int b,
                            uint16_t* __restrict__ out, int ld16, int Rp) {
@@ -71,7 +99,7 @@ __global__ void k_oz_slice(const double* __restrict__ X, int n, int ld, const in
     tile[r][tx] = (i < n && j < n) ? X[(size_t)i * ld + j] : 0.0;
   }
   __syncthreads();
-  const double two_b = ldexp(1.0, b);
+  const int T = s * b;
   for (int r = ty; r < 32; r += 8) {
     int row, col;
     double x;
@@ -86,43 +114,72 @@ __global__ void k_oz_slice(const double* __restrict__ X, int n, int ld, const in
     }
     if (row >= n || col >= n) continue;
     const int er = e[row];
-    x = (er > -1000) ? ldexp(x, -er) : 0.0;
+    long long F = (er > -1000) ? fixed_point(x, er, T) : 0;
     for (int p = 0; p < s; ++p) {
-      const double t = x * two_b;
-      const double a = rint(t);
-      x = t - a;
-      out[((size_t)p * Rp + row) * ld16 + col] = __bfloat16_as_ushort(__double2bfloat16(a));
+      const int sh = T - b * (p + 1);
+      const long long a = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;
+      F -= a << sh;
+      out[((size_t)p * Rp + row) * ld16 + col] = __bfloat16_as_ushort(__float2bfloat16((float)a));
     }
   }
 }
 
-// Sum of the groups in FP64 with the scales: val = 2^{eA_i + eB_j} 2^{-2b} sum_t 2^{-bt} T_t,
-// T_t = sum_c G[t * nch + c] (Horner from the smallest weight).  mode 0: out = val,
-// mode 1: out += val.  sym: only i <= j formed, written to (i, j) and (j, i).
+// Sum of the groups with the scales: val = 2^{eA_i + eB_j} 2^{-2b} sum_t 2^{-bt} T_t,
+// T_t = sum_c G[t * nch + c] (exact integers).  The leading groups t < k0 are summed exactly
+// as a 64-bit integer I = sum_{t<k0} T_t 2^{b(k0-1-t)}; the tail t >= k0, whose weight is
+// below 2^-29 of the leading term, in FP32; one FP64 addition joins them.
+// mode 0: out = val; mode 1: out += val; mode 2 (sym): d = I - val written to (i, j) and
+// (j, i), with the block's sum of d^2 (off-diagonal twice) in partials[block].
 __global__ void k_oz_combine(const float* __restrict__ G, size_t gstride, int ld32, int s, int nch, int b,
                              const int* __restrict__ eA, const int* __restrict__ eB, int n, double* out, int ld64,
-                             int mode, int sym) {
+                             int mode, int sym, double* partials) {
+  __shared__ double red[256];
   const int j = blockIdx.x * 32 + threadIdx.x;
   const int i = blockIdx.y * 8 + threadIdx.y;
-  if (i >= n || j >= n) return;
-  if (sym && j < i) return;
-  const size_t off = (size_t)i * ld32 + j;
-  const double wb = ldexp(1.0, -b);
-  double h = 0.0;
-  for (int t = s - 1; t >= 0; --t) {
-    double tt = 0.0;
-    for (int c = 0; c < nch; ++c) tt += (double)G[(size_t)(t * nch + c) * gstride + off];
-    h = h * wb + tt;
+  double ss = 0.0;
+  if (i < n && j < n && !(sym && j < i)) {
+    const size_t off = (size_t)i * ld32 + j;
+    int k0 = (29 + b - 1) / b;
+    if (k0 > s) k0 = s;
+    long long I = 0;
+    for (int t = 0; t < k0; ++t) {
+      int tt = 0;
+      for (int c = 0; c < nch; ++c) tt += __float2int_rn(G[(size_t)(t * nch + c) * gstride + off]);
+      I = (I << b) + tt;
+    }
+    const float wb = ldexpf(1.0f, -b);
+    float F = 0.0f;
+    for (int t = s - 1; t >= k0; --t) {
+      float tt = 0.0f;
+      for (int c = 0; c < nch; ++c) tt += G[(size_t)(t * nch + c) * gstride + off];
+      F = (F + tt) * wb;
+    }
+    const int ea = eA[i], eb = eB[j];
+    const double val =
+        (ea > -1000 && eb > -1000) ? ldexp((double)I + (double)F, ea + eb - 2 * b - b * (k0 - 1)) : 0.0;
+    double* o = out + (size_t)i * ld64 + j;
+    if (mode == 2) {
+      const double d = (i == j ? 1.0 : 0.0) - val;
+      *o = d;
+      if (j > i) out[(size_t)j * ld64 + i] = d;
+      ss = (i == j ? 1.0 : 2.0) * d * d;
+    } else if (mode == 1) {
+      *o += val;
+      if (sym && j > i) out[(size_t)j * ld64 + i] += val;
+    } else {
+      *o = val;
+      if (sym && j > i) out[(size_t)j * ld64 + i] = val;
+    }
   }
-  const int ea = eA[i], eb = eB[j];
-  const double val = (ea > -1000 && eb > -1000) ? ldexp(h, ea + eb - 2 * b) : 0.0;
-  double* o = out + (size_t)i * ld64 + j;
-  if (mode == 1) {
-    *o += val;
-    if (sym && j > i) out[(size_t)j * ld64 + i] += val;
-  } else {
-    *o = val;
-    if (sym && j > i) out[(size_t)j * ld64 + i] = val;
+  if (mode == 2) {
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    red[tid] = ss;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
   }
 }
 
@@ -196,9 +253,11 @@ cudaError_t launch_oz_slice(const double* X, int n, int ld, bool trans, const in
 }
 
 cudaError_t launch_oz_combine(const float* G, size_t gstride, int ld32, int sl, int nch, int b, const int* eA,
-                              const int* eB, int n, double* out, int ld64, int mode, bool sym, cudaStream_t s) {
+                              const int* eB, int n, double* out, int ld64, int mode, bool sym, double* partials,
+                              cudaStream_t s) {
   dim3 grid((n + 31) / 32, (n + 7) / 8), block(32, 8);
-  k_oz_combine<<<grid, block, 0, s>>>(G, gstride, ld32, sl, nch, b, eA, eB, n, out, ld64, mode, sym ? 1 : 0);
+  k_oz_combine<<<grid, block, 0, s>>>(G, gstride, ld32, sl, nch, b, eA, eB, n, out, ld64, mode, sym ? 1 : 0,
+                                      partials);
   return cudaGetLastError();
 }
 

@@ -46,9 +46,15 @@ cudaError_t launch_finish_err(const double* partials, int nparts, IterState* st,
 // (j, i) when transpose.  scale = *scale_ptr when scale_ptr != nullptr, else `scale`.
 cudaError_t launch_cvt16(const double* src, int n, int ld_src, uint16_t* hi, uint16_t* lo, int ld16, double scale,
                          const float* scale_ptr, bool transpose, bool bf16, cudaStream_t s);
-// The same from an FP32 source.
+// The same from an FP32 source (scale from *scale_ptr when non-null, else 1).
 cudaError_t launch_cvt16_f32(const float* src, int n, int ld_src, uint16_t* hi, uint16_t* lo, int ld16,
-                             bool transpose, bool bf16, cudaStream_t s);
+                             bool transpose, bool bf16, const float* scale_ptr, cudaStream_t s);
+// FP16 operand scales of the bulk iteration (powers of two, bound * scale <= 2^14 / headroom):
+//   op 0 (after the residual): scale[0] (d) from amaxf[1]; scale[1] (Q) from c1*|d|max + c2*hist[idx]^2
+//   op 1 (before K1): scale[4] (A^T) from amax[0] (Gershgorin row sum of S) * amax[6] (|Z|max)
+//   op 2 (before K4): scale[zslot_next] from 16 * amax[6]
+//   op 3 (after K4): amax[6] = amaxf[2] (|Z|max of the new iterate)
+cudaError_t launch_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next, cudaStream_t s);
 // Flat split of n values (zfact_split).
 cudaError_t launch_split_flat(const double* A, int64_t n, double scale, uint16_t* hi, uint16_t* lo, bool bf16,
                               cudaStream_t s);
@@ -68,9 +74,12 @@ cudaError_t launch_oz_exp(const double* X, int n, int ld, bool cols, int* e, cud
 // operand row r at out[(p * Rp + r) * ld16 + k]; rows n..Rp-1 of every slice are zeroed.
 cudaError_t launch_oz_slice(const double* X, int n, int ld, bool trans, const int* e, int sl, int b, uint16_t* out,
                             int ld16, int Rp, cudaStream_t s);
-// out (=, or += when mode 1) 2^{eA_i + eB_j} sum_t 2^{-b(t+2)} sum_c G[t * nch + c]; sym: i <= j, mirrored.
+// val = 2^{eA_i + eB_j} sum_t 2^{-b(t+2)} sum_c G[t * nch + c]; mode 0: out = val, 1: out += val,
+// 2: out = I - val with per-block sums of squares in partials (grid of resid_from_x_blocks(n));
+// sym: i <= j only, mirrored.
 cudaError_t launch_oz_combine(const float* G, size_t gstride, int ld32, int sl, int nch, int b, const int* eA,
-                              const int* eB, int n, double* out, int ld64, int mode, bool sym, cudaStream_t s);
+                              const int* eB, int n, double* out, int ld64, int mode, bool sym, double* partials,
+                              cudaStream_t s);
 int resid_from_x_blocks(int n);
 // st->scale[scale_slot] = power of two s with st->amax[amax_slot] * s <= 2^14.
 cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, cudaStream_t s);

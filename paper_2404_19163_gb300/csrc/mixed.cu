@@ -271,7 +271,11 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
                  const zfact_opts& o, int* iters_out, int* ridx_out, zfact_info* inf) {
   const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
   const bool split = (precision == ZFACT_P_FP16_SPLIT || precision == ZFACT_P_BF16_SPLIT);
-  if (!bf16) return ctx_fail(c, ZFACT_ERR_UNSUPPORTED, "FP16 bulk precisions are not available yet");
+  // FP16 has a 5-bit exponent: every FP16 operand carries a power-of-two scale (exact, so it
+  // changes no significand bit) chosen from a bound on its magnitude; BF16 needs none.
+  const bool scaled = !bf16;
+  IterState* sd = c->st_dev;
+  auto sp = [&](int k) -> const float* { return scaled ? &sd->scale[k] : nullptr; };
   const int ld = round_up(n, 64);
   const int bn = pick_bn(n);
   int st = ZFACT_OK;
@@ -306,13 +310,34 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   double* partials = (double*)ctx_buf(c, "tc_partials", sizeof(double) * 4 * (size_t)max_units, &st);
   if (!partials) return st;
 
+  auto elem = [&](const char* what, int count, auto&& f) -> int {
+    return ctx_cuda(c, klaunch(c, "elementwise", 0, 0, count, f), what);
+  };
+  const int kSlotS = 3, kSlotAt = 4, kSlotD = 0, kSlotQ = 1;
+  int zc_slot = 5, zn_slot = 6;
+
   // ---- set-up: 16-bit S (once), FP32 master Z and its 16-bit copies
-  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_cvt16(S, n, n, S16.h, S16.l, ld, 1.0, nullptr, false, bf16, c->stream); }), "S16")))
+  if (scaled) {
+    if ((st = elem("scales S", 5, [&] {
+           cudaError_t e = launch_gershgorin(S, n, sd, c->stream);  // amax[0] = max row sum of |S|
+           if (e == cudaSuccess) e = launch_amax_f64(S, n, sd, kSlotS, c->stream);
+           if (e == cudaSuccess) e = launch_pow2_slot(sd, kSlotS, kSlotS, c->stream);
+           if (e == cudaSuccess) e = launch_amax_f64(Za64, n, sd, 6, c->stream);
+           if (e == cudaSuccess) e = launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zc_slot, c->stream);
+           return e;
+         })))
+      return st;
+  }
+  if ((st = elem("S16", 1, [&] {
+         return launch_cvt16(S, n, n, S16.h, S16.l, ld, 1.0, sp(kSlotS), false, bf16, c->stream);
+       })))
     return st;
-  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f64_to_f32(Za64, n, n, Zm, ld, c->stream); }), "Z master"))) return st;
-  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_cvt16(Za64, n, n, Za.h, Za.l, ld, 1.0, nullptr, false, bf16, c->stream); }), "Z16")))
-    return st;
-  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_cvt16(Za64, n, n, Zta.h, Zta.l, ld, 1.0, nullptr, true, bf16, c->stream); }), "Zt16")))
+  if ((st = elem("Z master", 1, [&] { return launch_f64_to_f32(Za64, n, n, Zm, ld, c->stream); }))) return st;
+  if ((st = elem("Z16", 2, [&] {
+         cudaError_t e = launch_cvt16(Za64, n, n, Za.h, Za.l, ld, 1.0, sp(zc_slot), false, bf16, c->stream);
+         if (e == cudaSuccess) e = launch_cvt16(Za64, n, n, Zta.h, Zta.l, ld, 1.0, sp(zc_slot), true, bf16, c->stream);
+         return e;
+       })))
     return st;
 
   Mat16* Zc = &Za;
@@ -323,31 +348,52 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   // d = I - Z^T S Z from the current 16-bit Z; Err -> hist[idx]
   auto residual = [&](int idx, int check_stop) -> int {
     int s2;
+    if (scaled && (s2 = elem("scale At", 1, [&] { return launch_fp16_scales(sd, 1, 0, 0.f, 0.f, 0, c->stream); })))
+      return s2;
     TcArgs k1 = tc_args(n, bf16);
     k1.epi = kEpiStore16;
     k1.split_out = split;
     k1.o16h = At.h;
     k1.o16l = At.l;
     k1.ld16 = ld;
+    k1.sa_ptr = sp(zc_slot);
+    k1.sb_ptr = sp(kSlotS);
+    k1.out_scale = sp(kSlotAt);
     if ((s2 = tc_product(c, k1, *Ztc, S16, ld, bn))) return s2;
+    cudaMemsetAsync(&sd->amaxf[1], 0, sizeof(unsigned int), c->stream);
     TcArgs k2 = tc_args(n, bf16);
     k2.epi = kEpiResid;
     k2.sym = 1;
     k2.split_out = split;
     k2.f32 = D32;
     k2.ld32 = ld;
-    k2.o16h = D16.h;
-    k2.o16l = D16.l;
+    if (!scaled) {  // BF16: the 16-bit d is written in the same epilogue
+      k2.o16h = D16.h;
+      k2.o16l = D16.l;
+    }
     k2.ld16 = ld;
     k2.partials = partials;
-    k2.amax_bits = &c->st_dev->amaxf[1];
+    k2.amax_bits = &sd->amaxf[1];
+    k2.sa_ptr = sp(zc_slot);
+    k2.sb_ptr = sp(kSlotAt);
     if ((s2 = tc_product(c, k2, *Ztc, At, ld, bn))) return s2;
     const int np = 4 * tc_num_units(k2, bn);
-    return ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
-                      return launch_finish_err(partials, np, c->st_dev, idx, o.stop_rule, o.tol, n, check_stop,
-                                               c->stream);
-                    }),
-                    "finish err");
+    if ((s2 = ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
+                         return launch_finish_err(partials, np, sd, idx, o.stop_rule, o.tol, n, check_stop, c->stream);
+                       }),
+                       "finish err")))
+      return s2;
+    if (scaled) {
+      // FP16: the scale of d needs its maximum, known only after the residual epilogue
+      if ((s2 = elem("d16", 2, [&] {
+             cudaError_t e = launch_fp16_scales(sd, 0, idx, (float)coef[1], (float)coef[2], 0, c->stream);
+             if (e == cudaSuccess)
+               e = launch_cvt16_f32(D32, n, ld, D16.h, D16.l, ld, false, false, sp(kSlotD), c->stream);
+             return e;
+           })))
+        return s2;
+    }
+    return ZFACT_OK;
   };
 
   // Q = sum_k c_k d^k (products of commuting symmetric matrices: symmetric tiles)
@@ -365,13 +411,17 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
       kp.c1 = (k == 2) ? (float)coef[1] : 1.0f;
       kp.c2 = (float)coef[k];
       kp.ld16 = ld;
+      kp.sa_ptr = sp(kSlotD);  // d^(k-1) carries the scale of d
+      kp.sb_ptr = sp(kSlotD);
       if (k == order) {
         kp.o16h = Q16.h;
         kp.o16l = Q16.l;
+        kp.out_scale = sp(kSlotQ);
       } else {
         kp.f32 = Q32;
         kp.t16h = Pout->h;
         kp.t16l = Pout->l;
+        kp.p_scale = sp(kSlotD);
       }
       if ((s2 = tc_product(c, kp, *Pin, D16, ld, bn))) return s2;
       Pin = Pout;
@@ -390,6 +440,11 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   int iters = 0;
   while (!done && iters < limit && iters + 1 + o.refine_steps + 1 < kHistMax) {
     if ((st = polynomial())) return st;
+    if (scaled && (st = elem("scale Z", 1, [&] {
+                     return launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zn_slot, c->stream);
+                   })))
+      return st;
+    cudaMemsetAsync(&sd->amaxf[2], 0, sizeof(unsigned int), c->stream);
     TcArgs k4 = tc_args(n, bf16);
     k4.epi = kEpiZupd;
     k4.split_out = split;
@@ -400,9 +455,16 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     k4.t16h = Ztn->h;
     k4.t16l = Ztn->l;
     k4.ld16 = ld;
+    k4.sa_ptr = sp(zc_slot);
+    k4.sb_ptr = sp(kSlotQ);
+    k4.out_scale = sp(zn_slot);
+    k4.amax_bits = &sd->amaxf[2];
     if ((st = tc_product(c, k4, *Zc, Q16, ld, bn))) return st;
+    if (scaled && (st = elem("amax Z", 1, [&] { return launch_fp16_scales(sd, 3, 0, 0.f, 0.f, 0, c->stream); })))
+      return st;
     std::swap(Zc, Zn);
     std::swap(Ztc, Ztn);
+    std::swap(zc_slot, zn_slot);
     ++iters;
     if ((st = residual(iters, o.fixed_iters <= 0 ? 1 : 0))) return st;
     if ((st = ctx_read_state(c))) return st;

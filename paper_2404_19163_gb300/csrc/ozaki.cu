@@ -60,7 +60,7 @@ int oz_make(zfact_ctx* c, const char* name, const double* X, int n, int ldx, boo
 
 // out (mode 0: =, 1: +=) A B^T to FP64 accuracy, A and B given by their row slices.
 int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool sym, double* out, int ld64,
-               int mode) {
+               int mode, double* partials = nullptr, bool* fused_resid = nullptr) {
   int st = ZFACT_OK;
   const int s = A.s < B.s ? A.s : B.s;
   const int ld = ld16_of(n);
@@ -109,10 +109,16 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
                                   [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, c->stream); }),
                        "tcgen05 ozaki")))
       return st;
-    const int md = (c0 == 0) ? mode : 1;
+    int md = (c0 == 0) ? mode : 1;
+    // a symmetric product that fits one launch goes straight to d = I - X (fused residual)
+    const bool fuse = partials && fused_resid && sym && c0 == 0 && nch == nch_total;
+    if (fuse) {
+      md = 2;
+      *fused_resid = true;
+    }
     if ((st = ctx_cuda(c, klaunch(c, "oz_combine", 0, 4.0 * s * nch * n * (double)n + 16.0 * n * n, 1, [&] {
                          return launch_oz_combine(G, (size_t)n * ld, ld, s, nch, kOzBits, A.e, B.e, n, out, ld64, md,
-                                                  sym, c->stream);
+                                                  sym, partials, c->stream);
                        }),
                        "oz combine")))
       return st;
@@ -147,12 +153,20 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   // A^T = Z^T S  (S symmetric: B operand rows are rows of S)
   if ((st = oz_product(c, Zt, Sop, n, false, A64, n, 0))) return st;
   if ((st = oz_make(c, "At", A64, n, n, false, kOzSlicesResid, &At))) return st;
-  // X = Z^T A = Z^T (A^T)^T, symmetric tiles
-  if ((st = oz_product(c, Zt, At, n, true, X64, n, 0))) return st;
-  if ((st = ctx_cuda(c, klaunch(c, "resid_from_x", 2.0 * n * n, 16.0 * n * n, 1,
-                                [&] { return launch_resid_from_x(X64, D, n, partials, c->stream); }),
-                     "resid from X")))
-    return st;
+  // X = Z^T A = Z^T (A^T)^T, symmetric tiles; d = I - X fused into the combine when possible
+  bool fused = false;
+  double* Xout = X64;
+  if ((st = oz_product(c, Zt, At, n, true, D, n, 0, partials, &fused))) return st;
+  if (!fused) {
+    // several K-chunk batches: the combine accumulated X into D; form d = I - X from it
+    if ((st = ctx_cuda(c, cudaMemcpyAsync(Xout, D, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, c->stream),
+                       "X copy")))
+      return st;
+    if ((st = ctx_cuda(c, klaunch(c, "resid_from_x", 2.0 * n * n, 16.0 * n * n, 1,
+                                  [&] { return launch_resid_from_x(Xout, D, n, partials, c->stream); }),
+                       "resid from X")))
+      return st;
+  }
   return ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
                     return launch_finish_err(partials, nb, c->st_dev, idx, rule, tol, n, check_stop, c->stream);
                   }),

@@ -99,14 +99,14 @@ def test_mixed_bf16_workload1(ctx):
     assert np.linalg.norm(Z @ Z.T - np.linalg.inv(S)) / np.linalg.norm(np.linalg.inv(S)) <= 1e-11
 
 
-@pytest.mark.parametrize("prec", ["bf16", "bf16_split"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16_split", "fp16", "fp16_split"])
 def test_mixed_bulk_history_tracks_fp64(ctx, prec):
     """Before the BF16 noise floor, Err_n of the mixed bulk follows the FP64 oracle's."""
     S = synth.cubic_overlap(n_side=8)
     n = S.shape[0]
     Zo, ho, it = oracle.refine(S, None, m=2, nmax=50, fixed_iters=2)
     r = ctx.refine(dev(S), None, order=2, precision=prec, fixed_iters=2, refine_steps=0)
-    u = 2.0 ** -8 if prec == "bf16" else 2.0 ** -16
+    u = {"bf16": 2.0 ** -8, "bf16_split": 2.0 ** -16, "fp16": 2.0 ** -11, "fp16_split": 2.0 ** -20}[prec]
     for k in range(3):
         assert abs(r.hist[k] - ho[k]) <= 8 * u * math.sqrt(n) + 1e-3 * ho[k], (k, r.hist, ho)
 
@@ -118,10 +118,11 @@ def test_mixed_higher_order(ctx, m):
     assert r.info["resid_f"] / math.sqrt(200) <= 1e-12
 
 
-@pytest.mark.parametrize("n", [1, 7, 100, 129, 383])
-def test_mixed_ragged(ctx, n):
+@pytest.mark.parametrize("n,prec", [(1, "bf16_split"), (7, "fp16_split"), (100, "bf16_split"), (129, "fp16"),
+                                    (383, "fp16_split")])
+def test_mixed_ragged(ctx, n, prec):
     S, Q, lam = synth.householder_spd(n, seed=n)
-    r = ctx.refine(dev(S), None, order=2, precision="bf16_split", tol=1e-12)
+    r = ctx.refine(dev(S), None, order=2, precision=prec, tol=1e-12)
     Z = r.Z.cpu().numpy()
     assert np.linalg.norm(np.eye(n) - Z.T @ S @ Z) / math.sqrt(n) <= 1e-12
 
@@ -141,3 +142,26 @@ def test_mixed_workload2_full_size(ctx):
         sz_j = S @ Z[:, j]
         d_ij = (1.0 if i == j else 0.0) - float(np.dot(Z[:, i], sz_j))
         assert abs(d_ij) <= 1e-12 * 10
+
+
+@pytest.mark.parametrize("prec", ["fp16", "fp16_split"])
+def test_mixed_fp16_scaled_operands(ctx, prec):
+    """FP16 operands carry power-of-two scales: a badly scaled S (entries ~1e-3, so FP16
+    without scaling would lose the lo parts to subnormals) still converges to tol."""
+    S, Q, lam = synth.householder_spd(160, seed=21)
+    S = S * 1e-3
+    r = ctx.refine(dev(S), None, order=2, precision=prec, tol=1e-12)
+    Z = r.Z.cpu().numpy()
+    _, e = oracle.residual(S, Z)
+    assert e / math.sqrt(160) <= 1e-12
+    assert r.info["iters"] >= 1
+
+
+def test_fp16_split_bulk_floor_below_bf16(ctx):
+    """The split scheme's bulk floor (Sec. 3.2) sits far below plain BF16's."""
+    S = synth.cubic_overlap(n_side=10)
+    r1 = ctx.refine(dev(S), None, order=2, precision="bf16", refine_steps=0)
+    r2 = ctx.refine(dev(S), None, order=2, precision="fp16_split", refine_steps=0)
+    b1 = min(r1.hist[:r1.info["iters"] + 1])
+    b2 = min(r2.hist[:r2.info["iters"] + 1])
+    assert b2 < 1e-2 * b1, (r1.hist, r2.hist)
