@@ -342,6 +342,67 @@ def run_case_residual(args):
     print(json.dumps({"case": "residual_ozaki", "N": n, "ms": round(ms, 3), "err": err}), flush=True)
 
 
+def run_batched(args):
+    """Workload 4: 128 cluster overlaps, N_i ~ U[256, 3072], frames of a trajectory (sites
+    displaced by N(0, 0.02^2) per frame); frame 0 is a cold start (untimed), frames 1..F are
+    warm-started from the previous frame's Z and timed, one zfact_refine_batched call each."""
+    import numpy as np
+    import torch
+    from paper_2404_19163_gb300 import Context, synth, build as zbuild
+    zbuild.build()
+    count = args.batch_count
+    sizes, frame = synth.trajectory(count=count)
+    frames = max(2, args.steps + 1)
+    stream = torch.cuda.Stream()
+    ctx = Context(0, stream=stream)
+    prec = args.precision
+
+    def mats(f):
+        return [synth.gaussian_overlap_torch(p) for p in frame.positions(f)]
+
+    S0 = mats(0)
+    Zp, h, infos, st = ctx.refine_batched(S0, None, precision=prec)
+    cold_iters = [i["iters"] for i in infos]
+    del S0
+    times, iters, resid, launches = [], [], [], 0
+    ctx.set_profiling(True)
+    ctx.kernel_stats(reset=True)
+    with ClockSampler(0) as clk:
+        for f in range(1, frames):
+            Sf = mats(f)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Zf, h, infos, st = ctx.refine_batched(Sf, Zp, precision=prec)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            iters.append([i["iters"] for i in infos])
+            resid.append(max(i["resid_f"] / math.sqrt(n) for i, n in zip(infos, sizes)))
+            launches += infos[0]["launches"]
+            Zp = Zf
+    stats = ctx.kernel_stats(reset=True)
+    ctx.close()
+    tc = [k for k in stats if k["name"].startswith("tc_gemm.b_")]
+    tc_ms = sum(k["ms"] for k in tc)
+    tc_fl = sum(k["flops"] for k in tc)
+    sum_n3 = float(np.sum(np.asarray(sizes, dtype=np.float64) ** 3))
+    print(json.dumps({
+        "workload": "batched_trajectory_128_clusters_N256-3072_warm_frames",
+        "metric": "ms per frame (all 128 factorizations, bulk + FP64-accurate final residual)",
+        "value": round(statistics.mean(times), 3), "unit": "ms", "frames_timed": len(times),
+        "precision": prec, "sum_N": int(np.sum(sizes)), "sum_N3": sum_n3,
+        "cold_iters_mean": float(np.mean(cold_iters)),
+        "warm_iters_mean": float(np.mean(iters)), "warm_iters_max": int(np.max(iters)),
+        "max_resid_over_sqrtN": max(resid), "gpu_launches": launches,
+        "grouped_tc_tflops": round(tc_fl / (tc_ms * 1e-3) / 1e12, 1) if tc_ms else None,
+        "clocks": clk.summary(),
+        "kernels": sorted([{k: (round(v, 3) if isinstance(v, float) else v) for k, v in x.items()}
+                           for x in stats], key=lambda x: -x["ms"])[:10],
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,9 +413,14 @@ def main():
     ap.add_argument("--refine-mode", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, choices=[None, "residual"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--batch-count", type=int, default=128)
     args = ap.parse_args()
     if args.case == "residual":
         run_case_residual(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
         return
     args.warmup = max(args.warmup, 1)
     if args.impl == "reference":

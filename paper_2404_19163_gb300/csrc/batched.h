@@ -1,0 +1,37 @@
+// Batched (grouped) mode: device tables describing the stacked instances.
+#pragma once
+#include "common.cuh"
+
+namespace zf {
+
+struct BatchTables {
+  const int* n;        // size of instance i
+  const int* row0;     // first row of instance i in every packed buffer
+  const int* part0;    // first norm partial of instance i
+  const int* nparts;   // norm partials of instance i (4 per symmetric tile)
+  const double* const* S;   // caller's FP64 S_i (device)
+  const double* const* Z0;  // caller's FP64 Z0_i (device) or null: Gershgorin-scaled identity
+  double* const* Z;         // caller's FP64 output Z_i (device)
+};
+
+struct BatchState {
+  double* hist;     // count x cap: Err history per instance
+  int cap;
+  double* prev_err;
+  int* iters;
+  int* done;        // instance stopped (Algorithm 2 / 1, nmax, or non-finite)
+  int* nonfinite;
+  int* hist_len;
+  int* live;        // instances not done
+};
+
+cudaError_t launch_b_gersh(const BatchTables& t, int count, int max_n, unsigned long long* gmax_bits,
+                           cudaStream_t s);
+cudaError_t launch_b_pack(const BatchTables& t, int count, int max_n, int mode, const unsigned long long* gmax_bits,
+                          int ld, bool bf16, uint16_t* h16, uint16_t* l16, uint16_t* th16, uint16_t* tl16, float* m32,
+                          cudaStream_t s);
+cudaError_t launch_b_unpack(const BatchTables& t, int count, int max_n, const float* m32, int ld, cudaStream_t s);
+cudaError_t launch_b_finish(const double* partials, const BatchTables& t, const BatchState& bs, int count,
+                            int initial, int rule, double tol, int check_stop, int limit, cudaStream_t s);
+
+}  // namespace zf

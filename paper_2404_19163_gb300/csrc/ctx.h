@@ -45,6 +45,9 @@ struct zfact_ctx {
   std::vector<KStat> kstats;
   std::vector<PendingEv> pending;
   std::vector<cudaEvent_t> ev_pool;
+  // batched mode
+  std::map<std::string, int> batch_bn;  // autotuned tile width per set of sizes
+  std::string batch_sig;                // layout of the packed buffers (zeroed on change)
 };
 
 int kstat_id(zfact_ctx* c, const char* name);

@@ -44,17 +44,41 @@ __host__ __device__ inline int tiles_of(int M, int N, int sym, int bn_size) {
 }
 
 __host__ __device__ inline int units_of(const TcArgs& a, int bn_size) {
+  if (a.ninst > 0) return a.M;  // grouped: total units passed in M by the host
   const int t = tiles_of(a.M, a.N, a.sym, bn_size);
   return a.oz_s > 0 ? t * a.oz_s * a.oz_nch : t;
 }
 
-// Work of one unit: `npairs` operand pairs over K-blocks [kb0, kb1).
+// Work of one unit: `npairs` operand pairs over K-blocks [kb0, kb1) of the output tile `tile`
+// of a problem of size n whose rows start at row0 (grouped mode) or 0.
 struct UnitPlan {
   int tile, group, npairs, p0, t, kb0, kb1;
+  int inst, n, row0, skip;
 };
 
-__device__ __forceinline__ UnitPlan plan_unit(int u, const TcArgs& a, int kblocks) {
+__device__ __forceinline__ UnitPlan plan_unit(int u, const TcArgs& a, int kblocks_all) {
   UnitPlan pl;
+  pl.inst = 0;
+  pl.row0 = 0;
+  pl.n = a.N;
+  pl.skip = 0;
+  int kblocks = kblocks_all;
+  if (a.ninst > 0) {
+    int lo = 0, hi = a.ninst - 1;  // slot j with g_prefix[j] <= u < g_prefix[j+1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.g_prefix[mid] <= u)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    pl.inst = a.g_inst[lo];
+    pl.n = a.g_n[pl.inst];
+    pl.row0 = a.g_row0[pl.inst];
+    pl.skip = (a.g_done && a.g_done[pl.inst]) ? 1 : 0;
+    u -= a.g_prefix[lo];
+    kblocks = (pl.n + BK - 1) / BK;
+  }
   if (a.oz_s > 0) {
     const int ng = a.oz_s * a.oz_nch;
     pl.tile = u / ng;
@@ -78,8 +102,9 @@ __device__ __forceinline__ UnitPlan plan_unit(int u, const TcArgs& a, int kblock
   return pl;
 }
 
-__device__ __forceinline__ void decode_unit(int u, const TcArgs& a, int bn_size, int& bm, int& bn) {
-  const int tm = (a.M + BM - 1) / BM, tn = (a.N + bn_size - 1) / bn_size;
+__device__ __forceinline__ void decode_unit(int u, const TcArgs& a, int n_inst, int bn_size, int& bm, int& bn) {
+  const int M = a.ninst > 0 ? n_inst : a.M, N = a.ninst > 0 ? n_inst : a.N;
+  const int tm = (M + BM - 1) / BM, tn = (N + bn_size - 1) / bn_size;
   if (!a.sym) {
     bm = u % tm;
     bn = u / tm;
@@ -182,9 +207,17 @@ __device__ __forceinline__ void split32(const float (&x)[32], float sc, int bf16
 }
 
 __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, float (&v)[32], double& ss, float& amax,
-                                          float osc, float us, int group) {
-  const int n = a.N;
-  if (i >= a.M) return;
+                                          float osc, float us, int group, int n, int row0) {
+  // grouped problems are stacked along rows: shift every output/input base to the instance
+  const size_t r16 = (size_t)row0 * a.ld16, r32 = (size_t)row0 * a.ld32, r64 = (size_t)row0 * a.ld64;
+  uint16_t* o16h = a.o16h ? a.o16h + r16 : nullptr;
+  uint16_t* o16l = a.o16l ? a.o16l + r16 : nullptr;
+  uint16_t* t16h = a.t16h ? a.t16h + r16 : nullptr;
+  uint16_t* t16l = a.t16l ? a.t16l + r16 : nullptr;
+  float* f32 = a.f32 ? a.f32 + r32 : nullptr;
+  const float* f32_in = a.f32_in ? a.f32_in + r32 : nullptr;
+  double* f64 = a.f64 ? a.f64 + r64 : nullptr;
+  if (i >= (a.ninst > 0 ? n : a.M)) return;
   const bool lo = a.split_out != 0;
   uint16_t h[32], l[32];
   switch (a.epi) {
@@ -192,8 +225,8 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) v[jj] *= us;
       split32(v, osc, a.bf16, lo, h, l);
-      put16(a.o16h, a.ld16, i, col0, n, false, false, h);
-      if (lo) put16(a.o16l, a.ld16, i, col0, n, false, false, l);
+      put16(o16h, a.ld16, i, col0, n, false, false, h);
+      if (lo) put16(o16l, a.ld16, i, col0, n, false, false, l);
       break;
     }
     case kEpiResid: {
@@ -208,17 +241,17 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
           amax = fmaxf(amax, fabsf(d));
         }
       }
-      put32(a.f32, a.ld32, i, col0, n, true, true, v);
+      put32(f32, a.ld32, i, col0, n, true, true, v);
       split32(v, osc, a.bf16, lo, h, l);
-      put16(a.o16h, a.ld16, i, col0, n, true, true, h);
-      if (lo) put16(a.o16l, a.ld16, i, col0, n, true, true, l);
+      put16(o16h, a.ld16, i, col0, n, true, true, h);
+      if (lo) put16(o16l, a.ld16, i, col0, n, true, true, l);
       break;
     }
     case kEpiPoly: {
       // r = c1 * f32_in + c2 * v: the running sum of c_k d^k.  Outputs: the running sum in
       // FP32 (f32), its 16-bit copy (o16, the final Q), and the raw power v (t16, P_k for
       // the next product of the chain), all at (i, j) and (j, i).
-      const float* drow = a.f32_in + (size_t)i * a.ld32;
+      const float* drow = f32_in + (size_t)i * a.ld32;
       float r[32];
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
@@ -227,21 +260,21 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
         v[jj] *= us;
         r[jj] = a.c1 * d + a.c2 * v[jj];
       }
-      if (a.f32) put32(a.f32, a.ld32, i, col0, n, true, true, r);
-      if (a.o16h) {
+      if (f32) put32(f32, a.ld32, i, col0, n, true, true, r);
+      if (o16h) {
         split32(r, osc, a.bf16, lo, h, l);
-        put16(a.o16h, a.ld16, i, col0, n, true, true, h);
-        if (lo) put16(a.o16l, a.ld16, i, col0, n, true, true, l);
+        put16(o16h, a.ld16, i, col0, n, true, true, h);
+        if (lo) put16(o16l, a.ld16, i, col0, n, true, true, l);
       }
-      if (a.t16h) {
+      if (t16h) {
         split32(v, a.p_scale ? *a.p_scale : 1.0f, a.bf16, lo, h, l);
-        put16(a.t16h, a.ld16, i, col0, n, true, true, h);
-        if (lo) put16(a.t16l, a.ld16, i, col0, n, true, true, l);
+        put16(t16h, a.ld16, i, col0, n, true, true, h);
+        if (lo) put16(t16l, a.ld16, i, col0, n, true, true, l);
       }
       break;
     }
     case kEpiZupd: {
-      float* zrow = a.f32 + (size_t)i * a.ld32;
+      float* zrow = f32 + (size_t)i * a.ld32;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int j = col0 + jj;
@@ -255,32 +288,32 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
         }
       }
       split32(v, osc, a.bf16, lo, h, l);
-      put16(a.o16h, a.ld16, i, col0, n, false, false, h);
-      if (lo) put16(a.o16l, a.ld16, i, col0, n, false, false, l);
-      put16_t(a.t16h, a.ld16, i, col0, n, h);
-      if (lo) put16_t(a.t16l, a.ld16, i, col0, n, l);
+      put16(o16h, a.ld16, i, col0, n, false, false, h);
+      if (lo) put16(o16l, a.ld16, i, col0, n, false, false, l);
+      put16_t(t16h, a.ld16, i, col0, n, h);
+      if (lo) put16_t(t16l, a.ld16, i, col0, n, l);
       break;
     }
     case kEpiF64: {
-      double* crow = a.f64 + (size_t)i * a.ld64;
+      double* crow = f64 + (size_t)i * a.ld64;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int j = col0 + jj;
         if (j < n && (!a.sym || j >= i)) {
           const double x = (double)v[jj] * (double)us;
           crow[j] = x;
-          if (a.sym && j > i) a.f64[(size_t)j * a.ld64 + i] = x;
+          if (a.sym && j > i) f64[(size_t)j * a.ld64 + i] = x;
         }
       }
       break;
     }
     case kEpiG32: {
-      float* g = a.f32 + (size_t)group * a.g_stride;
+      float* g = f32 + (size_t)group * a.g_stride;
       put32(g, a.ld32, i, col0, n, a.sym != 0, false, v);
       break;
     }
     case kEpiZupd64: {
-      double* zrow = a.f64 + (size_t)i * a.ld64;
+      double* zrow = f64 + (size_t)i * a.ld64;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int j = col0 + jj;
@@ -293,12 +326,12 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
           v[jj] = 0.0f;
         }
       }
-      if (a.o16h) {
+      if (o16h) {
         split32(v, osc, a.bf16, lo, h, l);
-        put16(a.o16h, a.ld16, i, col0, n, false, false, h);
-        if (lo) put16(a.o16l, a.ld16, i, col0, n, false, false, l);
-        put16_t(a.t16h, a.ld16, i, col0, n, h);
-        if (lo) put16_t(a.t16l, a.ld16, i, col0, n, l);
+        put16(o16h, a.ld16, i, col0, n, false, false, h);
+        if (lo) put16(o16l, a.ld16, i, col0, n, false, false, l);
+        put16_t(t16h, a.ld16, i, col0, n, h);
+        if (lo) put16_t(t16l, a.ld16, i, col0, n, l);
       }
       break;
     }
@@ -360,10 +393,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
         const UnitPlan pl = plan_unit(u, a, kblocks);
+        if (pl.skip) continue;
         int bm, bn;
-        decode_unit(pl.tile, a, BN, bm, bn);
+        decode_unit(pl.tile, a, pl.n, BN, bm, bn);
         for (int pi = 0; pi < pl.npairs && ok; ++pi) {
-          int mi = pi, ya = bm * BM, yb = bn * BN;
+          int mi = pi, ya = pl.row0 + bm * BM, yb = pl.row0 + bn * BN;
           if (a.oz_s > 0) {
             const int p = pl.p0 + pi, q = pl.t - p;
             mi = 0;
@@ -390,14 +424,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       const uint32_t idesc = idesc_f16(BM, BN, a.bf16 != 0);
       int it = 0, ui = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const UnitPlan pl = plan_unit(u, a, kblocks);
+        if (pl.skip) continue;
         const int buf = ui & 1;
         const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
+        ++ui;
         if (!mbar_wait(&tempty[buf], uph ^ 1u, a.err_flag, 2)) break;
         tc_fence_after();
         const uint32_t dtm = tmem_base + (uint32_t)(buf * BN);
         uint32_t acc = 0;
-        const UnitPlan pl = plan_unit(u, a, kblocks);
         for (int pi = 0; pi < pl.npairs && ok; ++pi) {
           for (int kb = pl.kb0; kb < pl.kb1; ++kb, ++it) {
             const int st = it % C::STAGES;
@@ -431,14 +467,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
     if (a.sa_ptr) us /= *a.sa_ptr;
     if (a.sb_ptr) us /= *a.sb_ptr;
     float amax = 0.0f;
-    for (int u = blockIdx.x; u < units; u += gridDim.x, ++ui) {
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+      const UnitPlan pl = plan_unit(u, a, kblocks);
+      if (pl.skip) continue;
       const int buf = ui & 1;
       const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
+      ++ui;
       if (!mbar_wait(&tfull[buf], uph, a.err_flag, 5)) break;
       tc_fence_after();
-      const UnitPlan pl = plan_unit(u, a, kblocks);
       int bm, bn;
-      decode_unit(pl.tile, a, BN, bm, bn);
+      decode_unit(pl.tile, a, pl.n, BN, bm, bn);
       const int i = bm * BM + q * 32 + lane;
       double ss = 0.0;
 #pragma unroll 1
@@ -447,7 +485,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
         const int col0 = bn * BN + c * 32;
         if (a.sym && col0 + 31 < bm * BM) continue;  // chunk entirely below the diagonal block
-        epi_chunk(a, i, col0, v, ss, amax, osc, us, pl.group);
+        epi_chunk(a, i, col0, v, ss, amax, osc, us, pl.group, pl.n, pl.row0);
       }
       tc_fence_before();
       __syncwarp();
@@ -456,7 +494,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
         // fixed-order warp reduction; one partial per (tile, quadrant), summed in order later
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if (lane == 0) a.partials[(size_t)u * 4 + q] = ss;
+        const size_t pidx = a.ninst > 0 ? (size_t)a.g_part0[pl.inst] + (size_t)pl.tile * 4 : (size_t)u * 4;
+        if (lane == 0) a.partials[pidx + q] = ss;
       }
     }
     if (a.amax_bits) {

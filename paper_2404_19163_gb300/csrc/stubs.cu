@@ -6,11 +6,6 @@
   if (c) ctx_fail(c, ZFACT_ERR_UNSUPPORTED, "%s is not available in this build", name); \
   return ZFACT_ERR_UNSUPPORTED;
 
-extern "C" int zfact_refine_batched(zfact_ctx* c, int, const double* const*, const double* const*, const int64_t*,
-                                    const int*, int, const zfact_opts*, double* const*, double*, int, zfact_info*,
-                                    int*) {
-  ZF_STUB("zfact_refine_batched")
-}
 extern "C" int zfact_features(zfact_ctx* c, const double*, int64_t, float*) { ZF_STUB("zfact_features") }
 extern "C" int zfact_mlp_forward(zfact_ctx* c, const float*, const float*, const float*, const float*, int, float*) {
   ZF_STUB("zfact_mlp_forward")

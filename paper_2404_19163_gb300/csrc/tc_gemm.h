@@ -49,6 +49,17 @@ struct TcArgs {
   // (tile, group g) with g = t * oz_nch + c: all slice pairs p + q = t over K-chunk c.
   int oz_s, oz_nch, oz_chunk_kb, oz_ra, oz_rb, oz_c0;  // oz_c0: first K-chunk of this launch
   size_t g_stride;              // kEpiG32: elements between group slots
+  // Grouped mode (ninst > 0): independent square problems stacked along the rows of every
+  // operand and output buffer (common leading dimensions).  Scheduling slot j covers units
+  // [g_prefix[j], g_prefix[j+1]) of instance g_inst[j]; instance i has size g_n[i], first row
+  // g_row0[i], first partial g_part0[i], and is skipped entirely while g_done[i] != 0.
+  int ninst;
+  const int* g_prefix;
+  const int* g_inst;
+  const int* g_n;
+  const int* g_row0;
+  const int* g_part0;
+  const int* g_done;
 };
 
 // Tensor maps of the operands: A segment s is a_maps[s] (M x K, K-major = row-major),

@@ -127,39 +127,38 @@ CUBIC_DENSITY = 1.0 / 2.5 ** 3
 
 def cluster_sites(n: int, seed: int, min_dist: float = 1.5, density: float = CUBIC_DENSITY,
                   workload: int = 4):
-    """n random points in a sphere of volume n/density, no two closer than min_dist."""
+    """n random points in a sphere of volume n/density, no two closer than min_dist
+    (random sequential addition; candidates are tested in batches against a KD-tree)."""
+    from scipy.spatial import cKDTree
     g = rng(workload, seed)
     radius = (3.0 * n / (4.0 * math.pi * density)) ** (1.0 / 3.0)
-    pts = []
-    cell = min_dist
-    grid: dict = {}
-    md2 = min_dist * min_dist
-    while len(pts) < n:
-        cand = g.uniform(-radius, radius, (4 * n, 3))
+    pts = np.empty((0, 3))
+    while pts.shape[0] < n:
+        cand = g.uniform(-radius, radius, (2 * n, 3))
         cand = cand[np.sum(cand * cand, axis=1) <= radius * radius]
-        for p in cand:
-            kx, ky, kz = (int(v) for v in np.floor(p / cell))
-            ok = True
-            for dx in (-1, 0, 1):
-                for dy in (-1, 0, 1):
-                    for dz in (-1, 0, 1):
-                        for q in grid.get((kx + dx, ky + dy, kz + dz), ()):
-                            d0, d1, d2 = p[0] - q[0], p[1] - q[1], p[2] - q[2]
-                            if d0 * d0 + d1 * d1 + d2 * d2 < md2:
-                                ok = False
-                                break
-                        if not ok:
-                            break
-                    if not ok:
-                        break
-                if not ok:
-                    break
-            if ok:
-                grid.setdefault((kx, ky, kz), []).append(p)
-                pts.append(p)
-                if len(pts) == n:
-                    break
-    return np.array(pts)
+        if pts.shape[0]:
+            d, _ = cKDTree(pts).query(cand, k=1)
+            cand = cand[d >= min_dist]
+        # within the batch, keep the first of every conflicting pair (sequential order)
+        keep = np.ones(cand.shape[0], dtype=bool)
+        for a, b in sorted(cKDTree(cand).query_pairs(min_dist)):
+            if keep[a] and keep[b]:
+                keep[b] = False
+        cand = cand[keep]
+        pts = np.vstack([pts, cand[: n - pts.shape[0]]])
+    return pts
+
+
+def gaussian_overlap_torch(pos, device="cuda"):
+    """exp(-r^2/2) overlap of s-type sites (unit exponents) built on a torch device."""
+    import torch
+    p = torch.as_tensor(np.asarray(pos, dtype=np.float64), device=device)
+    sq = (p * p).sum(dim=1)
+    r2 = (sq[:, None] + sq[None, :] - 2.0 * (p @ p.T)).clamp_min_(0.0)
+    S = torch.exp(-0.5 * r2)
+    S = 0.5 * (S + S.T)
+    S.fill_diagonal_(1.0)
+    return S.contiguous()
 
 
 def trajectory(count: int = 128, n_lo: int = 256, n_hi: int = 3072, frames: int = 11,
@@ -184,6 +183,7 @@ def trajectory(count: int = 128, n_lo: int = 256, n_hi: int = 3072, frames: int 
     def frame(f):
         return [gaussian_overlap(p) for p in positions(f)]
 
+    frame.positions = positions
     return sizes, frame
 
 

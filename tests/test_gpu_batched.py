@@ -1,0 +1,85 @@
+"""Batched (grouped) factorizations of uneven N against single-instance runs and the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_19163_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [100, 257, 64, 300, 129, 513, 1, 700]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2404_19163_gb300 import Context, build
+    build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def mats(sizes, seed=0):
+    out = []
+    for k, n in enumerate(sizes):
+        if k % 2 == 0:
+            S, Q, lam = synth.householder_spd(n, seed=seed * 100 + k)
+        else:
+            pos = synth.cluster_sites(n, seed * 100 + k)
+            S = synth.gaussian_overlap(pos)
+        out.append(S)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["bf16", "bf16_split"])
+def test_batched_matches_single_instance(ctx, prec):
+    import torch
+    Ss = mats(SIZES)
+    St = [torch.from_numpy(S).cuda() for S in Ss]
+    Zb, hist, infos, status = ctx.refine_batched(St, None, precision=prec, hist_cap=32)
+    assert all(s in (0, 100) for s in status), status
+    for k, S in enumerate(Ss):
+        n = S.shape[0]
+        r = ctx.refine(St[k], None, order=2, precision=prec, refine_steps=0)
+        # same arithmetic per instance: the same stop iteration and the same history
+        assert infos[k]["iters"] == r.info["iters"], (k, infos[k], r.info)
+        h = hist[k][:infos[k]["hist_len"]]
+        assert np.allclose(h, r.hist[:len(h)], rtol=1e-3, atol=1e-6), (k, h, r.hist)
+        Z = Zb[k].cpu().numpy()
+        # the FP64-accurate final residual reported for instance k is the oracle's residual of Z_k
+        _, e = oracle.residual(S, Z)
+        assert abs(infos[k]["resid_f"] - e) <= 1e-12 + 1e-9 * e
+        floor = 2.0 ** -7 if prec == "bf16" else 2.0 ** -14
+        assert e / math.sqrt(n) <= floor
+
+
+def test_batched_warm_start_frames(ctx):
+    """Frame f+1 starts from frame f's Z (sites displaced by 0.02): it needs fewer updates."""
+    import torch
+    sizes = [300, 180, 420]
+    base = [synth.cluster_sites(n, 900 + k) for k, n in enumerate(sizes)]
+    g = np.random.default_rng(5)
+    S0 = [torch.from_numpy(synth.gaussian_overlap(p)).cuda() for p in base]
+    Z0, h0, i0, s0 = ctx.refine_batched(S0, None, precision="bf16_split")
+    moved = [p + g.normal(0, 0.02, p.shape) for p in base]
+    S1 = [torch.from_numpy(synth.gaussian_overlap(p)).cuda() for p in moved]
+    Z1, h1, i1, s1 = ctx.refine_batched(S1, Z0, precision="bf16_split")
+    for k in range(3):
+        assert h1[k][0] < 0.1 * h0[k][0]          # the warm start is much closer
+        assert i1[k]["iters"] <= i0[k]["iters"]
+        _, e = oracle.residual(S1[k].cpu().numpy(), Z1[k].cpu().numpy())
+        assert e / math.sqrt(sizes[k]) <= 2.0 ** -14
+
+
+def test_batched_fixed_iters_and_errors(ctx):
+    import torch
+    from paper_2404_19163_gb300 import ZfactError
+    Ss = [torch.from_numpy(S).cuda() for S in mats([90, 200], seed=3)]
+    Zb, hist, infos, status = ctx.refine_batched(Ss, None, precision="bf16", fixed_iters=2)
+    assert [i["iters"] for i in infos] == [2, 2]
+    Sn = np.eye(50)
+    Sn[3, 4] = Sn[4, 3] = np.nan
+    with pytest.raises(ZfactError):
+        ctx.refine_batched([Ss[0], torch.from_numpy(Sn).cuda()], None, precision="bf16")
