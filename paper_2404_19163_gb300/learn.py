@@ -1,0 +1,189 @@
+"""Learned start proposal: labels from the method itself, training on the library's
+MLP kernels, and evaluation against the plain schedule.
+
+For every training matrix the method is run (grouped launches, BF16 hi/lo split bulk,
+Algorithm 2 stop) from Z0 = f s0 I for each start factor f of a grid and each order m;
+the label is the (f, m) of least work to reach ||I - Z^T S Z||_F / sqrt(N) <= tau, the
+work of one bulk iteration being (m + 4) N^3 multiply-adds on symmetric tiles (K1 2N^3,
+K2 N^3, the polynomial chain (m - 1) N^3, K4 2N^3) plus 3 N^3 for the first residual.
+The network (16 -> 64 -> 64 -> 5, GELU) maps the features of S to log f and to logits of
+m; zfact_propose applies it with the plain schedule (f = 1, m = 2) as fallback.
+
+  python -m paper_2404_19163_gb300.learn --train 2000 --heldout 256 --out weights.npz
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import synth
+from .zfact import MLP_NPARAMS, Context
+
+F_GRID = (0.9, 1.0, 1.1, 1.25, 1.4, 1.6, 1.8, 2.0)
+ORDERS = (2, 3, 4, 5)
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "propose_mlp.npz")
+
+
+def instances(count: int, split: str, n_lo: int, n_hi: int):
+    import torch
+    return [torch.from_numpy(synth.proposal_instance(k, n_lo, n_hi, split)).cuda() for k in range(count)]
+
+
+def features(ctx: Context, S_list):
+    return np.stack([ctx.features(S) for S in S_list]).astype(np.float32)
+
+
+def work(hist, n, m, tau):
+    """Multiply-adds until Err/sqrt(N) <= tau (inf if never reached)."""
+    for k, h in enumerate(hist):
+        if not np.isfinite(h):
+            return math.inf
+        if h / math.sqrt(n) <= tau:
+            return (3.0 + (m + 4.0) * k) * float(n) ** 3
+    return math.inf
+
+
+def label(ctx: Context, S_list, feats, tau=1e-4, precision="bf16_split", nmax=30):
+    """Run the method over the (f, m) grid; returns (log f*, index of m*, work table)."""
+    import torch
+    B = len(S_list)
+    ns = [int(S.shape[0]) for S in S_list]
+    s0 = np.exp(-0.5 * feats[:, 1].astype(np.float64))
+    table = np.full((B, len(F_GRID), len(ORDERS)), math.inf)
+    for fi, f in enumerate(F_GRID):
+        Z0 = [torch.eye(n, dtype=torch.float64, device="cuda") * (f * s0[i]) for i, n in enumerate(ns)]
+        for mi, m in enumerate(ORDERS):
+            _, hist, infos, status = ctx.refine_batched(S_list, Z0, orders=[m] * B, precision=precision,
+                                                        hist_cap=nmax + 2, nmax=nmax, final_residual=0,
+                                                        raise_on_error=False)
+            for i in range(B):
+                table[i, fi, mi] = work(hist[i][:infos[i]["hist_len"]], ns[i], m, tau)
+        del Z0
+    flat = table.reshape(B, -1)
+    best = np.argmin(flat, axis=1)
+    ok = np.isfinite(flat[np.arange(B), best])
+    fi, mi = np.unravel_index(best, (len(F_GRID), len(ORDERS)))
+    y_scale = np.log(np.asarray(F_GRID))[fi].astype(np.float32)
+    y_order = mi.astype(np.int32)
+    # instances no grid point solved keep the plain schedule as their label
+    y_scale[~ok] = 0.0
+    y_order[~ok] = 0
+    return y_scale, y_order, table
+
+
+def init_params(seed=0):
+    g = np.random.default_rng(seed)
+    sizes = (16, 64, 64, 5)
+    out = []
+    for fi, fo in zip(sizes[:-1], sizes[1:]):
+        out.append(g.standard_normal(fo * fi) * math.sqrt(2.0 / (fi + fo)))
+        out.append(np.zeros(fo))
+    p = np.concatenate(out).astype(np.float32)
+    assert p.size == MLP_NPARAMS
+    return p
+
+
+def train(ctx: Context, X, y_scale, y_order, steps=3000, lr=3e-3, w_order=1.0, seed=0, log_every=0):
+    """Full-batch Adam on the library's forward/backward/Adam kernels.  Returns
+    (params, mean, std, loss history) with params/mean/std as device tensors."""
+    import torch
+    X = np.asarray(X, dtype=np.float32)
+    mean = X.mean(axis=0)
+    std = X.std(axis=0) + 1e-6
+    dev = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+    P = dev(init_params(seed))
+    M = torch.zeros_like(P)
+    V = torch.zeros_like(P)
+    Xd, mu, sd = dev(X), dev(mean), dev(std)
+    ts, to = dev(y_scale), dev(y_order, torch.int32)
+    losses = []
+    for step in range(1, steps + 1):
+        grad, loss = ctx.mlp_backward(P, mu, sd, Xd, ts, to, w_order)
+        ctx.mlp_adam(P, grad, M, V, step, lr=lr)
+        losses.append(loss)
+        if log_every and step % log_every == 0:
+            print("step %d loss %.5f" % (step, loss), flush=True)
+    return P, mu, sd, losses
+
+
+def evaluate(ctx: Context, S_list, P, mu, sd, precision="bf16_split", tol=1e-12):
+    """Plain schedule vs proposal on each matrix: device ms and bulk iterations to tol
+    (full path: bulk + refinement + FP64-accurate final residual)."""
+    import torch
+    rows = []
+    for S in S_list:
+        n = int(S.shape[0])
+        rp = ctx.refine(S, None, order=2, precision=precision, tol=tol, raise_on_error=False)
+        s, m = ctx.propose(S, P, mu, sd)
+        Z0 = torch.eye(n, dtype=torch.float64, device="cuda") * s
+        rl = ctx.refine(S, Z0, order=m, precision=precision, tol=tol, raise_on_error=False)
+        rows.append({"n": n, "plain_ms": rp.info["ms"], "plain_iters": rp.info["iters"],
+                     "plain_ok": rp.status in (0, 100), "prop_ms": rl.info["ms"], "prop_iters": rl.info["iters"],
+                     "prop_ok": rl.status in (0, 100), "s_over_s0": float(s * math.exp(0.5 * float(
+                         ctx.features(S)[1]))), "m": m})
+    return rows
+
+
+def save(path, P, mu, sd, meta):
+    np.savez(path, params=P.cpu().numpy(), mean=mu.cpu().numpy(), std=sd.cpu().numpy(),
+             meta=json.dumps(meta))
+
+
+def load(path=WEIGHTS):
+    import torch
+    z = np.load(path)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float32)
+    return dev(z["params"]), dev(z["mean"]), dev(z["std"]), json.loads(str(z["meta"]))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--heldout", type=int, default=256)
+    ap.add_argument("--n-lo", type=int, default=128)
+    ap.add_argument("--n-hi", type=int, default=1536)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--tau", type=float, default=1e-4)
+    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--chunk", type=int, default=500)
+    args = ap.parse_args()
+    t0 = time.time()
+    with Context(0) as ctx:
+        feats, ys, yo = [], [], []
+        for c0 in range(0, args.train, args.chunk):
+            Ss = [__import__("torch").from_numpy(synth.proposal_instance(k, args.n_lo, args.n_hi, "train")).cuda()
+                  for k in range(c0, min(args.train, c0 + args.chunk))]
+            f = features(ctx, Ss)
+            a, b, _ = label(ctx, Ss, f, tau=args.tau)
+            feats.append(f)
+            ys.append(a)
+            yo.append(b)
+            del Ss
+        X = np.concatenate(feats)
+        y_scale = np.concatenate(ys)
+        y_order = np.concatenate(yo)
+        t_label = time.time() - t0
+        P, mu, sd, losses = train(ctx, X, y_scale, y_order, steps=args.steps)
+        Sh = instances(args.heldout, "heldout", args.n_lo, args.n_hi)
+        rows = evaluate(ctx, Sh, P, mu, sd)
+        plain = sum(r["plain_ms"] for r in rows)
+        prop = sum(r["prop_ms"] for r in rows)
+        meta = {"train": args.train, "heldout": args.heldout, "n_range": [args.n_lo, args.n_hi], "tau": args.tau,
+                "label_seconds": round(t_label, 1), "final_loss": losses[-1],
+                "label_order_hist": np.bincount(y_order, minlength=4).tolist(),
+                "label_f_mean": float(np.exp(y_scale).mean()),
+                "heldout_plain_ms": plain, "heldout_proposed_ms": prop,
+                "heldout_plain_iters": float(np.mean([r["plain_iters"] for r in rows])),
+                "heldout_proposed_iters": float(np.mean([r["prop_iters"] for r in rows])),
+                "heldout_all_converged": all(r["plain_ok"] and r["prop_ok"] for r in rows)}
+        save(args.out, P, mu, sd, meta)
+        print(json.dumps(meta), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -211,7 +211,7 @@ class Context:
 
     # ------------------------------------------------------------ batched
     def refine_batched(self, S_list: Sequence, Z0_list=None, orders=None, precision: str = "bf16",
-                       Z_list=None, hist_cap: int = 64, **opts):
+                       Z_list=None, hist_cap: int = 64, raise_on_error: bool = True, **opts):
         import torch
         count = len(S_list)
         ns = np.array([int(s.shape[0]) for s in S_list], dtype=np.int64)
@@ -232,7 +232,8 @@ class Context:
         rc = self.lib.zfact_refine_batched(self.h, count, sp, z0p, ns.ctypes.data, ords.ctypes.data,
                                            PRECISION[precision], ctypes.byref(o), zp, hist.ctypes.data,
                                            hist_cap, infos, status.ctypes.data)
-        self._raise(rc)
+        if raise_on_error or rc not in (OK, WARN_NONCONTRACTIVE, ERR_NONFINITE, ERR_NOT_CONVERGED):
+            self._raise(rc)
         return Z_list, hist, [i.as_dict() for i in infos], status
 
     # ------------------------------------------------------------ per-kernel timing
