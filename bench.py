@@ -33,7 +33,25 @@ sys.path.insert(0, ROOT)
 METRIC = "ms to ||I−ZᵀSZ||_F/√N≤tol per factorization; TFLOP/s & tensor-pipe % vs FP64 path"
 UNIT = "ms"
 TOL = 1e-12
+# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/ozaki_product_N4096.md),
+# valid only while the kernel's source is the one that was captured
+TRAFFIC = {"tc_gemm.ozaki": {"bytes_per_launch": 7.32e9, "source": "paper_2404_19163_gb300/csrc/k_tc.cu",
+                             "sha1": "b4f7e57d908ea369ec1c020d960a1317e36ba946"}}
 FP64_ITERS_WORKLOAD2 = 4   # updates the FP64 recursion needs on workload 2 (counted by the FP64 GPU path)
+
+
+def captured_traffic(kernel):
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    try:
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != t["sha1"]:
+                return None
+    except OSError:
+        return None
+    return t["bytes_per_launch"]
 
 
 def measured_peaks():
@@ -265,7 +283,7 @@ def run_ours(args, rank, ws, local):
             ach = fl / (avg_ms * 1e-3) / 1e12
             peak = peaks.get("bf16_tflops_sustained", 1736.2)
             roof = {"bound": "tensor", "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
-                    "frac": round(ach / peak, 4), "traffic": None, "kernel": dom["name"],
+                    "frac": round(ach / peak, 4), "traffic": captured_traffic(dom["name"]), "kernel": dom["name"],
                     "peak_source": "%s bf16 sustained" % peak_src}
         elif dom["name"].startswith("f64_gemm"):
             ach = fl / (avg_ms * 1e-3) / 1e12
@@ -403,6 +421,63 @@ def run_batched(args):
     }), flush=True)
 
 
+def run_ill(args):
+    """Workload 3: fcc Gaussian overlap, 4 exponents per site, N = 16384 (cond ~1e5-1e6),
+    warm start Z0 = the converged factor of the same system with sites displaced by
+    N(0, 0.01^2); FP16 hi/lo split bulk, Algorithm 3 refinement with FP64-accurate d."""
+    import numpy as np
+    import torch
+    from paper_2404_19163_gb300 import Context, synth, build as zbuild
+    zbuild.build()
+    S = synth.fcc_overlap_torch()
+    n = S.shape[0]
+    lam = torch.linalg.eigvalsh(S)
+    cond = float(lam[-1] / lam[0])
+    Sp = synth.fcc_overlap_torch(perturb=0.01)
+    stream = torch.cuda.Stream()
+    ctx = Context(0, stream=stream)
+    prec = "fp16_split" if args.precision == "bf16_split" else args.precision
+    Z0 = ctx.refine(Sp, None, order=2, precision=prec, tol=0.0, raise_on_error=False).Z
+    del Sp
+    Z = torch.empty_like(S)
+    kw = dict(order=2, precision=prec, tol=args.tol_ill, Z=Z, raise_on_error=False)
+    r = ctx.refine(S, Z0, **kw)  # warm-up
+    ctx.set_profiling(True)
+    ctx.kernel_stats(reset=True)
+    times, infos = [], []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = ctx.refine(S, Z0, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(dict(r.info, status=r.status))
+    stats = ctx.kernel_stats(reset=True)
+    ctx.set_profiling(False)
+    native = ctx.residual(S, Z, "native")
+    out = {"workload": "fcc_overlap_N16384_4exp_warm_start", "metric": METRIC, "value": round(statistics.mean(times), 2),
+           "unit": "ms", "N": n, "cond": cond, "precision": prec, "tol": args.tol_ill,
+           "iters": infos[-1]["iters"], "refine_iters": infos[-1]["refine_iters"], "status": infos[-1]["status"],
+           "resid": infos[-1]["resid_f"] / math.sqrt(n), "resid_native_fp64": native / math.sqrt(n),
+           "hist": [float(h) for h in r.hist], "clocks": clk.summary(),
+           "kernels": sorted([{k: (round(v, 3) if isinstance(v, float) else v) for k, v in x.items()}
+                              for x in stats], key=lambda x: -x["ms"])[:8]}
+    if args.fp64_comparator:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r64 = ctx.refine(S, Z0, order=2, precision="fp64", Z=Z, raise_on_error=False)
+        e1.record(stream)
+        e1.synchronize()
+        out["fp64_path"] = {"ms": e0.elapsed_time(e1), "iters": r64.info["iters"],
+                            "resid": r64.info["resid_f"] / math.sqrt(n), "hist": [float(h) for h in r64.hist]}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,7 +488,9 @@ def main():
     ap.add_argument("--refine-mode", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, choices=[None, "residual"])
-    ap.add_argument("--workload", default="single", choices=["single", "batched"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "ill"])
+    ap.add_argument("--tol-ill", type=float, default=2e-12)  # 10x the FP64 path's 1.86e-13 on this input
+    ap.add_argument("--fp64-comparator", action="store_true")
     ap.add_argument("--batch-count", type=int, default=128)
     args = ap.parse_args()
     if args.case == "residual":
@@ -421,6 +498,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "ill":
+        run_ill(args)
         return
     args.warmup = max(args.warmup, 1)
     if args.impl == "reference":

@@ -236,8 +236,8 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
     const uint16_t* bs2[3] = {Bh, Bl, Bh};
     const int nseg = (Al && Bl) ? 3 : 1;
     for (int s = 0; s < nseg; ++s) {
-      int r1 = tc_make_map(&maps.a[s], as[s], rows, ld, ld, 128, true);
-      int r2 = tc_make_map(&maps.b[s], bs2[s], rows, ld, ld, bnv, true);
+      int r1 = ctx_make_map(c, &maps.a[s], as[s], rows, ld, ld, 128, true);
+      int r2 = ctx_make_map(c, &maps.b[s], bs2[s], rows, ld, ld, bnv, true);
       if (r1 || r2) return ctx_fail(c, ZFACT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d, %d)", r1, r2);
     }
     a.nseg = nseg;

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tc_gemm.h"
 
 struct DevBuf {
   void* ptr;
@@ -45,6 +46,8 @@ struct zfact_ctx {
   std::vector<KStat> kstats;
   std::vector<PendingEv> pending;
   std::vector<cudaEvent_t> ev_pool;
+  // encoded TMA descriptors keyed by (address, rows, cols, ld, box rows, type)
+  std::map<std::string, CUtensorMap> map_cache;
   // batched mode
   std::map<std::string, int> batch_bn;  // autotuned tile width per set of sizes
   std::string batch_sig;                // layout of the packed buffers (zeroed on change)
@@ -73,6 +76,9 @@ int ctx_cuda(zfact_ctx* c, cudaError_t e, const char* what);
 void* ctx_buf(zfact_ctx* c, const char* name, size_t bytes, int* status);
 bool is_device_ptr(const void* p);
 int ctx_read_state(zfact_ctx* c);
+
+// Cached tc_make_map (tc_gemm.h): identical (address, shape, box, type) reuse one encoding.
+int ctx_make_map(zfact_ctx* c, CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows, bool bf16);
 
 // FP64 building blocks (capi.cu)
 int f64_residual(zfact_ctx* c, const double* S, const double* Z, double* A, double* D, int n, int idx, int rule,

@@ -80,9 +80,10 @@ __device__ __forceinline__ UnitPlan plan_unit(int u, const TcArgs& a, int kblock
     kblocks = (pl.n + BK - 1) / BK;
   }
   if (a.oz_s > 0) {
-    const int ng = a.oz_s * a.oz_nch;
-    pl.tile = u / ng;
-    pl.group = u % ng;
+    // group-major order: the CTAs running at the same time form different tiles of the same
+    // (group, K-chunk) and so read the same slice panels, which then stay in L2
+    pl.group = u / a.oz_tiles;
+    pl.tile = u % a.oz_tiles;
     pl.t = pl.group / a.oz_nch;
     const int c = pl.group % a.oz_nch;
     pl.p0 = pl.t - (a.oz_s - 1) > 0 ? pl.t - (a.oz_s - 1) : 0;

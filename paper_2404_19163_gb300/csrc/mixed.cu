@@ -12,6 +12,7 @@
 // product are then K-major (row-major) 16-bit matrices, which is what a TMA
 // box and a tcgen05 shared-memory descriptor read directly.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <utility>
@@ -48,6 +49,23 @@ int alloc16(zfact_ctx* c, const char* name, int n, int ld, bool split, Mat16* m)
 
 }  // namespace
 
+int ctx_make_map(zfact_ctx* c, CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows,
+                 bool bf16) {
+  char key[96];
+  snprintf(key, sizeof(key), "%p:%d:%d:%d:%d:%d", base, rows, cols, ld, box_rows, bf16 ? 1 : 0);
+  auto it = c->map_cache.find(key);
+  if (it != c->map_cache.end()) {
+    *m = it->second;
+    return 0;
+  }
+  const int r = tc_make_map(m, base, rows, cols, ld, box_rows, bf16);
+  if (r == 0) {
+    if (c->map_cache.size() > 4096) c->map_cache.clear();
+    c->map_cache[key] = *m;
+  }
+  return r;
+}
+
 // A tensor-core product D = sum_s A_s B_s^T (B_s given N x K, i.e. the row-major matrix whose
 // rows are the columns of the right factor), with the split segments of Sec. 3.2 when
 // A.l / B.l are present: (h)(h) + (h)(l) + (l)(h).
@@ -59,8 +77,8 @@ int tc_product(zfact_ctx* c, TcArgs& a, const Mat16& A, const Mat16& B, int ld, 
   int nseg = 1;
   if (A.l && B.l) nseg = 3;
   for (int s = 0; s < nseg; ++s) {
-    int r1 = tc_make_map(&maps.a[s], as[s], a.M, a.K, ld, 128, a.bf16 != 0);
-    int r2 = tc_make_map(&maps.b[s], bs[s], a.N, a.K, ld, bn, a.bf16 != 0);
+    int r1 = ctx_make_map(c, &maps.a[s], as[s], a.M, a.K, ld, 128, a.bf16 != 0);
+    int r2 = ctx_make_map(c, &maps.b[s], bs[s], a.N, a.K, ld, bn, a.bf16 != 0);
     if (r1 || r2) return ctx_fail(c, ZFACT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d, %d)", r1, r2);
   }
   a.nseg = nseg;

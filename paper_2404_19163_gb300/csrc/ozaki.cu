@@ -76,8 +76,8 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
   TcMaps maps;
   memset(&maps, 0, sizeof(maps));
   const int bn = 256;
-  int r1 = tc_make_map(&maps.a[0], A.sl, A.s * A.Rp, n, ld, 128, true);
-  int r2 = tc_make_map(&maps.b[0], B.sl, B.s * B.Rp, n, ld, bn, true);
+  int r1 = ctx_make_map(c, &maps.a[0], A.sl, A.s * A.Rp, n, ld, 128, true);
+  int r2 = ctx_make_map(c, &maps.b[0], B.sl, B.s * B.Rp, n, ld, bn, true);
   if (r1 || r2) return ctx_fail(c, ZFACT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d, %d)", r1, r2);
   for (int c0 = 0; c0 < nch_total; c0 += nch_b) {
     const int nch = (nch_total - c0) < nch_b ? (nch_total - c0) : nch_b;
@@ -98,6 +98,7 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
     a.oz_c0 = c0;
     a.oz_ra = A.Rp;
     a.oz_rb = B.Rp;
+    a.oz_tiles = tc_num_units(a, bn) / (s * nch);
     a.err_flag = &c->st_dev->error;
     // algorithmic work: s(s+1)/2 slice pairs over this launch's share of K
     const int kb_lo = c0 * ckb, kb_hi = (c0 + nch) * ckb < kblocks ? (c0 + nch) * ckb : kblocks;

@@ -149,16 +149,35 @@ def cluster_sites(n: int, seed: int, min_dist: float = 1.5, density: float = CUB
     return pts
 
 
-def gaussian_overlap_torch(pos, device="cuda"):
-    """exp(-r^2/2) overlap of s-type sites (unit exponents) built on a torch device."""
+def gaussian_overlap_torch(pos, exps=None, device="cuda", chunk: int = 4096):
+    """The overlap of ``gaussian_overlap`` built on a torch device (FP64), row chunk by chunk."""
     import torch
     p = torch.as_tensor(np.asarray(pos, dtype=np.float64), device=device)
+    n = p.shape[0]
+    a = torch.ones(n, dtype=torch.float64, device=device) if exps is None else \
+        torch.as_tensor(np.asarray(exps, dtype=np.float64), device=device)
     sq = (p * p).sum(dim=1)
-    r2 = (sq[:, None] + sq[None, :] - 2.0 * (p @ p.T)).clamp_min_(0.0)
-    S = torch.exp(-0.5 * r2)
+    S = torch.empty((n, n), dtype=torch.float64, device=device)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        r2 = (sq[r0:r1, None] + sq[None, :] - 2.0 * (p[r0:r1] @ p.T)).clamp_min_(0.0)
+        ai = a[r0:r1, None]
+        asum = ai + a[None, :]
+        pref = (2.0 * torch.sqrt(ai * a[None, :]) / asum) ** 1.5
+        S[r0:r1] = pref * torch.exp(-(ai * a[None, :] / asum) * r2)
     S = 0.5 * (S + S.T)
     S.fill_diagonal_(1.0)
     return S.contiguous()
+
+
+def fcc_overlap_torch(cells=(8, 8, 16), a_lat: float = FCC_LATTICE, exps=FCC_EXPONENTS, perturb: float = 0.0,
+                      perturb_seed: int = 1, device="cuda"):
+    """``fcc_overlap`` built on a torch device."""
+    pos = fcc_sites(cells, a_lat)
+    if perturb > 0:
+        pos = pos + rng(3, 100 + perturb_seed).normal(0.0, perturb, pos.shape)
+    c, a = fcc_basis(pos, exps)
+    return gaussian_overlap_torch(c, a, device=device)
 
 
 def trajectory(count: int = 128, n_lo: int = 256, n_hi: int = 3072, frames: int = 11,
