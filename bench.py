@@ -260,6 +260,23 @@ def run_ours(args, rank, ws, local):
     e1.synchronize()
     fp64_ms = e0.elapsed_time(e1)
 
+    # FP32 CUDA-core path ("single") on the same input: bulk to the Algorithm 2 stop + the
+    # FP64-accurate residual of its result (it cannot reach tol without refinement)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r32 = ctx.refine(S, None, order=2, precision="fp32", Z=Z64)
+    e1.record(stream)
+    e1.synchronize()
+    fp32_ms = e0.elapsed_time(e1)
+    fp32_info = {"ms": round(fp32_ms, 3), "iters": r32.info["iters"], "resid": r32.info["resid_f"] / math.sqrt(n)}
+    e0.record(stream)
+    r32r = ctx.refine(S, None, order=2, precision="fp32", refine_steps=3, tol=TOL, Z=Z64)
+    e1.record(stream)
+    e1.synchronize()
+    fp32_info.update({"refined_ms": round(e0.elapsed_time(e1), 3), "refined_resid": r32r.info["resid_f"] / math.sqrt(n),
+                      "refined_iters": r32r.info["refine_iters"]})
+
     # e2e: host (pinned) buffers through the public C ABI, copies inside the call
     S_pin = torch.from_numpy(S_host).pin_memory()
     Z_pin = torch.empty_like(S_pin).pin_memory()
@@ -327,6 +344,7 @@ def run_ours(args, rank, ws, local):
             "iters": infos[-1]["iters"], "refine_iters": infos[-1]["refine_iters"],
             "resid": resid, "rel_z_vs_fp64": rel_z,
             "fp64_path": {"ms": round(fp64_ms, 3), "iters": fp64_iters, "resid": fp64_resid},
+            "fp32_path": fp32_info,
             "speedup_vs_fp64_path": round(fp64_ms / ms, 2),
             "tc_tflops": round(tc_fl / (tc_ms * 1e-3) / 1e12, 1) if tc_ms > 0 else None,
             "kernels": sorted([{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}

@@ -58,6 +58,8 @@ typedef enum zfact_status {
 /* Arithmetic of the bulk iterations (Table I of the paper, GB300 forms). */
 typedef enum zfact_precision {
     ZFACT_P_FP64 = 0,        /* "double": every product in FP64 (CUDA cores) */
+    ZFACT_P_FP32 = 1,        /* "single": every bulk product in FP32 (CUDA cores); Algorithm 3's
+                                refinement only when refine_steps > 0 */
     ZFACT_P_BF16 = 3,        /* "(h)(h)" with BF16 operands, FP32 accumulation (tcgen05) */
     ZFACT_P_FP16 = 4,        /* "(h)(h)" with FP16 operands (power-of-two scaled), FP32 accumulation */
     ZFACT_P_FP16_SPLIT = 5,  /* "(h)(h)+(h)(l)+(l)(h)": FP16 hi+lo split operands, FP32 accumulation */
@@ -77,7 +79,7 @@ typedef enum zfact_refine_mode {
 typedef struct zfact_opts {
     int nmax;            /* max bulk updates (default 50) */
     int refine_steps;    /* max FP64-d refinement updates after the bulk stop (Algorithm 3);
-                            default 0 for FP64, 3 for the mixed precisions */
+                            default 0 for FP64 and FP32, 3 for the 16-bit precisions */
     int refine_mode;     /* zfact_refine_mode (default ZFACT_R_OZAKI when available) */
     int stop_rule;       /* 0: Algorithm 2 (Err_n > Err_{n-1}^3, or Err_n >= Err_{n-1}, or non-finite);
                             1: Algorithm 1 (Err_n / sqrt(N) <= tol) */
@@ -194,7 +196,8 @@ int zfact_kernel_stats(zfact_ctx* ctx, zfact_kstat* out, int cap, int* n, int re
 
 /* ---- single steps, exposed for step-level parity tests ----------------------------- */
 /* C = A B for N x N FP64 matrices with the operands rounded to the 16-bit format of
- * `precision` (BF16 / FP16 / the hi+lo splits; FP64 = plain FP64 product) and FP32
+ * `precision` (BF16 / FP16 / the hi+lo splits; FP64 = plain FP64 product; FP32 = FP32 operands
+ * and CUDA-core FP32 product, scales ignored) and FP32
  * tensor-core accumulation; C returned in FP64.  scale_a / scale_b are the power-of-two
  * factors applied before rounding (undone after).  DEVICE pointers. */
 int zfact_gemm(zfact_ctx* ctx, int precision, int64_t N, const double* A, double scale_a,

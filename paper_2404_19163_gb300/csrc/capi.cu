@@ -270,8 +270,8 @@ static int check_common(zfact_ctx* c, const double* S, int64_t N, int order, int
   if (!S) return ctx_fail(c, ZFACT_ERR_ARG, "S is NULL");
   if (N < 1 || N > 65536) return ctx_fail(c, ZFACT_ERR_ARG, "N=%lld out of range [1, 65536]", (long long)N);
   if (order < 2 || order > 5) return ctx_fail(c, ZFACT_ERR_ARG, "order=%d out of range [2, 5]", order);
-  if (precision != ZFACT_P_FP64 && precision != ZFACT_P_BF16 && precision != ZFACT_P_FP16 &&
-      precision != ZFACT_P_FP16_SPLIT && precision != ZFACT_P_BF16_SPLIT)
+  if (precision != ZFACT_P_FP64 && precision != ZFACT_P_FP32 && precision != ZFACT_P_BF16 &&
+      precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT && precision != ZFACT_P_BF16_SPLIT)
     return ctx_fail(c, ZFACT_ERR_ARG, "unknown precision %d", precision);
   return ZFACT_OK;
 }
@@ -288,7 +288,7 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   zfact_default_opts(&o);
   if (opts_in) o = *opts_in;
   if (o.nmax < 1) o.nmax = 1;
-  if (o.refine_steps < 0) o.refine_steps = (precision == ZFACT_P_FP64) ? 0 : 3;
+  if (o.refine_steps < 0) o.refine_steps = (precision == ZFACT_P_FP64 || precision == ZFACT_P_FP32) ? 0 : 3;
   if (o.refine_mode < 0) o.refine_mode = ZFACT_R_OZAKI;
   const int n = (int)N;
   const size_t nn = (size_t)n * n, bytes = nn * sizeof(double);
@@ -370,6 +370,10 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
       if ((st = ctx_read_state(c))) return st;
     }
     inf.resid_f = c->st_host->hist[c->st_host->hist_len - 1];
+  } else if (precision == ZFACT_P_FP32) {
+    st = single_refine(c, S, Zcur, n, order, o, &iters, &ridx, &inf);
+    if (st) return st;
+    Zcur = c->mixed_result;
   } else {
     st = mixed_refine(c, S, Zcur, Znext, n, order, precision, o, &iters, &ridx, &inf);
     if (st) return st;

@@ -91,6 +91,13 @@ int oz_prepare_S(zfact_ctx* c, const double* S, int n);
 int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop);
 int oz_update(zfact_ctx* c, double* Z, const double* Q, int n);
 
+// Algorithm 3 with FP64-accurate sliced products, from the FP64 iterate Z64 (mixed.cu)
+int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o, int iters,
+                 int* ridx_out, zfact_info* inf);
+// The paper's "single": every bulk product in FP32 on the CUDA cores (single.cu)
+int single_refine(zfact_ctx* c, const double* S, double* Za64, int n, int order, const zfact_opts& o, int* iters_out,
+                  int* ridx_out, zfact_info* inf);
+
 // Mixed-precision driver (mixed.cu): bulk tensor-core iterations, then Algorithm 3's refinement.
 int mixed_refine(zfact_ctx* c, const double* S, double* Za, double* Zb, int n, int order, int precision,
                  const zfact_opts& o, int* iters, int* ridx, zfact_info* inf);

@@ -1,4 +1,5 @@
-// FP64 CUDA-core products of the recursion (the paper's "double", Table I),
+// CUDA-core products of the recursion in FP64 (the paper's "double", Table I) and FP32
+// ("single"),
 // with the element-wise steps fused into the epilogues:
 //   residual   d = I - Z^T (S Z), symmetric, upper tiles only   (Eq. np1, Algorithm 2's Err)
 //   polynomial Q = c1 d + c2 d^2 (+ c_k d^k chains)               (delta-form of Eq. np1)
@@ -24,15 +25,16 @@ __device__ __forceinline__ void sym_tile_of(int b, int T, int& bi, int& bj) {
   bj = row + rem;
 }
 
-__global__ void __launch_bounds__(NT) k64_gemm(F64Gemm g) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+template <typename T, typename G>
+__global__ void __launch_bounds__(NT) k64_gemm(G g) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
   __shared__ double red[NT / 32];
   const int n = g.n;
-  const int T = (n + BM - 1) / BM;
+  const int TB = (n + BM - 1) / BM;
   int bi, bj;
   if (g.sym) {
-    sym_tile_of(blockIdx.x, T, bi, bj);
+    sym_tile_of(blockIdx.x, TB, bi, bj);
   } else {
     bi = blockIdx.y;
     bj = blockIdx.x;
@@ -40,13 +42,13 @@ __global__ void __launch_bounds__(NT) k64_gemm(F64Gemm g) {
   const int i0 = bi * BM, j0 = bj * BN;
   const int t = threadIdx.x;
   const int ty = t / 16, tx = t % 16;
-  double acc[4][4] = {};
+  T acc[4][4] = {};
   for (int k0 = 0; k0 < n; k0 += BK) {
 #pragma unroll
     for (int e = 0; e < (BM * BK) / NT; ++e) {
       const int idx = t + e * NT;
       int ii, kk;
-      double v = 0.0;
+      T v = 0;
       if (g.transA) {
         kk = idx / BM;
         ii = idx % BM;
@@ -65,12 +67,12 @@ __global__ void __launch_bounds__(NT) k64_gemm(F64Gemm g) {
       const int idx = t + e * NT;
       const int kk = idx / BN, jj = idx % BN;
       const int gk = k0 + kk, gj = j0 + jj;
-      Bs[kk][jj] = (gk < n && gj < n) ? g.B[(size_t)gk * n + gj] : 0.0;
+      Bs[kk][jj] = (gk < n && gj < n) ? g.B[(size_t)gk * n + gj] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
 #pragma unroll
@@ -92,13 +94,13 @@ __global__ void __launch_bounds__(NT) k64_gemm(F64Gemm g) {
       const int j = j0 + tx * 4 + c;
       if (j >= n) continue;
       if (g.sym && j < i) continue;  // the (j, i) entry is written by the tile that owns it
-      double v;
+      T v;
       if (g.resid) {
-        v = (i == j ? 1.0 : 0.0) - acc[r][c];
-        ss += (i == j ? 1.0 : 2.0) * v * v;
+        v = (i == j ? T(1) : T(0)) - acc[r][c];
+        ss += (i == j ? 1.0 : 2.0) * (double)v * (double)v;
       } else {
-        v = g.beta * acc[r][c];
-        if (g.Add) v = fma(g.alpha, g.Add[(size_t)i * n + j], v);
+        v = (T)g.beta * acc[r][c];
+        if (g.Add) v = fma((T)g.alpha, g.Add[(size_t)i * n + j], v);
         if (g.P) {
           g.P[(size_t)i * n + j] = acc[r][c];
           if (g.sym && j != i) g.P[(size_t)j * n + i] = acc[r][c];
@@ -131,7 +133,14 @@ int f64_num_blocks(int n, bool sym) {
 cudaError_t launch_f64_gemm(const F64Gemm& g, cudaStream_t s) {
   const int T = (g.n + BM - 1) / BM;
   dim3 grid = g.sym ? dim3(T * (T + 1) / 2) : dim3(T, T);
-  k64_gemm<<<grid, NT, 0, s>>>(g);
+  k64_gemm<double, F64Gemm><<<grid, NT, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_gemm(const F32Gemm& g, cudaStream_t s) {
+  const int T = (g.n + BM - 1) / BM;
+  dim3 grid = g.sym ? dim3(T * (T + 1) / 2) : dim3(T, T);
+  k64_gemm<float, F32Gemm><<<grid, NT, 0, s>>>(g);
   return cudaGetLastError();
 }
 

@@ -27,34 +27,19 @@ __device__ __forceinline__ int exp_bound(double v) {
   return e;
 }
 
-// Row (COLS = false) or column (COLS = true) exponents of X (n x n, leading dimension ld).
-template <bool COLS>
-__global__ void k_oz_exp(const double* __restrict__ X, int n, int ld, int* __restrict__ e) {
+// Column exponents of X (operand rows = columns of X): each block owns a stripe of 32 columns
+// and walks every row (coalesced), so no atomics are needed.
+__global__ void k_oz_colexp(const double* __restrict__ X, int n, int ld, int* __restrict__ e) {
   __shared__ double red[8][33];
-  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  double cm = 0.0;
-  for (int r = ty; r < 32; r += 8) {
-    const int i = bi + r, j = bj + tx;
-    const double v = (i < n && j < n) ? fabs(X[(size_t)i * ld + j]) : 0.0;
-    if (COLS) {
-      cm = fmax(cm, v);
-    } else {
-      double m = v;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (tx == 0 && i < n && m > 0.0) atomicMax(&e[i], exp_bound(m));
-    }
-  }
-  if (COLS) {
-    red[ty][tx] = cm;
-    __syncthreads();
-    if (ty == 0) {
-      double m = red[0][tx];
-      for (int y = 1; y < 8; ++y) m = fmax(m, red[y][tx]);
-      const int j = bj + tx;
-      if (j < n && m > 0.0) atomicMax(&e[j], exp_bound(m));
-    }
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  double m = 0.0;
+  if (j < n)
+    for (int i = threadIdx.y; i < n; i += 8) m = fmax(m, fabs(X[(size_t)i * ld + j]));
+  red[threadIdx.y][threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < n) {
+    for (int y = 1; y < 8; ++y) m = fmax(m, red[y][threadIdx.x]);
+    e[j] = m > 0.0 ? exp_bound(m) : -2000000000;
   }
 }
 
@@ -124,55 +109,116 @@ __global__ void k_oz_slice(const double* __restrict__ X, int n, int ld, const in
   }
 }
 
+// Row slices of X (operand rows = rows of X): one warp per row finds the row's exponent and
+// then slices the row (two coalesced passes, the second from cache; no atomics).
+__global__ void k_oz_rowslice(const double* __restrict__ X, int n, int ld, int* __restrict__ e, int s, int b,
+                              uint16_t* __restrict__ out, int ld16, int Rp) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* xr = X + (size_t)row * ld;
+  double m = 0.0;
+  for (int c = lane; c < n; c += 32) m = fmax(m, fabs(xr[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int er = m > 0.0 ? exp_bound(m) : -2000000000;
+  if (lane == 0) e[row] = er;
+  const int T = s * b;
+  for (int c = lane; c < n; c += 32) {
+    long long F = (er > -1000) ? fixed_point(xr[c], er, T) : 0;
+    for (int p = 0; p < s; ++p) {
+      const int sh = T - b * (p + 1);
+      const long long a = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;
+      F -= a << sh;
+      out[((size_t)p * Rp + row) * ld16 + c] = __bfloat16_as_ushort(__float2bfloat16((float)a));
+    }
+  }
+}
+
 // Sum of the groups with the scales: val = 2^{eA_i + eB_j} 2^{-2b} sum_t 2^{-bt} T_t,
 // T_t = sum_c G[t * nch + c] (exact integers).  The leading groups t < k0 are summed exactly
 // as a 64-bit integer I = sum_{t<k0} T_t 2^{b(k0-1-t)}; the tail t >= k0, whose weight is
 // below 2^-29 of the leading term, in FP32; one FP64 addition joins them.
-// mode 0: out = val; mode 1: out += val; mode 2 (sym): d = I - val written to (i, j) and
-// (j, i), with the block's sum of d^2 (off-diagonal twice) in partials[block].
+// mode 0: out = val; mode 1: out += val; mode 2 (sym): d = I - val, with the block's sum of
+// d^2 (off-diagonal entries twice) in partials[block].  32 x 32 tiles (blockDim 32 x 8): with
+// sym only tiles on or above the diagonal run, and the mirrored tile is written through shared
+// memory so that both writes are coalesced.
 __global__ void k_oz_combine(const float* __restrict__ G, size_t gstride, int ld32, int s, int nch, int b,
                              const int* __restrict__ eA, const int* __restrict__ eB, int n, double* out, int ld64,
                              int mode, int sym, double* partials) {
+  __shared__ double tile[32][33];
   __shared__ double red[256];
-  const int j = blockIdx.x * 32 + threadIdx.x;
-  const int i = blockIdx.y * 8 + threadIdx.y;
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const bool active = !(sym && bj < bi);
   double ss = 0.0;
-  if (i < n && j < n && !(sym && j < i)) {
-    const size_t off = (size_t)i * ld32 + j;
-    int k0 = (29 + b - 1) / b;
-    if (k0 > s) k0 = s;
-    long long I = 0;
-    for (int t = 0; t < k0; ++t) {
-      int tt = 0;
-      for (int c = 0; c < nch; ++c) tt += __float2int_rn(G[(size_t)(t * nch + c) * gstride + off]);
-      I = (I << b) + tt;
+  int k0 = (29 + b - 1) / b;
+  if (k0 > s) k0 = s;
+  const float wb = ldexpf(1.0f, -b);
+  if (active) {
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      const int i = bi + r, j = bj + threadIdx.x;
+      double val = 0.0;
+      if (i < n && j < n) {
+        const size_t off = (size_t)i * ld32 + j;
+        long long I = 0;
+        for (int t = 0; t < k0; ++t) {
+          int tt = 0;
+          for (int c = 0; c < nch; ++c) tt += __float2int_rn(G[(size_t)(t * nch + c) * gstride + off]);
+          I = (I << b) + tt;
+        }
+        float F = 0.0f;
+        for (int t = s - 1; t >= k0; --t) {
+          float tt = 0.0f;
+          for (int c = 0; c < nch; ++c) tt += G[(size_t)(t * nch + c) * gstride + off];
+          F = (F + tt) * wb;
+        }
+        const int ea = eA[i], eb = eB[j];
+        val = (ea > -1000 && eb > -1000) ? ldexp((double)I + (double)F, ea + eb - 2 * b - b * (k0 - 1)) : 0.0;
+        if (mode == 2) {
+          val = (i == j ? 1.0 : 0.0) - val;
+          if (j >= i) ss += (i == j ? 1.0 : 2.0) * val * val;
+        }
+        double* o = out + (size_t)i * ld64 + j;
+        const bool own = !sym || j >= i;  // in a diagonal tile only the upper half is formed
+        if (own) {
+          if (mode == 1)
+            *o += val;
+          else
+            *o = val;
+        }
+      }
+      tile[r][threadIdx.x] = val;
     }
-    const float wb = ldexpf(1.0f, -b);
-    float F = 0.0f;
-    for (int t = s - 1; t >= k0; --t) {
-      float tt = 0.0f;
-      for (int c = 0; c < nch; ++c) tt += G[(size_t)(t * nch + c) * gstride + off];
-      F = (F + tt) * wb;
-    }
-    const int ea = eA[i], eb = eB[j];
-    const double val =
-        (ea > -1000 && eb > -1000) ? ldexp((double)I + (double)F, ea + eb - 2 * b - b * (k0 - 1)) : 0.0;
-    double* o = out + (size_t)i * ld64 + j;
-    if (mode == 2) {
-      const double d = (i == j ? 1.0 : 0.0) - val;
-      *o = d;
-      if (j > i) out[(size_t)j * ld64 + i] = d;
-      ss = (i == j ? 1.0 : 2.0) * d * d;
-    } else if (mode == 1) {
-      *o += val;
-      if (sym && j > i) out[(size_t)j * ld64 + i] += val;
-    } else {
-      *o = val;
-      if (sym && j > i) out[(size_t)j * ld64 + i] = val;
+    if (sym && bj > bi) {
+      // the (j, i) mirror of this off-diagonal tile, coalesced through shared memory
+      __syncthreads();
+      for (int r = threadIdx.y; r < 32; r += 8) {
+        const int oi = bj + r, oj = bi + threadIdx.x;
+        if (oi < n && oj < n) {
+          double* o = out + (size_t)oi * ld64 + oj;
+          if (mode == 1)
+            *o += tile[threadIdx.x][r];
+          else
+            *o = tile[threadIdx.x][r];
+        }
+      }
+    } else if (sym) {
+      // diagonal tile: mirror its upper half into its lower half
+      __syncthreads();
+      for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = bi + r, j = bj + threadIdx.x;
+        if (i < n && j < n && j < i) {
+          double* o = out + (size_t)i * ld64 + j;
+          if (mode == 1)
+            *o += tile[threadIdx.x][r];
+          else
+            *o = tile[threadIdx.x][r];
+        }
+      }
     }
   }
   if (mode == 2) {
-    const int tid = threadIdx.y * 32 + threadIdx.x;
     red[tid] = ss;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
@@ -231,12 +277,9 @@ cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, cudaS
 }
 
 cudaError_t launch_oz_exp(const double* X, int n, int ld, bool cols, int* e, cudaStream_t s) {
-  cudaMemsetAsync(e, 0x80, sizeof(int) * (size_t)n, s);  // very negative: all-zero rows stay marked
-  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-  if (cols)
-    k_oz_exp<true><<<grid, block, 0, s>>>(X, n, ld, e);
-  else
-    k_oz_exp<false><<<grid, block, 0, s>>>(X, n, ld, e);
+  // column exponents only: row exponents are found by the row slicing kernel itself
+  if (!cols) return cudaSuccess;
+  k_oz_colexp<<<(n + 31) / 32, dim3(32, 8), 0, s>>>(X, n, ld, e);
   return cudaGetLastError();
 }
 
@@ -244,18 +287,21 @@ cudaError_t launch_oz_slice(const double* X, int n, int ld, bool trans, const in
                             int ld16, int Rp, cudaStream_t s) {
   for (int p = 0; p < sl; ++p)  // padding rows n..Rp-1 of every slice must read as zero
     if (Rp > n) cudaMemsetAsync(out + ((size_t)p * Rp + n) * ld16, 0, sizeof(uint16_t) * (size_t)(Rp - n) * ld16, s);
-  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-  if (trans)
+  if (trans) {
+    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
     k_oz_slice<true><<<grid, block, 0, s>>>(X, n, ld, e, sl, b, out, ld16, Rp);
-  else
-    k_oz_slice<false><<<grid, block, 0, s>>>(X, n, ld, e, sl, b, out, ld16, Rp);
+  } else {
+    k_oz_rowslice<<<(n + 7) / 8, 256, 0, s>>>(X, n, ld, const_cast<int*>(e), sl, b, out, ld16, Rp);
+  }
   return cudaGetLastError();
 }
+
+int oz_combine_blocks(int n) { return ((n + 31) / 32) * ((n + 31) / 32); }
 
 cudaError_t launch_oz_combine(const float* G, size_t gstride, int ld32, int sl, int nch, int b, const int* eA,
                               const int* eB, int n, double* out, int ld64, int mode, bool sym, double* partials,
                               cudaStream_t s) {
-  dim3 grid((n + 31) / 32, (n + 7) / 8), block(32, 8);
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
   k_oz_combine<<<grid, block, 0, s>>>(G, gstride, ld32, sl, nch, b, eA, eB, n, out, ld64, mode, sym ? 1 : 0,
                                       partials);
   return cudaGetLastError();

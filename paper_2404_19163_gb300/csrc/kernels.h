@@ -30,6 +30,19 @@ struct F64Gemm {
 };
 int f64_num_blocks(int n, bool sym);
 cudaError_t launch_f64_gemm(const F64Gemm& g, cudaStream_t s);
+// The same product in FP32 (the paper's "single"); Err partials stay FP64.
+struct F32Gemm {
+  const float* A;
+  const float* B;
+  float* C;
+  const float* Add;
+  float* P;
+  double alpha, beta;
+  double* partials;
+  int n;
+  bool transA, sym, resid;
+};
+cudaError_t launch_f32_gemm(const F32Gemm& g, cudaStream_t s);
 
 // ----------------------------------------------------------------- elementwise / reductions (k_elem.cu)
 // st->gscale = 1/sqrt(max_i sum_j |S_ij|) (st->amax[0] is used as scratch).
@@ -81,6 +94,7 @@ cudaError_t launch_oz_combine(const float* G, size_t gstride, int ld32, int sl, 
                               const int* eB, int n, double* out, int ld64, int mode, bool sym, double* partials,
                               cudaStream_t s);
 int resid_from_x_blocks(int n);
+int oz_combine_blocks(int n);  // partials written by launch_oz_combine in mode 2
 // st->scale[scale_slot] = power of two s with st->amax[amax_slot] * s <= 2^14.
 cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, cudaStream_t s);
 // D = I - X (FP64), per-block sums of D_ij^2 into partials.

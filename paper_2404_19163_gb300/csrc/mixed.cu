@@ -194,8 +194,8 @@ static int refine_native(zfact_ctx* c, const double* S, double* Z64, int n, int 
 
 // Algorithm 3 with d = I - Z^T S Z and Z + Z Q formed to FP64 accuracy by error-free slicing on
 // the BF16 tensor cores; the polynomial's powers d^k (k >= 2) by FP16 hi/lo products.
-static int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o,
-                        int iters, int* ridx_out, zfact_info* inf) {
+int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o, int iters,
+                 int* ridx_out, zfact_info* inf) {
   int st = ZFACT_OK;
   double coef[8];
   coef[0] = 1.0;
@@ -498,6 +498,12 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f32_to_f64(Zm, n, ld, Za64, n, c->stream); }), "Z to FP64"))) return st;
   double* Z64 = Za64;
   int ridx = 0;
+  if (o.refine_steps <= 0 && !o.final_residual) {
+    // bulk only: no refinement and no FP64-accurate residual requested
+    *ridx_out = 0;
+    c->mixed_result = Z64;
+    return ZFACT_OK;
+  }
   if (o.refine_mode == ZFACT_R_OZAKI) {
     if ((st = refine_ozaki(c, S, Z64, n, order, o, iters, &ridx, inf))) return st;
   } else {

@@ -146,8 +146,9 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   if (!A64) return st;
   double* X64 = (double*)ctx_buf(c, "oz.X64", sizeof(double) * (size_t)n * n, &st);
   if (!X64) return st;
-  const int nb = resid_from_x_blocks(n);
-  double* partials = (double*)ctx_buf(c, "oz.partials", sizeof(double) * (size_t)nb, &st);
+  const int nb_fused = oz_combine_blocks(n), nb_sep = resid_from_x_blocks(n);
+  double* partials =
+      (double*)ctx_buf(c, "oz.partials", sizeof(double) * (size_t)(nb_fused > nb_sep ? nb_fused : nb_sep), &st);
   if (!partials) return st;
   // rows of Z^T = columns of Z
   if ((st = oz_make(c, "Zt", Z, n, n, true, kOzSlicesResid, &Zt))) return st;
@@ -168,6 +169,7 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
                        "resid from X")))
       return st;
   }
+  const int nb = fused ? nb_fused : nb_sep;
   return ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
                     return launch_finish_err(partials, nb, c->st_dev, idx, rule, tol, n, check_stop, c->stream);
                   }),

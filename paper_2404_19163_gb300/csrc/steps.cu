@@ -30,6 +30,21 @@ extern "C" int zfact_gemm(zfact_ctx* c, int precision, int64_t N, const double* 
     if ((st = ctx_cuda(c, launch_f64_gemm(g, c->stream), "f64 gemm"))) return st;
     return ctx_read_state(c);
   }
+  if (precision == ZFACT_P_FP32) {
+    // FP32 operands (rounded to nearest), FP32 CUDA-core product, FP64 result
+    float* A32 = (float*)ctx_buf(c, "g.A32", sizeof(float) * (size_t)n * n, &st);
+    if (!A32) return st;
+    float* B32 = (float*)ctx_buf(c, "g.B32", sizeof(float) * (size_t)n * n, &st);
+    if (!B32) return st;
+    float* C32 = (float*)ctx_buf(c, "g.C32", sizeof(float) * (size_t)n * n, &st);
+    if (!C32) return st;
+    if ((st = ctx_cuda(c, launch_f64_to_f32(A, n, n, A32, n, c->stream), "A32"))) return st;
+    if ((st = ctx_cuda(c, launch_f64_to_f32(B, n, n, B32, n, c->stream), "B32"))) return st;
+    F32Gemm g{A32, B32, C32, nullptr, nullptr, 0.0, 1.0, nullptr, n, false, false, false};
+    if ((st = ctx_cuda(c, launch_f32_gemm(g, c->stream), "f32 gemm"))) return st;
+    if ((st = ctx_cuda(c, launch_f32_to_f64(C32, n, n, C, n, c->stream), "C64"))) return st;
+    return ctx_read_state(c);
+  }
   const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
   const bool split = (precision == ZFACT_P_FP16_SPLIT || precision == ZFACT_P_BF16_SPLIT);
   if (!bf16 && precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT)

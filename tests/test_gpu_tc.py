@@ -99,14 +99,15 @@ def test_mixed_bf16_workload1(ctx):
     assert np.linalg.norm(Z @ Z.T - np.linalg.inv(S)) / np.linalg.norm(np.linalg.inv(S)) <= 1e-11
 
 
-@pytest.mark.parametrize("prec", ["bf16", "bf16_split", "fp16", "fp16_split"])
+@pytest.mark.parametrize("prec", ["bf16", "bf16_split", "fp16", "fp16_split", "fp32"])
 def test_mixed_bulk_history_tracks_fp64(ctx, prec):
     """Before the BF16 noise floor, Err_n of the mixed bulk follows the FP64 oracle's."""
     S = synth.cubic_overlap(n_side=8)
     n = S.shape[0]
     Zo, ho, it = oracle.refine(S, None, m=2, nmax=50, fixed_iters=2)
     r = ctx.refine(dev(S), None, order=2, precision=prec, fixed_iters=2, refine_steps=0)
-    u = {"bf16": 2.0 ** -8, "bf16_split": 2.0 ** -16, "fp16": 2.0 ** -11, "fp16_split": 2.0 ** -20}[prec]
+    u = {"bf16": 2.0 ** -8, "bf16_split": 2.0 ** -16, "fp16": 2.0 ** -11, "fp16_split": 2.0 ** -20,
+         "fp32": 2.0 ** -22}[prec]
     for k in range(3):
         assert abs(r.hist[k] - ho[k]) <= 8 * u * math.sqrt(n) + 1e-3 * ho[k], (k, r.hist, ho)
 
@@ -119,10 +120,10 @@ def test_mixed_higher_order(ctx, m):
 
 
 @pytest.mark.parametrize("n,prec", [(1, "bf16_split"), (7, "fp16_split"), (100, "bf16_split"), (129, "fp16"),
-                                    (383, "fp16_split")])
+                                    (383, "fp16_split"), (150, "fp32")])
 def test_mixed_ragged(ctx, n, prec):
     S, Q, lam = synth.householder_spd(n, seed=n)
-    r = ctx.refine(dev(S), None, order=2, precision=prec, tol=1e-12)
+    r = ctx.refine(dev(S), None, order=2, precision=prec, tol=1e-12, refine_steps=3)
     Z = r.Z.cpu().numpy()
     assert np.linalg.norm(np.eye(n) - Z.T @ S @ Z) / math.sqrt(n) <= 1e-12
 
@@ -165,3 +166,27 @@ def test_fp16_split_bulk_floor_below_bf16(ctx):
     b1 = min(r1.hist[:r1.info["iters"] + 1])
     b2 = min(r2.hist[:r2.info["iters"] + 1])
     assert b2 < 1e-2 * b1, (r1.hist, r2.hist)
+
+
+@pytest.mark.parametrize("n", [64, 129, 300])
+def test_fp32_gemm_parity(ctx, n):
+    """The paper's "single" product: FP32 operands, FP32 CUDA-core accumulation."""
+    g = np.random.default_rng(40 + n)
+    A = g.standard_normal((n, n))
+    B = g.standard_normal((n, n))
+    C = ctx.gemm(dev(A), dev(B), "fp32").cpu().numpy()
+    A32 = A.astype(np.float32).astype(np.float64)
+    B32 = B.astype(np.float32).astype(np.float64)
+    ref = A32 @ B32
+    bound = n * 2.0 ** -23 * (np.abs(A32) @ np.abs(B32))
+    assert np.all(np.abs(C - ref) <= bound)
+
+
+def test_fp32_single_path_reaches_its_floor_and_refines(ctx):
+    S, Q, lam = synth.householder_spd(200, seed=31)
+    r = ctx.refine(dev(S), None, order=2, precision="fp32")
+    _, e = oracle.residual(S, r.Z.cpu().numpy())
+    assert e / math.sqrt(200) <= 1e-5 and abs(r.info["resid_f"] - e) <= 1e-12
+    r2 = ctx.refine(dev(S), None, order=2, precision="fp32", refine_steps=2, tol=1e-12)
+    _, e2 = oracle.residual(S, r2.Z.cpu().numpy())
+    assert e2 / math.sqrt(200) <= 1e-12
