@@ -397,19 +397,42 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
   kstats_flush(c);
   const int bulk_launches = c->launches;
 
-  // ---- FP64-accurate final residual of every returned Z (error-free slicing)
+  // ---- FP64-accurate final residual of every returned Z (error-free slicing), kLanes instances
+  // at a time on concurrent streams (each lane with its own workspace and Err slot)
   std::vector<double> resid(count, NAN);
   if (o.final_residual) {
-    for (int j = 0; j < count; ++j) {
-      const int i = order_idx[j];
-      double* D64 = (double*)ctx_buf(c, "D64", sizeof(double) * (size_t)max_n * max_n, &st);
-      if (!D64) return st;
-      cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
-      if ((st = oz_prepare_S(c, S[i], n[i]))) return st;
-      if ((st = oz_residual(c, Z[i], D64, n[i], 0, 0, 0.0, 0))) return st;
+    const int L = zfact_ctx::kLanes;
+    for (int l = 0; l < L; ++l)
+      if (!c->lane_stream[l] && cudaStreamCreateWithFlags(&c->lane_stream[l], cudaStreamNonBlocking) != cudaSuccess)
+        return ctx_fail(c, ZFACT_ERR_CUDA, "lane stream");
+    cudaEvent_t fork = ev_get(c);
+    cudaEvent_t join[zfact_ctx::kLanes];
+    for (int l = 0; l < L; ++l) join[l] = ev_get(c);
+    cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
+    for (int j0 = 0; j0 < count; j0 += L) {
+      cudaEventRecord(fork, c->stream);
+      const int nl = std::min(L, count - j0);
+      for (int l = 0; l < nl; ++l) {
+        const int i = order_idx[j0 + l];  // largest first: a lane's buffers never have to grow
+        c->lane = l;
+        cudaStreamWaitEvent(c->lane_stream[l], fork, 0);
+        double* D64 = (double*)ctx_buf(c, lane_name(c, "D64").c_str(), sizeof(double) * (size_t)n[i] * n[i], &st);
+        if (!D64) {
+          c->lane = -1;
+          return st;
+        }
+        st = oz_prepare_S(c, S[i], n[i]);
+        if (!st) st = oz_residual(c, Z[i], D64, n[i], l, 0, 0.0, 0);
+        cudaEventRecord(join[l], c->lane_stream[l]);
+        c->lane = -1;
+        if (st) return st;
+      }
+      for (int l = 0; l < nl; ++l) cudaStreamWaitEvent(c->stream, join[l], 0);
       if ((st = ctx_read_state(c))) return st;
-      resid[i] = c->st_host->hist[0];
+      for (int l = 0; l < nl; ++l) resid[order_idx[j0 + l]] = c->st_host->hist[l];
     }
+    c->ev_pool.push_back(fork);
+    for (int l = 0; l < L; ++l) c->ev_pool.push_back(join[l]);
   }
   cudaEventRecord(c->ev1, c->stream);
   cudaEventSynchronize(c->ev1);

@@ -189,6 +189,8 @@ extern "C" void zfact_destroy(zfact_ctx* c) {
   if (c->st_host) cudaFreeHost(c->st_host);
   cudaEventDestroy(c->ev0);
   cudaEventDestroy(c->ev1);
+  for (int l = 0; l < zfact_ctx::kLanes; ++l)
+    if (c->lane_stream[l]) cudaStreamDestroy(c->lane_stream[l]);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }

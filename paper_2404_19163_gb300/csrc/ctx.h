@@ -46,6 +46,11 @@ struct zfact_ctx {
   std::vector<KStat> kstats;
   std::vector<PendingEv> pending;
   std::vector<cudaEvent_t> ev_pool;
+  // concurrent lanes (batched verification): while lane >= 0, the sliced-product driver issues
+  // its work on lane_stream[lane] and uses workspace buffers suffixed with the lane
+  static constexpr int kLanes = 8;
+  cudaStream_t lane_stream[kLanes] = {};
+  int lane = -1;
   // encoded TMA descriptors keyed by (address, rows, cols, ld, box rows, type)
   std::map<std::string, CUtensorMap> map_cache;
   // batched mode
@@ -59,14 +64,19 @@ void kstats_flush(zfact_ctx* c);  // stream must be idle
 
 // Launch `f` (returning cudaError_t) as `count` kernels of family `name` with the given
 // algorithmic FLOPs / bytes; bracketed by events when profiling is on.
+inline cudaStream_t cur_stream(zfact_ctx* c) { return c->lane >= 0 ? c->lane_stream[c->lane] : c->stream; }
+inline std::string lane_name(zfact_ctx* c, const char* name) {
+  return c->lane >= 0 ? std::string(name) + ".L" + std::to_string(c->lane) : std::string(name);
+}
+
 template <class F>
 cudaError_t klaunch(zfact_ctx* c, const char* name, double flops, double bytes, int count, F&& f) {
   c->launches += count;
   if (!c->profiling) return f();
   cudaEvent_t a = ev_get(c), b = ev_get(c);
-  cudaEventRecord(a, c->stream);
+  cudaEventRecord(a, cur_stream(c));
   cudaError_t e = f();
-  cudaEventRecord(b, c->stream);
+  cudaEventRecord(b, cur_stream(c));
   c->pending.push_back(PendingEv{kstat_id(c, name), a, b, flops, bytes, count});
   return e;
 }

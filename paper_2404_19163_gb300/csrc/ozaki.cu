@@ -41,7 +41,8 @@ int chunk_kb(int s) {
 int oz_make(zfact_ctx* c, const char* name, const double* X, int n, int ldx, bool trans, int s, OzOperand* op) {
   int st = ZFACT_OK;
   const int ld16 = ld16_of(n), Rp = rp_of(n);
-  std::string ns = std::string("oz.") + name + ".sl", ne = std::string("oz.") + name + ".e";
+  std::string ns = lane_name(c, (std::string("oz.") + name + ".sl").c_str()),
+              ne = lane_name(c, (std::string("oz.") + name + ".e").c_str());
   op->sl = (uint16_t*)ctx_buf(c, ns.c_str(), sizeof(uint16_t) * (size_t)s * Rp * ld16, &st);
   if (!op->sl) return st;
   op->e = (int*)ctx_buf(c, ne.c_str(), sizeof(int) * (size_t)n, &st);
@@ -49,9 +50,9 @@ int oz_make(zfact_ctx* c, const char* name, const double* X, int n, int ldx, boo
   op->Rp = Rp;
   op->s = s;
   if ((st = ctx_cuda(c, klaunch(c, "oz_slice", 0, 8.0 * n * n * 2 + 2.0 * s * n * n, 2, [&] {
-                       cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, c->stream);
+                       cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, cur_stream(c));
                        if (e != cudaSuccess) return e;
-                       return launch_oz_slice(X, n, ldx, trans, op->e, s, kOzBits, op->sl, ld16, Rp, c->stream);
+                       return launch_oz_slice(X, n, ldx, trans, op->e, s, kOzBits, op->sl, ld16, Rp, cur_stream(c));
                      }),
                      "oz slice")))
     return st;
@@ -71,7 +72,7 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
   int nch_b = (int)(kOzGBudget / (slot_bytes * s));
   if (nch_b < 1) nch_b = 1;
   if (nch_b > nch_total) nch_b = nch_total;
-  float* G = (float*)ctx_buf(c, "oz.G", slot_bytes * s * nch_b, &st);
+  float* G = (float*)ctx_buf(c, lane_name(c, "oz.G").c_str(), slot_bytes * s * nch_b, &st);
   if (!G) return st;
   TcMaps maps;
   memset(&maps, 0, sizeof(maps));
@@ -107,7 +108,7 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
     const double flops = pairs * 2.0 * n * n * kk * (sym ? 0.5 : 1.0);
     const double bytes = pairs * 2.0 * 2.0 * n * kk + 4.0 * s * nch * (double)n * n;
     if ((st = ctx_cuda(c, klaunch(c, "tc_gemm.ozaki", flops, bytes, 1,
-                                  [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, c->stream); }),
+                                  [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, cur_stream(c)); }),
                        "tcgen05 ozaki")))
       return st;
     int md = (c0 == 0) ? mode : 1;
@@ -119,7 +120,7 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
     }
     if ((st = ctx_cuda(c, klaunch(c, "oz_combine", 0, 4.0 * s * nch * n * (double)n + 16.0 * n * n, 1, [&] {
                          return launch_oz_combine(G, (size_t)n * ld, ld, s, nch, kOzBits, A.e, B.e, n, out, ld64, md,
-                                                  sym, partials, c->stream);
+                                                  sym, partials, cur_stream(c));
                        }),
                        "oz combine")))
       return st;
@@ -138,17 +139,18 @@ int oz_prepare_S(zfact_ctx* c, const double* S, int n) {
 int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop) {
   int st = ZFACT_OK;
   OzOperand Sop, Zt, At;
-  Sop.sl = (uint16_t*)ctx_buf(c, "oz.S.sl", 0, &st);
-  Sop.e = (int*)ctx_buf(c, "oz.S.e", 0, &st);
+  Sop.sl = (uint16_t*)ctx_buf(c, lane_name(c, "oz.S.sl").c_str(), 0, &st);
+  Sop.e = (int*)ctx_buf(c, lane_name(c, "oz.S.e").c_str(), 0, &st);
   Sop.Rp = rp_of(n);
   Sop.s = kOzSlicesResid;
-  double* A64 = (double*)ctx_buf(c, "oz.At64", sizeof(double) * (size_t)n * n, &st);
+  double* A64 = (double*)ctx_buf(c, lane_name(c, "oz.At64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!A64) return st;
-  double* X64 = (double*)ctx_buf(c, "oz.X64", sizeof(double) * (size_t)n * n, &st);
+  double* X64 = (double*)ctx_buf(c, lane_name(c, "oz.X64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!X64) return st;
   const int nb_fused = oz_combine_blocks(n), nb_sep = resid_from_x_blocks(n);
   double* partials =
-      (double*)ctx_buf(c, "oz.partials", sizeof(double) * (size_t)(nb_fused > nb_sep ? nb_fused : nb_sep), &st);
+      (double*)ctx_buf(c, lane_name(c, "oz.partials").c_str(),
+                       sizeof(double) * (size_t)(nb_fused > nb_sep ? nb_fused : nb_sep), &st);
   if (!partials) return st;
   // rows of Z^T = columns of Z
   if ((st = oz_make(c, "Zt", Z, n, n, true, kOzSlicesResid, &Zt))) return st;
@@ -161,17 +163,17 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   if ((st = oz_product(c, Zt, At, n, true, D, n, 0, partials, &fused))) return st;
   if (!fused) {
     // several K-chunk batches: the combine accumulated X into D; form d = I - X from it
-    if ((st = ctx_cuda(c, cudaMemcpyAsync(Xout, D, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, c->stream),
+    if ((st = ctx_cuda(c, cudaMemcpyAsync(Xout, D, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, cur_stream(c)),
                        "X copy")))
       return st;
     if ((st = ctx_cuda(c, klaunch(c, "resid_from_x", 2.0 * n * n, 16.0 * n * n, 1,
-                                  [&] { return launch_resid_from_x(Xout, D, n, partials, c->stream); }),
+                                  [&] { return launch_resid_from_x(Xout, D, n, partials, cur_stream(c)); }),
                        "resid from X")))
       return st;
   }
   const int nb = fused ? nb_fused : nb_sep;
   return ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
-                    return launch_finish_err(partials, nb, c->st_dev, idx, rule, tol, n, check_stop, c->stream);
+                    return launch_finish_err(partials, nb, c->st_dev, idx, rule, tol, n, check_stop, cur_stream(c));
                   }),
                   "finish err");
 }
