@@ -378,23 +378,28 @@ def run_case_residual(args):
     print(json.dumps({"case": "residual_ozaki", "N": n, "ms": round(ms, 3), "err": err}), flush=True)
 
 
-def run_batched(args):
+def run_batched(args, rank=0, ws=1, local=0):
     """Workload 4: 128 cluster overlaps, N_i ~ U[256, 3072], frames of a trajectory (sites
     displaced by N(0, 0.02^2) per frame); frame 0 is a cold start (untimed), frames 1..F are
-    warm-started from the previous frame's Z and timed, one zfact_refine_batched call each."""
+    warm-started from the previous frame's Z and timed, one zfact_refine_batched call each.
+    With several ranks the instances are sharded (greedy by N^3, no data-path collective);
+    the frame time is the maximum over ranks (strong scaling: the batch is fixed)."""
     import numpy as np
     import torch
-    from paper_2404_19163_gb300 import Context, synth, build as zbuild
+    from paper_2404_19163_gb300 import Context, synth, shard, build as zbuild
     zbuild.build()
     count = args.batch_count
-    sizes, frame = synth.trajectory(count=count)
+    all_sizes, frame = synth.trajectory(count=count)
+    mine = shard.mine(list(all_sizes), rank, ws) if ws > 1 else list(range(count))
+    sizes = [int(all_sizes[i]) for i in mine]
     frames = max(2, args.steps + 1)
     stream = torch.cuda.Stream()
-    ctx = Context(0, stream=stream)
+    ctx = Context(local, stream=stream)
     prec = args.precision
 
     def mats(f):
-        return [synth.gaussian_overlap_torch(p) for p in frame.positions(f)]
+        pos = frame.positions(f)
+        return [synth.gaussian_overlap_torch(pos[i]) for i in mine]
 
     S0 = mats(0)
     Zp, h, infos, st = ctx.refine_batched(S0, None, precision=prec)
@@ -413,7 +418,7 @@ def run_batched(args):
             Zf, h, infos, st = ctx.refine_batched(Sf, Zp, precision=prec)
             e1.record(stream)
             e1.synchronize()
-            times.append(e0.elapsed_time(e1))
+            times.append(barrier_max(e0.elapsed_time(e1), ws))
             iters.append([i["iters"] for i in infos])
             resid.append(max(i["resid_f"] / math.sqrt(n) for i, n in zip(infos, sizes)))
             launches += infos[0]["launches"]
@@ -423,12 +428,15 @@ def run_batched(args):
     tc = [k for k in stats if k["name"].startswith("tc_gemm.b_")]
     tc_ms = sum(k["ms"] for k in tc)
     tc_fl = sum(k["flops"] for k in tc)
-    sum_n3 = float(np.sum(np.asarray(sizes, dtype=np.float64) ** 3))
+    sum_n3 = float(np.sum(np.asarray(all_sizes, dtype=np.float64) ** 3))
+    if rank != 0:
+        return
     print(json.dumps({
         "workload": "batched_trajectory_128_clusters_N256-3072_warm_frames",
         "metric": "ms per frame (all 128 factorizations, bulk + FP64-accurate final residual)",
         "value": round(statistics.mean(times), 3), "unit": "ms", "frames_timed": len(times),
-        "precision": prec, "sum_N": int(np.sum(sizes)), "sum_N3": sum_n3,
+        "n_gpus": ws, "scaling": "strong", "higher_is_better": False,
+        "precision": prec, "sum_N": int(np.sum(all_sizes)), "sum_N3": sum_n3,
         "cold_iters_mean": float(np.mean(cold_iters)),
         "warm_iters_mean": float(np.mean(iters)), "warm_iters_max": int(np.max(iters)),
         "max_resid_over_sqrtN": max(resid), "gpu_launches": launches,
@@ -515,7 +523,11 @@ def main():
         run_case_residual(args)
         return
     if args.workload == "batched":
-        run_batched(args)
+        rank, ws, local = dist_setup()
+        run_batched(args, rank, ws, local)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
     if args.workload == "ill":
         run_ill(args)
