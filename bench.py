@@ -515,7 +515,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, choices=[None, "residual"])
     ap.add_argument("--workload", default="single", choices=["single", "batched", "ill"])
-    ap.add_argument("--tol-ill", type=float, default=2e-12)  # 10x the FP64 path's 1.86e-13 on this input
+    ap.add_argument("--tol-ill", type=float, default=1e-12)
     ap.add_argument("--fp64-comparator", action="store_true")
     ap.add_argument("--batch-count", type=int, default=128)
     args = ap.parse_args()

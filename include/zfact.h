@@ -23,8 +23,14 @@
  *   - Scalar outputs (hist, info, status arrays, scale, order) are HOST pointers.
  *   - The caller owns every pointer it passes.  The context owns its device
  *     workspace, grows it on demand and frees it in zfact_destroy.
- *   - Work is ordered on the context's stream.  Every zfact_refine* call
- *     synchronises that stream before it returns.
+ *   - Work is ordered on the context's stream.  Every call that takes a
+ *     context synchronises that stream before it returns, so outputs are
+ *     complete on return.  Device inputs must be complete when the context's
+ *     stream reaches the call: the stream the context creates (cuda_stream
+ *     NULL in zfact_create) is a blocking stream, ordered after work on the
+ *     legacy default stream; inputs written on any other stream are the
+ *     caller's to order (synchronise that stream, or create the context on
+ *     it).  An input read while its producer still runs is silently wrong.
  *   - Nothing is thrown across the ABI.  Each call returns a zfact_status;
  *     zfact_last_error() returns a message for the last failure on a context.
  *     On failure, outputs are unspecified except info->hist_len / iters,

@@ -159,7 +159,9 @@ extern "C" int zfact_create(zfact_ctx** out, int device, void* stream) {
     c->stream = (cudaStream_t)stream;
     c->own_stream = false;
   } else {
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    // a blocking stream: its work is ordered after the legacy default stream's, where
+    // most callers produce their device inputs
+    if (cudaStreamCreate(&c->stream) != cudaSuccess) {
       delete c;
       return ZFACT_ERR_CUDA;
     }

@@ -49,6 +49,7 @@ struct zfact_ctx {
   // concurrent lanes (batched verification): while lane >= 0, the sliced-product driver issues
   // its work on lane_stream[lane] and uses workspace buffers suffixed with the lane
   static constexpr int kLanes = 8;
+  int oz_s = 9;  // slices per operand of the current residual products
   cudaStream_t lane_stream[kLanes] = {};
   int lane = -1;
   // encoded TMA descriptors keyed by (address, rows, cols, ld, box rows, type)
@@ -97,7 +98,8 @@ int f64_poly(zfact_ctx* c, const double* D, double* Q, double* P, double* P2, in
 int f64_update(zfact_ctx* c, const double* Z, const double* Q, double* Zn, int n);
 
 // FP64-accurate products by error-free slicing (ozaki.cu)
-int oz_prepare_S(zfact_ctx* c, const double* S, int n);
+int oz_slices_for(double zmax, double g_hi);
+int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s = 0);
 int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop);
 int oz_update(zfact_ctx* c, double* Z, const double* Q, int n);
 

@@ -27,6 +27,41 @@ __device__ __forceinline__ int exp_bound(double v) {
   return e;
 }
 
+// The same for T > 62 bits (more than ten 6-bit slices): a 128-bit fixed point.
+__device__ __forceinline__ __int128 fixed_point128(double x, int e, int T) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  if (eb == 0 && m == 0) return 0;
+  int E;
+  if (eb == 0) {
+    E = -1074;
+  } else {
+    m |= 1ull << 52;
+    E = eb - 1075;
+  }
+  const int sh = E - e + T;
+  __int128 F;
+  if (sh >= 0)
+    F = (__int128)m << (sh < 74 ? sh : 74);
+  else if (sh > -63)
+    F = (__int128)((m + (1ull << (-sh - 1))) >> (-sh));
+  else
+    F = 0;
+  return (bits >> 63) ? -F : F;
+}
+
+// Digits of a fixed-point row value: digit p is the next b bits, rounded to nearest.
+template <typename I>
+__device__ __forceinline__ void slice_digits(I F, int T, int s, int b, uint16_t* out, size_t stride) {
+  for (int p = 0; p < s; ++p) {
+    const int sh = T - b * (p + 1);
+    const I a = sh > 0 ? ((F + ((I)1 << (sh - 1))) >> sh) : F;
+    F -= a << sh;
+    out[(size_t)p * stride] = __bfloat16_as_ushort(__float2bfloat16((float)(long long)a));
+  }
+}
+
 // Column exponents of X (operand rows = columns of X): each block owns a stripe of 32 columns
 // and walks every row (coalesced), so no atomics are needed.
 __global__ void k_oz_colexp(const double* __restrict__ X, int n, int ld, int* __restrict__ e) {
@@ -99,13 +134,12 @@ __global__ void k_oz_slice(const double* __restrict__ X, int n, int ld, const in
     }
     if (row >= n || col >= n) continue;
     const int er = e[row];
-    long long F = (er > -1000) ? fixed_point(x, er, T) : 0;
-    for (int p = 0; p < s; ++p) {
-      const int sh = T - b * (p + 1);
-      const long long a = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;
-      F -= a << sh;
-      out[((size_t)p * Rp + row) * ld16 + col] = __bfloat16_as_ushort(__float2bfloat16((float)a));
-    }
+    uint16_t* o = out + (size_t)row * ld16 + col;
+    const size_t stride = (size_t)Rp * ld16;
+    if (T <= 62)
+      slice_digits<long long>((er > -1000) ? fixed_point(x, er, T) : 0, T, s, b, o, stride);
+    else
+      slice_digits<__int128>((er > -1000) ? fixed_point128(x, er, T) : 0, T, s, b, o, stride);
   }
 }
 
@@ -124,21 +158,25 @@ __global__ void k_oz_rowslice(const double* __restrict__ X, int n, int ld, int* 
   const int er = m > 0.0 ? exp_bound(m) : -2000000000;
   if (lane == 0) e[row] = er;
   const int T = s * b;
+  const size_t stride = (size_t)Rp * ld16;
   for (int c = lane; c < n; c += 32) {
-    long long F = (er > -1000) ? fixed_point(xr[c], er, T) : 0;
-    for (int p = 0; p < s; ++p) {
-      const int sh = T - b * (p + 1);
-      const long long a = sh > 0 ? ((F + (1ll << (sh - 1))) >> sh) : F;
-      F -= a << sh;
-      out[((size_t)p * Rp + row) * ld16 + c] = __bfloat16_as_ushort(__float2bfloat16((float)a));
-    }
+    uint16_t* o = out + (size_t)row * ld16 + c;
+    if (T <= 62)
+      slice_digits<long long>((er > -1000) ? fixed_point(xr[c], er, T) : 0, T, s, b, o, stride);
+    else
+      slice_digits<__int128>((er > -1000) ? fixed_point128(xr[c], er, T) : 0, T, s, b, o, stride);
   }
 }
 
 // Sum of the groups with the scales: val = 2^{eA_i + eB_j} 2^{-2b} sum_t 2^{-bt} T_t,
-// T_t = sum_c G[t * nch + c] (exact integers).  The leading groups t < k0 are summed exactly
-// as a 64-bit integer I = sum_{t<k0} T_t 2^{b(k0-1-t)}; the tail t >= k0, whose weight is
-// below 2^-29 of the leading term, in FP32; one FP64 addition joins them.
+// T_t = sum_c G[t * nch + c] (exact integers, |T_t| < 2^30).  Two 64-bit integers hold the
+// groups exactly: I = sum_{t<k0} T_t 2^{b(k0-1-t)} and J = sum_{k0<=t<k1} T_t 2^{b(k1-1-t)}
+// (each below 2^55), so every group whose weight is above 2^-(b k1) ~ 2^-60 of the leading
+// term is exact; only the tail t >= k1 is summed in FP32.  The scale 2^{eA_i + eB_j} belongs to
+// the largest entries of row i and column j, so an inexact group here would cost a fixed
+// fraction of |Z|^T |S Z| rather than of the result: with ill-conditioned Z, where
+// I - Z^T S Z cancels by many orders, the sum has to stay exact well past the 53 bits of the
+// result.  Two FP64 roundings join I, J and the tail.
 // mode 0: out = val; mode 1: out += val; mode 2 (sym): d = I - val, with the block's sum of
 // d^2 (off-diagonal entries twice) in partials[block].  32 x 32 tiles (blockDim 32 x 8): with
 // sym only tiles on or above the diagonal run, and the mirrored tile is written through shared
@@ -154,6 +192,8 @@ __global__ void k_oz_combine(const float* __restrict__ G, size_t gstride, int ld
   double ss = 0.0;
   int k0 = (29 + b - 1) / b;
   if (k0 > s) k0 = s;
+  int k1 = k0 + (29 + b - 1) / b;
+  if (k1 > s) k1 = s;
   const float wb = ldexpf(1.0f, -b);
   if (active) {
     for (int r = threadIdx.y; r < 32; r += 8) {
@@ -161,20 +201,26 @@ __global__ void k_oz_combine(const float* __restrict__ G, size_t gstride, int ld
       double val = 0.0;
       if (i < n && j < n) {
         const size_t off = (size_t)i * ld32 + j;
-        long long I = 0;
-        for (int t = 0; t < k0; ++t) {
-          int tt = 0;
+        long long I = 0, J = 0;
+        for (int t = 0; t < k1; ++t) {
+          long long tt = 0;
           for (int c = 0; c < nch; ++c) tt += __float2int_rn(G[(size_t)(t * nch + c) * gstride + off]);
-          I = (I << b) + tt;
+          if (t < k0)
+            I = I * (1ll << b) + tt;
+          else
+            J = J * (1ll << b) + tt;
         }
         float F = 0.0f;
-        for (int t = s - 1; t >= k0; --t) {
+        for (int t = s - 1; t >= k1; --t) {
           float tt = 0.0f;
           for (int c = 0; c < nch; ++c) tt += G[(size_t)(t * nch + c) * gstride + off];
           F = (F + tt) * wb;
         }
         const int ea = eA[i], eb = eB[j];
-        val = (ea > -1000 && eb > -1000) ? ldexp((double)I + (double)F, ea + eb - 2 * b - b * (k0 - 1)) : 0.0;
+        if (ea > -1000 && eb > -1000) {
+          const int e0 = ea + eb - 2 * b - b * (k0 - 1), e1 = ea + eb - 2 * b - b * (k1 - 1);
+          val = ldexp((double)I, e0) + ldexp((double)J + (double)F, e1);
+        }
         if (mode == 2) {
           val = (i == j ? 1.0 : 0.0) - val;
           if (j >= i) ss += (i == j ? 1.0 : 2.0) * val * val;

@@ -212,7 +212,17 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
   Mat16 Dr, Pr;
   if ((st = alloc16(c, "D16r", n, ld, true, &Dr))) return st;
   if (order > 2 && (st = alloc16(c, "P16r", n, ld, true, &Pr))) return st;
-  if ((st = oz_prepare_S(c, S, n))) return st;
+  // slice count from the dynamic range of Z and S (see oz_slices_for)
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 3, [&] {
+                       cudaError_t e = launch_gershgorin(S, n, c->st_dev, c->stream);
+                       if (e == cudaSuccess) e = launch_amax_f64(Z64, n, c->st_dev, 2, c->stream);
+                       return e;
+                     }),
+                     "dynamic range")))
+    return st;
+  if ((st = ctx_read_state(c))) return st;
+  const int s_res = oz_slices_for(c->st_host->amax[2], c->st_host->amax[0]);
+  if ((st = oz_prepare_S(c, S, n, s_res))) return st;
   int ridx = 0, idx = iters;
   for (int r = 0; r <= o.refine_steps; ++r) {
     ++idx;

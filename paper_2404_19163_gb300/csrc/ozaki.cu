@@ -15,8 +15,9 @@ using namespace zf;
 namespace {
 
 constexpr int kOzBits = 6;             // bits per slice
-constexpr int kOzSlicesResid = 9;      // 54 bits: residual products
+constexpr int kOzSlicesResid = 9;      // 54 bits: residual products of a well-scaled Z
 constexpr int kOzSlicesUpdate = 8;     // 48 bits: Z Q (its result is a small correction)
+constexpr int kOzSlicesMax = 14;
 constexpr size_t kOzGBudget = (size_t)6 << 30;  // bytes of FP32 group partials per launch
 
 struct OzOperand {
@@ -130,9 +131,23 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
 
 }  // namespace
 
-int oz_prepare_S(zfact_ctx* c, const double* S, int n) {
+// Slices per operand for FP64-level accuracy.  Row-scaled slicing is accurate relative to the
+// row maxima: an entry of Z^T S Z carries an error ~ 2^(-b s) max|Z|^2 g_hi (g_hi the largest
+// absolute row sum of S) where FP64 arithmetic errs by ~ 2^-53 |X_ij| ~ 2^-53.  So b s is made
+// at least 53 + log2(max|Z|^2 g_hi) (9 slices for a well-scaled Z, more for an ill-conditioned S).
+int oz_slices_for(double zmax, double g_hi) {
+  double extra = log2(zmax * zmax * g_hi);
+  if (!(extra > 0)) extra = 0;
+  int s = (int)ceil((53.0 + extra) / kOzBits);
+  if (s < kOzSlicesResid) s = kOzSlicesResid;
+  if (s > kOzSlicesMax) s = kOzSlicesMax;
+  return s;
+}
+
+int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s) {
   OzOperand op;
-  return oz_make(c, "S", S, n, n, false, kOzSlicesResid, &op);
+  c->oz_s = s > 0 ? s : kOzSlicesResid;
+  return oz_make(c, "S", S, n, n, false, c->oz_s, &op);
 }
 
 // d = I - Z^T S Z to FP64 accuracy; Err -> hist[idx].  oz_prepare_S must have run for this S.
@@ -142,7 +157,7 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   Sop.sl = (uint16_t*)ctx_buf(c, lane_name(c, "oz.S.sl").c_str(), 0, &st);
   Sop.e = (int*)ctx_buf(c, lane_name(c, "oz.S.e").c_str(), 0, &st);
   Sop.Rp = rp_of(n);
-  Sop.s = kOzSlicesResid;
+  Sop.s = c->oz_s;
   double* A64 = (double*)ctx_buf(c, lane_name(c, "oz.At64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!A64) return st;
   double* X64 = (double*)ctx_buf(c, lane_name(c, "oz.X64").c_str(), sizeof(double) * (size_t)n * n, &st);
@@ -153,10 +168,10 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
                        sizeof(double) * (size_t)(nb_fused > nb_sep ? nb_fused : nb_sep), &st);
   if (!partials) return st;
   // rows of Z^T = columns of Z
-  if ((st = oz_make(c, "Zt", Z, n, n, true, kOzSlicesResid, &Zt))) return st;
+  if ((st = oz_make(c, "Zt", Z, n, n, true, Sop.s, &Zt))) return st;
   // A^T = Z^T S  (S symmetric: B operand rows are rows of S)
   if ((st = oz_product(c, Zt, Sop, n, false, A64, n, 0))) return st;
-  if ((st = oz_make(c, "At", A64, n, n, false, kOzSlicesResid, &At))) return st;
+  if ((st = oz_make(c, "At", A64, n, n, false, Sop.s, &At))) return st;
   // X = Z^T A = Z^T (A^T)^T, symmetric tiles; d = I - X fused into the combine when possible
   bool fused = false;
   double* Xout = X64;
@@ -182,7 +197,8 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
 int oz_update(zfact_ctx* c, double* Z, const double* Q, int n) {
   int st = ZFACT_OK;
   OzOperand Zr, Qr;
-  if ((st = oz_make(c, "Zr", Z, n, n, false, kOzSlicesUpdate, &Zr))) return st;
-  if ((st = oz_make(c, "Qr", Q, n, n, false, kOzSlicesUpdate, &Qr))) return st;
+  const int su = c->oz_s - 1 > kOzSlicesUpdate ? c->oz_s - 1 : kOzSlicesUpdate;
+  if ((st = oz_make(c, "Zr", Z, n, n, false, su, &Zr))) return st;
+  if ((st = oz_make(c, "Qr", Q, n, n, false, su, &Qr))) return st;
   return oz_product(c, Zr, Qr, n, false, Z, n, 1);
 }

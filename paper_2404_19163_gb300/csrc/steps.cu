@@ -113,7 +113,11 @@ extern "C" int zfact_residual(zfact_ctx* c, int mode, const double* S, const dou
   }
   cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
   if (mode == ZFACT_R_OZAKI) {
-    if ((st = oz_prepare_S(c, S, n))) return st;
+    // slice count from the dynamic range of Z and S, as in the refinement
+    if ((st = ctx_cuda(c, launch_gershgorin(S, n, c->st_dev, c->stream), "gershgorin"))) return st;
+    if ((st = ctx_cuda(c, launch_amax_f64(Z, n, c->st_dev, 2, c->stream), "amax Z"))) return st;
+    if ((st = ctx_read_state(c))) return st;
+    if ((st = oz_prepare_S(c, S, n, oz_slices_for(c->st_host->amax[2], c->st_host->amax[0])))) return st;
     if ((st = oz_residual(c, Z, Dw, n, 0, 0, 0.0, 0))) return st;
   } else if ((st = f64_residual(c, S, Z, A64, Dw, n, 0, 0, 0.0, 0))) {
     return st;

@@ -186,6 +186,24 @@ class Context:
         if rc not in allow:
             raise ZfactError(rc, self.last_error())
 
+    @staticmethod
+    def _ready(*objs):
+        """Wait for the current torch stream of every CUDA tensor passed to a call.
+
+        The library queues its work on the context's stream, which is not ordered after the
+        stream torch wrote the inputs on (nor after torch work still reading a recycled output
+        block).  Every call is synchronous, so a host wait costs nothing the call would not."""
+        seen = set()
+        stack = list(objs)
+        while stack:
+            a = stack.pop()
+            if isinstance(a, (list, tuple)):
+                stack.extend(a)
+            elif getattr(a, "is_cuda", False) and a.device not in seen:
+                import torch
+                seen.add(a.device)
+                torch.cuda.current_stream(a.device).synchronize()
+
     # ------------------------------------------------------------ refine
     def refine(self, S, Z0=None, order: int = 2, precision: str = "fp64", Z=None, hist_cap: int = 128,
                raise_on_error: bool = True, **opts) -> Result:
@@ -202,6 +220,7 @@ class Context:
         o = make_opts(**opts)
         hist = np.full(hist_cap, np.nan)
         info = Info()
+        self._ready(S, Z0, Z)
         rc = self.lib.zfact_refine(self.h, _ptr(S), _ptr(Z0), n, int(order), PRECISION[precision],
                                    ctypes.byref(o), _ptr(Z), hist.ctypes.data, int(hist_cap),
                                    ctypes.byref(info))
@@ -229,6 +248,7 @@ class Context:
         infos = (Info * count)()
         status = np.zeros(count, dtype=np.int32)
         o = make_opts(**opts)
+        self._ready(S_list, Z_list, Z0_list)
         rc = self.lib.zfact_refine_batched(self.h, count, sp, z0p, ns.ctypes.data, ords.ctypes.data,
                                            PRECISION[precision], ctypes.byref(o), zp, hist.ctypes.data,
                                            hist_cap, infos, status.ctypes.data)
@@ -252,6 +272,7 @@ class Context:
     def gemm(self, A, B, precision: str = "bf16", scale_a: float = 1.0, scale_b: float = 1.0, C=None):
         n = int(A.shape[0])
         C = A.new_empty((n, n)) if C is None else C
+        self._ready(A, B, C)
         rc = self.lib.zfact_gemm(self.h, PRECISION[precision], n, _ptr(A), scale_a, _ptr(B), scale_b, _ptr(C))
         self._raise(rc)
         return C
@@ -261,6 +282,7 @@ class Context:
         n = int(A.numel())
         hi = torch.empty(n, dtype=torch.int16, device=A.device)
         lo = torch.empty(n, dtype=torch.int16, device=A.device)
+        self._ready(A, hi, lo)
         rc = self.lib.zfact_split(self.h, PRECISION[precision], _ptr(A), n, scale, _ptr(hi), _ptr(lo))
         self._raise(rc)
         return hi, lo
@@ -268,6 +290,7 @@ class Context:
     def residual(self, S, Z, mode: str = "native", D=None):
         n = int(S.shape[0])
         err = ctypes.c_double()
+        self._ready(S, Z, D)
         rc = self.lib.zfact_residual(self.h, REFINE_MODE[mode], _ptr(S), _ptr(Z), n, _ptr(D), ctypes.byref(err))
         self._raise(rc)
         return err.value
@@ -275,6 +298,7 @@ class Context:
     # ------------------------------------------------------------ learned start
     def features(self, S):
         feat = np.zeros(16, dtype=np.float32)
+        self._ready(S)
         rc = self.lib.zfact_features(self.h, _ptr(S), int(S.shape[0]), feat.ctypes.data)
         self._raise(rc)
         return feat
@@ -283,6 +307,7 @@ class Context:
         import torch
         b = int(x.shape[0])
         y = torch.empty((b, 5), dtype=torch.float32, device=x.device) if y is None else y
+        self._ready(params, mean, std, x, y)
         rc = self.lib.zfact_mlp_forward(self.h, _ptr(params), _ptr(mean), _ptr(std), _ptr(x), b, _ptr(y))
         self._raise(rc)
         return y
@@ -292,12 +317,14 @@ class Context:
         b = int(x.shape[0])
         grad = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=x.device) if grad is None else grad
         loss = ctypes.c_double()
+        self._ready(params, mean, std, x, t_scale, t_order, grad)
         rc = self.lib.zfact_mlp_backward(self.h, _ptr(params), _ptr(mean), _ptr(std), _ptr(x), _ptr(t_scale),
                                          _ptr(t_order), b, float(w_order), _ptr(grad), ctypes.byref(loss))
         self._raise(rc)
         return grad, loss.value
 
     def mlp_adam(self, params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._ready(params, grad, m, v)
         rc = self.lib.zfact_mlp_adam(self.h, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(params.numel()),
                                      int(step), float(lr), float(beta1), float(beta2), float(eps))
         self._raise(rc)
@@ -305,6 +332,7 @@ class Context:
     def propose(self, S, params, mean, std):
         s = ctypes.c_double()
         m = ctypes.c_int()
+        self._ready(S, params, mean, std)
         rc = self.lib.zfact_propose(self.h, _ptr(S), int(S.shape[0]), _ptr(params), _ptr(mean), _ptr(std),
                                     ctypes.byref(s), ctypes.byref(m))
         self._raise(rc)

@@ -95,3 +95,20 @@ def test_mixed_ozaki_workload2(ctx):
     e = ctx.residual(dev(S), r.Z, "native")
     assert e / math.sqrt(n) <= 1e-12
     assert abs(e - r.info["resid_f"]) <= 1e-12 * math.sqrt(n)
+
+
+def test_ozaki_residual_ill_conditioned_many_slices(ctx):
+    """cond ~1e5 with max|Z| ~ 300: the slice count grows past ten (128-bit fixed-point slicing);
+    the residual must still match the FP64 oracle normwise."""
+    import torch
+    n = 600
+    S, Q, lam = synth.householder_spd(n, seed=91, lam_lo=1e-5, lam_hi=1.0)
+    g = np.random.default_rng(91)
+    Z = (Q * lam ** -0.5) @ Q.T + 1e-6 * g.standard_normal((n, n))
+    assert np.max(np.abs(Z)) ** 2 * np.max(np.abs(S).sum(axis=1)) > 2.0 ** 13   # more than 11 slices
+    d_or, err_or = oracle.residual(S, Z)
+    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    err = ctx.residual(dev(S), dev(Z), "ozaki", D=D)
+    scale = np.max(np.abs(Z).T @ np.abs(S) @ np.abs(Z))
+    assert np.max(np.abs(D.cpu().numpy() - d_or)) <= 1e-13 * scale
+    assert abs(err - err_or) <= 1e-13 * scale * n
