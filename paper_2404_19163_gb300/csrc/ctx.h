@@ -101,7 +101,8 @@ int f64_update(zfact_ctx* c, const double* Z, const double* Q, double* Zn, int n
 int oz_slices_for(double zmax, double g_hi);
 int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s = 0);
 int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop);
-int oz_update(zfact_ctx* c, double* Z, const double* Q, int n);
+int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax);
+int oz_update_slices(int n, double q);
 
 // Algorithm 3 with FP64-accurate sliced products, from the FP64 iterate Z64 (mixed.cu)
 int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o, int iters,

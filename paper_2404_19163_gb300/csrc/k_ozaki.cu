@@ -62,6 +62,33 @@ __device__ __forceinline__ void slice_digits(I F, int T, int s, int b, uint16_t*
   }
 }
 
+// The same digits for T <= 62 in offset binary, with 32-bit operations only.  With
+// D = 2^(b-1) sum_{p>=1} 2^(T-b(p+1)) and U = F + D, digit p >= 1 is ((U >> (T-b(p+1))) mod 2^b) - 2^(b-1),
+// in [-2^(b-1), 2^(b-1)), and digit 0 is U >> (T-b) (floor), in [-2^b, 2^b]; they sum back to U - D = F.
+// (A balanced representation like slice_digits' round-to-nearest one, within the same digit bounds.)
+__device__ __forceinline__ long long offset_of(int T, int s, int b) {
+  long long D = 0;
+  for (int p = 1; p < s; ++p) D += 1ll << (T - b * (p + 1) + b - 1);
+  return D;
+}
+__device__ __forceinline__ uint16_t bf16_of_small_int(int a) {
+  // |a| <= 2^b with b <= 7: exact in BF16, whose bits are the top half of the FP32 bits
+  return (uint16_t)(__float_as_uint(__int2float_rn(a)) >> 16);
+}
+__device__ __forceinline__ void slice_digits_offset(long long F, long long D, int T, int s, int b, uint16_t* out,
+                                                    size_t stride) {
+  const long long U = F + D;
+  out[0] = bf16_of_small_int((int)(U >> (T - b)));
+  const unsigned lo = (unsigned)U, hi = (unsigned)((unsigned long long)U >> 32);
+  const unsigned mask = (1u << b) - 1u;
+  const int half = 1 << (b - 1);
+  for (int p = 1; p < s; ++p) {
+    const int sh = T - b * (p + 1);
+    const unsigned u = (sh >= 32 ? (hi >> (sh - 32)) : __funnelshift_r(lo, hi, sh)) & mask;
+    out[(size_t)p * stride] = bf16_of_small_int((int)u - half);
+  }
+}
+
 // Column exponents of X (operand rows = columns of X): each block owns a stripe of 32 columns
 // and walks every row (coalesced), so no atomics are needed.
 __global__ void k_oz_colexp(const double* __restrict__ X, int n, int ld, int* __restrict__ e) {
@@ -120,6 +147,7 @@ __global__ void k_oz_slice(const double* __restrict__ X, int n, int ld, const in
   }
   __syncthreads();
   const int T = s * b;
+  const long long D = T <= 62 ? offset_of(T, s, b) : 0;
   for (int r = ty; r < 32; r += 8) {
     int row, col;
     double x;
@@ -137,35 +165,176 @@ __global__ void k_oz_slice(const double* __restrict__ X, int n, int ld, const in
     uint16_t* o = out + (size_t)row * ld16 + col;
     const size_t stride = (size_t)Rp * ld16;
     if (T <= 62)
-      slice_digits<long long>((er > -1000) ? fixed_point(x, er, T) : 0, T, s, b, o, stride);
+      slice_digits_offset((er > -1000) ? fixed_point(x, er, T) : 0, D, T, s, b, o, stride);
     else
       slice_digits<__int128>((er > -1000) ? fixed_point128(x, er, T) : 0, T, s, b, o, stride);
+  }
+}
+
+// Slices of X^T (operand rows = columns of X), T <= 62: a 64 x 32 tile of X (rows bi.., columns
+// bj..) through shared memory (even and odd rows apart, so the transposed reads are conflict-free);
+// each thread forms two adjacent operand columns (X rows) and stores their digits as one 4-byte word.
+__global__ void k_oz_tslice2(const double* __restrict__ X, int n, int ld, const int* __restrict__ e, int s, int b,
+                             uint16_t* __restrict__ out, int ld16, int Rp) {
+  __shared__ double te[32][33], to[32][33];
+  const int bi = blockIdx.y * 64, bj = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int rr = ty; rr < 64; rr += 8) {
+    const int i = bi + rr, j = bj + tx;
+    const double x = (i < n && j < n) ? X[(size_t)i * ld + j] : 0.0;
+    if (rr & 1)
+      to[rr >> 1][tx] = x;
+    else
+      te[rr >> 1][tx] = x;
+  }
+  __syncthreads();
+  const int T = s * b;
+  const long long D = offset_of(T, s, b);
+  const unsigned mask = (1u << b) - 1u;
+  const int half = 1 << (b - 1);
+  const size_t stride = (size_t)Rp * ld16;
+  const int col = bi + 2 * tx;  // operand columns col, col + 1 = X rows
+  for (int r = ty; r < 32; r += 8) {
+    const int row = bj + r;  // operand row = X column
+    if (row >= n || col >= n) continue;
+    const int er = e[row];
+    const long long U0 = ((er > -1000) ? fixed_point(te[tx][r], er, T) : 0) + D;
+    const long long U1 = ((er > -1000) ? fixed_point(to[tx][r], er, T) : 0) + D;
+    uint16_t* o = out + (size_t)row * ld16 + col;
+    const bool pair = col + 1 < n;
+    unsigned w = (unsigned)bf16_of_small_int((int)(U0 >> (T - b))) |
+                 ((unsigned)bf16_of_small_int((int)(U1 >> (T - b))) << 16);
+    if (pair)
+      *reinterpret_cast<unsigned*>(o) = w;
+    else
+      *o = (uint16_t)w;
+    const unsigned lo0 = (unsigned)U0, hi0 = (unsigned)((unsigned long long)U0 >> 32);
+    const unsigned lo1 = (unsigned)U1, hi1 = (unsigned)((unsigned long long)U1 >> 32);
+    for (int p = 1; p < s; ++p) {
+      const int sh = T - b * (p + 1);
+      const unsigned u0 = (sh >= 32 ? (hi0 >> (sh - 32)) : __funnelshift_r(lo0, hi0, sh)) & mask;
+      const unsigned u1 = (sh >= 32 ? (hi1 >> (sh - 32)) : __funnelshift_r(lo1, hi1, sh)) & mask;
+      w = (unsigned)bf16_of_small_int((int)u0 - half) | ((unsigned)bf16_of_small_int((int)u1 - half) << 16);
+      uint16_t* op = o + (size_t)p * stride;
+      if (pair)
+        *reinterpret_cast<unsigned*>(op) = w;
+      else
+        *op = (uint16_t)w;
+    }
   }
 }
 
 // Row slices of X (operand rows = rows of X): one warp per row finds the row's exponent and
 // then slices the row (two coalesced passes, the second from cache; no atomics).
 __global__ void k_oz_rowslice(const double* __restrict__ X, int n, int ld, int* __restrict__ e, int s, int b,
-                              uint16_t* __restrict__ out, int ld16, int Rp) {
+                              uint16_t* __restrict__ out, int ld16, int Rp, int vec) {
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const double* xr = X + (size_t)row * ld;
+  // vec: the row starts on 16 bytes (X aligned, ld even), so lanes take element pairs
+  const int npair = vec ? n / 2 : 0;
   double m = 0.0;
-  for (int c = lane; c < n; c += 32) m = fmax(m, fabs(xr[c]));
+  for (int c = lane; c < npair; c += 32) {
+    const double2 v = reinterpret_cast<const double2*>(xr)[c];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int c = 2 * npair + lane; c < n; c += 32) m = fmax(m, fabs(xr[c]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   const int er = m > 0.0 ? exp_bound(m) : -2000000000;
   if (lane == 0) e[row] = er;
   const int T = s * b;
   const size_t stride = (size_t)Rp * ld16;
-  for (int c = lane; c < n; c += 32) {
-    uint16_t* o = out + (size_t)row * ld16 + c;
-    if (T <= 62)
-      slice_digits<long long>((er > -1000) ? fixed_point(xr[c], er, T) : 0, T, s, b, o, stride);
-    else
-      slice_digits<__int128>((er > -1000) ? fixed_point128(xr[c], er, T) : 0, T, s, b, o, stride);
+  uint16_t* orow = out + (size_t)row * ld16;
+  if (T <= 62) {
+    const long long D = offset_of(T, s, b);
+    for (int c = lane; c < npair; c += 32) {
+      const double2 v = reinterpret_cast<const double2*>(xr)[c];
+      const long long F0 = (er > -1000) ? fixed_point(v.x, er, T) : 0;
+      const long long F1 = (er > -1000) ? fixed_point(v.y, er, T) : 0;
+      // both elements' digits, packed into one 4-byte store per slice
+      const long long U0 = F0 + D, U1 = F1 + D;
+      unsigned* o = reinterpret_cast<unsigned*>(orow + 2 * c);
+      *o = (unsigned)bf16_of_small_int((int)(U0 >> (T - b))) |
+           ((unsigned)bf16_of_small_int((int)(U1 >> (T - b))) << 16);
+      const unsigned lo0 = (unsigned)U0, hi0 = (unsigned)((unsigned long long)U0 >> 32);
+      const unsigned lo1 = (unsigned)U1, hi1 = (unsigned)((unsigned long long)U1 >> 32);
+      const unsigned mask = (1u << b) - 1u;
+      const int half = 1 << (b - 1);
+      for (int p = 1; p < s; ++p) {
+        const int sh = T - b * (p + 1);
+        const unsigned u0 = (sh >= 32 ? (hi0 >> (sh - 32)) : __funnelshift_r(lo0, hi0, sh)) & mask;
+        const unsigned u1 = (sh >= 32 ? (hi1 >> (sh - 32)) : __funnelshift_r(lo1, hi1, sh)) & mask;
+        o = reinterpret_cast<unsigned*>(orow + (size_t)p * stride + 2 * c);
+        *o = (unsigned)bf16_of_small_int((int)u0 - half) | ((unsigned)bf16_of_small_int((int)u1 - half) << 16);
+      }
+    }
+    for (int c = 2 * npair + lane; c < n; c += 32)
+      slice_digits_offset((er > -1000) ? fixed_point(xr[c], er, T) : 0, D, T, s, b, orow + c, stride);
+  } else {
+    for (int c = lane; c < n; c += 32)
+      slice_digits<__int128>((er > -1000) ? fixed_point128(xr[c], er, T) : 0, T, s, b, orow + c, stride);
   }
+}
+
+// The same with the row held in registers: one block of NT threads per row, each thread up to
+// PAIRS element pairs (so n <= 2 NT PAIRS), 16-byte loads (the row starts on 16 bytes), one read of
+// X for both the exponent and the digits.  T <= 62 only.
+template <int NT, int PAIRS>
+__global__ void __launch_bounds__(NT) k_oz_rowslice_reg(const double* __restrict__ X, int n, int ld,
+                                                       int* __restrict__ e, int s, int b, uint16_t* __restrict__ out,
+                                                       int ld16, int Rp) {
+  __shared__ double red[NT / 32];
+  const int row = blockIdx.x;
+  const int tid = threadIdx.x;
+  const double* xr = X + (size_t)row * ld;
+  const int npair = n / 2;
+  double2 v[PAIRS];
+  double m = 0.0;
+#pragma unroll
+  for (int k = 0; k < PAIRS; ++k) {
+    const int c = tid + NT * k;
+    v[k] = c < npair ? reinterpret_cast<const double2*>(xr)[c] : make_double2(0.0, 0.0);
+    m = fmax(m, fmax(fabs(v[k].x), fabs(v[k].y)));
+  }
+  const double last = ((n & 1) && tid == 0) ? xr[n - 1] : 0.0;
+  m = fmax(m, fabs(last));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  m = red[0];
+#pragma unroll
+  for (int w = 1; w < NT / 32; ++w) m = fmax(m, red[w]);
+  const int er = m > 0.0 ? exp_bound(m) : -2000000000;
+  if (tid == 0) e[row] = er;
+  const int T = s * b;
+  const size_t stride = (size_t)Rp * ld16;
+  uint16_t* orow = out + (size_t)row * ld16;
+  const long long D = offset_of(T, s, b);
+  const unsigned mask = (1u << b) - 1u;
+  const int half = 1 << (b - 1);
+#pragma unroll
+  for (int k = 0; k < PAIRS; ++k) {
+    const int c = tid + NT * k;
+    if (c >= npair) break;
+    const long long U0 = ((er > -1000) ? fixed_point(v[k].x, er, T) : 0) + D;
+    const long long U1 = ((er > -1000) ? fixed_point(v[k].y, er, T) : 0) + D;
+    unsigned* o = reinterpret_cast<unsigned*>(orow + 2 * c);
+    *o = (unsigned)bf16_of_small_int((int)(U0 >> (T - b))) | ((unsigned)bf16_of_small_int((int)(U1 >> (T - b))) << 16);
+    const unsigned lo0 = (unsigned)U0, hi0 = (unsigned)((unsigned long long)U0 >> 32);
+    const unsigned lo1 = (unsigned)U1, hi1 = (unsigned)((unsigned long long)U1 >> 32);
+    for (int p = 1; p < s; ++p) {
+      const int sh = T - b * (p + 1);
+      const unsigned u0 = (sh >= 32 ? (hi0 >> (sh - 32)) : __funnelshift_r(lo0, hi0, sh)) & mask;
+      const unsigned u1 = (sh >= 32 ? (hi1 >> (sh - 32)) : __funnelshift_r(lo1, hi1, sh)) & mask;
+      o = reinterpret_cast<unsigned*>(orow + (size_t)p * stride + 2 * c);
+      *o = (unsigned)bf16_of_small_int((int)u0 - half) | ((unsigned)bf16_of_small_int((int)u1 - half) << 16);
+    }
+  }
+  if ((n & 1) && tid == 0)
+    slice_digits_offset((er > -1000) ? fixed_point(last, er, T) : 0, D, T, s, b, orow + (n - 1), stride);
 }
 
 // Sum of the groups with the scales: val = 2^{eA_i + eB_j} 2^{-2b} sum_t 2^{-bt} T_t,
@@ -196,30 +365,69 @@ __global__ void k_oz_combine(const float* __restrict__ G, size_t gstride, int ld
   if (k1 > s) k1 = s;
   const float wb = ldexpf(1.0f, -b);
   if (active) {
-    for (int r = threadIdx.y; r < 32; r += 8) {
-      const int i = bi + r, j = bj + threadIdx.x;
+    // the four rows of this thread side by side: four independent loads per (group, chunk)
+    const int j = bj + threadIdx.x;
+    bool ok[4];
+    size_t off[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = bi + threadIdx.y + 8 * q;
+      ok[q] = i < n && j < n;
+      off[q] = ok[q] ? (size_t)i * ld32 + j : 0;
+    }
+    long long I[4] = {0, 0, 0, 0}, J[4] = {0, 0, 0, 0}, tt[4] = {0, 0, 0, 0};
+    // the exact groups' slots u = t * nch + c in order, four slots (sixteen loads) in flight
+    const int nu = k1 * nch;
+    int t = 0, c = 0;
+    for (int u0 = 0; u0 < nu; u0 += 4) {
+      float v[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const float* g = G + (size_t)(u0 + x) * gstride;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[x][q] = (u0 + x < nu && ok[q]) ? __ldcs(g + off[q]) : 0.0f;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        if (u0 + x >= nu) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tt[q] += __float2int_rn(v[x][q]);
+        if (++c == nch) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (t < k0)
+              I[q] = I[q] * (1ll << b) + tt[q];
+            else
+              J[q] = J[q] * (1ll << b) + tt[q];
+            tt[q] = 0;
+          }
+          c = 0;
+          ++t;
+        }
+      }
+    }
+    float F[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int t = s - 1; t >= k1; --t) {
+      float tt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int c = 0; c < nch; ++c) {
+        const float* g = G + (size_t)(t * nch + c) * gstride;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tt[q] += ok[q] ? __ldcs(g + off[q]) : 0.0f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) F[q] = (F[q] + tt[q]) * wb;
+    }
+    const int eb = j < n ? eB[j] : -2000000000;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = threadIdx.y + 8 * q;
+      const int i = bi + r;
       double val = 0.0;
-      if (i < n && j < n) {
-        const size_t off = (size_t)i * ld32 + j;
-        long long I = 0, J = 0;
-        for (int t = 0; t < k1; ++t) {
-          long long tt = 0;
-          for (int c = 0; c < nch; ++c) tt += __float2int_rn(G[(size_t)(t * nch + c) * gstride + off]);
-          if (t < k0)
-            I = I * (1ll << b) + tt;
-          else
-            J = J * (1ll << b) + tt;
-        }
-        float F = 0.0f;
-        for (int t = s - 1; t >= k1; --t) {
-          float tt = 0.0f;
-          for (int c = 0; c < nch; ++c) tt += G[(size_t)(t * nch + c) * gstride + off];
-          F = (F + tt) * wb;
-        }
-        const int ea = eA[i], eb = eB[j];
+      if (ok[q]) {
+        const int ea = eA[i];
         if (ea > -1000 && eb > -1000) {
           const int e0 = ea + eb - 2 * b - b * (k0 - 1), e1 = ea + eb - 2 * b - b * (k1 - 1);
-          val = ldexp((double)I, e0) + ldexp((double)J + (double)F, e1);
+          val = ldexp((double)I[q], e0) + ldexp((double)J[q] + (double)F[q], e1);
         }
         if (mode == 2) {
           val = (i == j ? 1.0 : 0.0) - val;
@@ -334,10 +542,21 @@ cudaError_t launch_oz_slice(const double* X, int n, int ld, bool trans, const in
   for (int p = 0; p < sl; ++p)  // padding rows n..Rp-1 of every slice must read as zero
     if (Rp > n) cudaMemsetAsync(out + ((size_t)p * Rp + n) * ld16, 0, sizeof(uint16_t) * (size_t)(Rp - n) * ld16, s);
   if (trans) {
-    dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-    k_oz_slice<true><<<grid, block, 0, s>>>(X, n, ld, e, sl, b, out, ld16, Rp);
+    if (sl * b <= 62 && (ld16 & 1) == 0) {
+      dim3 grid((n + 31) / 32, (n + 63) / 64), block(32, 8);
+      k_oz_tslice2<<<grid, block, 0, s>>>(X, n, ld, e, sl, b, out, ld16, Rp);
+    } else {
+      dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+      k_oz_slice<true><<<grid, block, 0, s>>>(X, n, ld, e, sl, b, out, ld16, Rp);
+    }
   } else {
-    k_oz_rowslice<<<(n + 7) / 8, 256, 0, s>>>(X, n, ld, const_cast<int*>(e), sl, b, out, ld16, Rp);
+    const int vec = ((reinterpret_cast<uintptr_t>(X) & 15) == 0 && (ld & 1) == 0 && (ld16 & 1) == 0) ? 1 : 0;
+    if (vec && sl * b <= 62 && n <= 2 * 256 * 8)
+      k_oz_rowslice_reg<256, 8><<<n, 256, 0, s>>>(X, n, ld, const_cast<int*>(e), sl, b, out, ld16, Rp);
+    else if (vec && sl * b <= 62 && n <= 2 * 512 * 16)
+      k_oz_rowslice_reg<512, 16><<<n, 512, 0, s>>>(X, n, ld, const_cast<int*>(e), sl, b, out, ld16, Rp);
+    else
+      k_oz_rowslice<<<(n + 7) / 8, 256, 0, s>>>(X, n, ld, const_cast<int*>(e), sl, b, out, ld16, Rp, vec);
   }
   return cudaGetLastError();
 }

@@ -227,17 +227,23 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
   for (int r = 0; r <= o.refine_steps; ++r) {
     ++idx;
     if ((st = oz_residual(c, Z64, D64, n, idx, o.stop_rule, o.tol, 0))) return st;
+    // max|d| comes back with Err: it scales d's 16-bit copy and bounds Q for the update's slices
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
+                                  [&] { return launch_amax_f64(D64, n, c->st_dev, 1, c->stream); }),
+                       "amax d")))
+      return st;
     if ((st = ctx_read_state(c))) return st;
     const double err = c->st_host->hist[idx];
     inf->resid_f = err;
     if (c->st_host->nonfinite || r == o.refine_steps) break;
     if (o.tol > 0 && err / sqrt((double)n) <= o.tol) break;
+    // |Q_ij| <= sum_k c_k |(d^k)_ij| <= sum_k c_k N^(k-1) max|d|^k
+    const double dmax = c->st_host->amax[1];
+    double qmax = 0.0, dk = dmax;
+    for (int k = 1; k <= order; ++k, dk *= (double)n * dmax) qmax += coef[k] * dk;
     // Q = c1 d + sum_{k>=2} c_k d^k: the linear term exact in FP64, the powers by FP16 hi/lo products
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 2, [&] {
-                         cudaError_t e = launch_amax_f64(D64, n, c->st_dev, 1, c->stream);
-                         if (e != cudaSuccess) return e;
-                         return launch_pow2_slot(c->st_dev, 1, 0, c->stream);
-                       }),
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
+                                  [&] { return launch_pow2_slot(c->st_dev, 1, 0, c->stream); }),
                        "scale d")))
       return st;
     if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
@@ -288,7 +294,7 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
         Pprev = keep;
       }
     }
-    if ((st = oz_update(c, Z64, Q64, n))) return st;
+    if ((st = oz_update(c, Z64, Q64, n, qmax))) return st;
     ++ridx;
   }
   *ridx_out = ridx;

@@ -16,7 +16,7 @@ namespace {
 
 constexpr int kOzBits = 6;             // bits per slice
 constexpr int kOzSlicesResid = 9;      // 54 bits: residual products of a well-scaled Z
-constexpr int kOzSlicesUpdate = 8;     // 48 bits: Z Q (its result is a small correction)
+constexpr int kOzSlicesUpdateMin = 4;  // 24 bits: the least Z Q is formed with (see oz_update_slices)
 constexpr int kOzSlicesMax = 14;
 constexpr size_t kOzGBudget = (size_t)6 << 30;  // bytes of FP32 group partials per launch
 
@@ -119,7 +119,8 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
       md = 2;
       *fused_resid = true;
     }
-    if ((st = ctx_cuda(c, klaunch(c, "oz_combine", 0, 4.0 * s * nch * n * (double)n + 16.0 * n * n, 1, [&] {
+    const double cbytes = 4.0 * s * nch * n * (double)n + 16.0 * n * n;
+    if ((st = ctx_cuda(c, klaunch(c, "oz_combine", 0, cbytes, 1, [&] {
                          return launch_oz_combine(G, (size_t)n * ld, ld, s, nch, kOzBits, A.e, B.e, n, out, ld64, md,
                                                   sym, partials, cur_stream(c));
                        }),
@@ -193,11 +194,29 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
                   "finish err");
 }
 
-// Z <- Z + Z Q to FP64 accuracy (Q symmetric: B operand rows are rows of Q).
-int oz_update(zfact_ctx* c, double* Z, const double* Q, int n) {
+// Slices for Z Q given a bound q >= max|Q_ij|.  Row i of Z and column j of Q are kept to T bits
+// below their largest entries (2^ez_i, 2^eq_j); the truncation of either operand and the dropped
+// slice pairs leave N error terms of size ~2^(ez_i + eq_j - T) in entry (i, j).  They are rounding
+// errors uncorrelated with the other operand, so their sum grows like sqrt(N) (the probabilistic
+// model of Higham and Mary, SIAM J. Sci. Comput. 2019, which also describes FP64 GEMM's own error).
+// T = 53 + log2(4 sqrt(N) q) keeps that sum a factor 4 below 2^-53 2^ez_i, the rounding unit of row
+// i's largest entry: below what storing Z + Z Q in FP64 costs anyway.  A small correction needs
+// few bits.
+int oz_update_slices(int n, double q) {
+  double T = 53.0 + log2(4.0 * sqrt((double)n) * q);
+  if (!(T > 0)) T = 0;
+  int s = (int)ceil(T / kOzBits);
+  if (s < kOzSlicesUpdateMin) s = kOzSlicesUpdateMin;
+  if (s > kOzSlicesMax) s = kOzSlicesMax;
+  return s;
+}
+
+// Z <- Z + Z Q to FP64 accuracy (Q symmetric: B operand rows are rows of Q); qmax bounds |Q_ij|.
+int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax) {
   int st = ZFACT_OK;
   OzOperand Zr, Qr;
-  const int su = c->oz_s - 1 > kOzSlicesUpdate ? c->oz_s - 1 : kOzSlicesUpdate;
+  if (qmax == 0.0) return ZFACT_OK;  // Q = 0: Z is unchanged
+  const int su = (qmax > 0.0 && isfinite(qmax)) ? oz_update_slices(n, qmax) : kOzSlicesMax;
   if ((st = oz_make(c, "Zr", Z, n, n, false, su, &Zr))) return st;
   if ((st = oz_make(c, "Qr", Q, n, n, false, su, &Qr))) return st;
   return oz_product(c, Zr, Qr, n, false, Z, n, 1);

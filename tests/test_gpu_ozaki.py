@@ -30,7 +30,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("n", [5, 64, 200, 777, 1500, 3001])
+@pytest.mark.parametrize("n", [5, 64, 200, 777, 1500, 3001, 4097])
 def test_ozaki_residual_matches_oracle(ctx, n):
     import torch
     g = np.random.default_rng(n)
@@ -52,6 +52,40 @@ def test_ozaki_residual_matches_oracle(ctx, n):
     D2 = torch.empty_like(D)
     err2 = ctx.residual(dev(S), dev(Z), "native", D=D2)
     assert np.max(np.abs(D2.cpu().numpy() - d_or)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("n,zbits,sbits", [(300, 10, 4), (1500, 10, 4), (2048, 12, 3), (1201, 3, 3)])
+def test_ozaki_residual_exact_on_integer_inputs(ctx, n, zbits, sbits):
+    """Integer Z and S with X = Z^T S Z below 2^53: every partial sum is an integer FP64 holds, so
+    the exact d = I - X is known and the sliced residual must reproduce it bit for bit (several
+    K-chunks at n = 1500; more than 62 fixed-point bits at n = 2048)."""
+    import torch
+    g = np.random.default_rng(n + zbits)
+    Z = g.integers(-2 ** zbits, 2 ** zbits, (n, n)).astype(np.float64)
+    A = g.integers(-2 ** sbits, 2 ** sbits, (n, n)).astype(np.float64)
+    S = A + A.T
+    X = Z.T @ (S @ Z)
+    assert np.abs(X).max() < 2.0 ** 52 and np.abs(S @ Z).max() < 2.0 ** 52
+    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    ctx.residual(dev(S), dev(Z), "ozaki", D=D)
+    assert np.array_equal(D.cpu().numpy(), np.eye(n) - X)
+
+
+def test_ozaki_residual_unaligned_operand_bit_identical(ctx):
+    """S at an 8-byte offset (no 16-byte loads): the same digits, so the same bits as aligned S."""
+    import torch
+    n = 201
+    S, Q, lam = synth.householder_spd(n, seed=7)
+    Z = (Q * lam ** -0.5) @ Q.T + 1e-3 * np.random.default_rng(7).standard_normal((n, n))
+    buf = torch.empty(n * n + 1, dtype=torch.float64, device="cuda")
+    Su = buf[1:].view(n, n)
+    Su.copy_(dev(S))
+    assert Su.data_ptr() % 16 == 8
+    D1 = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    D2 = torch.empty_like(D1)
+    e1 = ctx.residual(dev(S), dev(Z), "ozaki", D=D1)
+    e2 = ctx.residual(Su, dev(Z), "ozaki", D=D2)
+    assert torch.equal(D1, D2) and e1 == e2
 
 
 def test_ozaki_residual_of_exact_factor_is_tiny(ctx):
