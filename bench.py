@@ -277,6 +277,13 @@ def run_ours(args, rank, ws, local):
     fp32_info.update({"refined_ms": round(e0.elapsed_time(e1), 3), "refined_resid": r32r.info["resid_f"] / math.sqrt(n),
                       "refined_iters": r32r.info["refine_iters"]})
 
+    # diagonalization comparator (cuSOLVER), once warm: time and the residual of its S^{-1/2}
+    eigh_inverse_sqrt(S)
+    Ze, eigh_ms = eigh_inverse_sqrt(S)
+    eigh_info = {"ms": round(eigh_ms, 3), "resid": ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n),
+                 "how": "torch.linalg.eigh (cuSOLVER syevd, FP64) + V diag(lambda^-1/2) V^T (cuBLAS)"}
+    del Ze
+
     # e2e: host (pinned) buffers through the public C ABI, copies inside the call
     S_pin = torch.from_numpy(S_host).pin_memory()
     Z_pin = torch.empty_like(S_pin).pin_memory()
@@ -345,13 +352,32 @@ def run_ours(args, rank, ws, local):
             "resid": resid, "rel_z_vs_fp64": rel_z,
             "fp64_path": {"ms": round(fp64_ms, 3), "iters": fp64_iters, "resid": fp64_resid},
             "fp32_path": fp32_info,
+            "eigh_comparator": eigh_info,
             "speedup_vs_fp64_path": round(fp64_ms / ms, 2),
+            "speedup_vs_eigh": round(eigh_info["ms"] / ms, 2),
             "tc_tflops": round(tc_fl / (tc_ms * 1e-3) / 1e12, 1) if tc_ms > 0 else None,
             "kernels": sorted([{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
                                for s in stats], key=lambda s: -s["ms"]),
         }
         print(json.dumps(out), flush=True)
     ctx.close()
+
+
+def eigh_inverse_sqrt(S):
+    """Comparator (the paper's diagonalization route, Sec. 2 and Sec. 5.1): S^{-1/2} =
+    V diag(lambda^{-1/2}) V^T with torch.linalg.eigh (cuSOLVER) and one cuBLAS product, timed
+    with CUDA events on torch's current stream.  Returns (Z, ms)."""
+    import torch
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    lam, V = torch.linalg.eigh(S)
+    Z = (V * lam.rsqrt()) @ V.T
+    e1.record(st)
+    e1.synchronize()
+    return Z, e0.elapsed_time(e1)
 
 
 def run_case_residual(args):
@@ -500,8 +526,60 @@ def run_ill(args):
         e1.synchronize()
         out["fp64_path"] = {"ms": e0.elapsed_time(e1), "iters": r64.info["iters"],
                             "resid": r64.info["resid_f"] / math.sqrt(n), "hist": [float(h) for h in r64.hist]}
+        with torch.cuda.stream(stream):
+            eigh_inverse_sqrt(S[:256, :256].contiguous())  # warm the solver
+            Ze, eigh_ms = eigh_inverse_sqrt(S)
+        out["eigh_comparator"] = {"ms": round(eigh_ms, 1),
+                                  "resid": ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n)}
+        del Ze
     ctx.close()
     print(json.dumps(out), flush=True)
+
+
+def run_paper(args):
+    """The paper's synthetic overlap (Sec. 5.1): S = (T + T^T)/2 shifted to lambda_min = 0.5,
+    Z0 = S^{-1/2} + 0.005 U, solved with the (h)(h)+(h)(l)+(l)(h) method (FP16 hi/lo split,
+    Table I) under Algorithm 2's stop and Algorithm 3's refinement: iterations, the Frobenius
+    history and the stop ratios Err_n / Err_{n-1}^3 of Fig. 1, time, the FP64 path's iterations
+    (N <= 4096) and the diagonalization comparator.  One JSON line."""
+    import torch
+    from paper_2404_19163_gb300 import Context, synth, build as zbuild
+    zbuild.build()
+    stream = torch.cuda.Stream()
+    ctx = Context(0, stream=stream)
+    rows = []
+    for n in [int(x) for x in args.paper_sizes.split(",")]:
+        S = synth.paper_synthetic_torch(n)
+        Z0 = synth.paper_start_torch(S, 0.005, seed=0)
+        Z = torch.empty_like(S)
+        kw = dict(order=2, precision="fp16_split", tol=TOL, Z=Z, raise_on_error=False)
+        ctx.refine(S, Z0, **kw)  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ctx.refine(S, Z0, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        h = [float(x) for x in r.hist]
+        it = r.info["iters"]
+        row = {"N": n, "iters": it, "refine_iters": r.info["refine_iters"], "status": r.status,
+               "ms": round(e0.elapsed_time(e1), 3), "resid": r.info["resid_f"] / math.sqrt(n), "hist": h,
+               "stop_ratios": [h[i] / h[i - 1] ** 3 for i in range(1, it + 1)]}
+        if n <= 4096:
+            r64 = ctx.refine(S, Z0, order=2, precision="fp64", Z=Z, raise_on_error=False)
+            row["fp64_iters"] = r64.info["iters"]
+            row["fp64_hist"] = [float(x) for x in r64.hist]
+        with torch.cuda.stream(stream):
+            Ze, eigh_ms = eigh_inverse_sqrt(S)
+        row["eigh_ms"] = round(eigh_ms, 2)
+        row["eigh_resid"] = ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n)
+        del Ze, S, Z0, Z
+        torch.cuda.empty_cache()
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    ctx.close()
+    print(json.dumps({"workload": "paper_synthetic_sweep", "alpha": 0.005, "gamma": 0.5,
+                      "precision": "fp16_split", "tol": TOL, "rows": rows}), flush=True)
 
 
 def main():
@@ -514,7 +592,8 @@ def main():
     ap.add_argument("--refine-mode", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, choices=[None, "residual"])
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "ill"])
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "ill", "paper"])
+    ap.add_argument("--paper-sizes", default="1024,4096,16384")
     ap.add_argument("--tol-ill", type=float, default=1e-12)
     ap.add_argument("--fp64-comparator", action="store_true")
     ap.add_argument("--batch-count", type=int, default=128)
@@ -531,6 +610,9 @@ def main():
         return
     if args.workload == "ill":
         run_ill(args)
+        return
+    if args.workload == "paper":
+        run_paper(args)
         return
     args.warmup = max(args.warmup, 1)
     if args.impl == "reference":

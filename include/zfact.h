@@ -218,6 +218,23 @@ int zfact_split(zfact_ctx* ctx, int precision, const double* A, int64_t n, doubl
 int zfact_residual(zfact_ctx* ctx, int refine_mode, const double* S, const double* Z,
                    int64_t N, double* D, double* err);
 
+/* ---- congruence transform: the consumer of Z ------------------------------------------
+ * H_perp = Z^T H Z for a symmetric N x N H (Sec. 2, Eq. standard_form).  With Z^T S Z = I
+ * (Eq. Def_Z) it turns the generalized eigenproblem H C = S C e into the standard problem
+ * H_perp C_perp = C_perp e, C = Z C_perp.  H_perp is symmetric by definition: its upper
+ * triangle is formed and mirrored (as X = Z^T S Z is).
+ *   precision ZFACT_P_FP64: FP64 accuracy by the method of refine_mode (ZFACT_R_NATIVE: FP64
+ *     CUDA-core products; ZFACT_R_OZAKI: error-free slicing on the BF16 tensor cores, 9 slices,
+ *     errors on the scale of FP64 products relative to |Z|^T |H| |Z|);
+ *   ZFACT_P_BF16 / ZFACT_P_BF16_SPLIT: BF16 (hi, or hi/lo) operands with FP32 accumulation
+ *     (refine_mode ignored);
+ *   FP32 and the FP16 precisions return ZFACT_ERR_UNSUPPORTED.
+ * H, Z (inputs) and Hp (output) are row-major FP64, DEVICE or HOST (host operands are staged
+ * through the context's workspace); Hp must not alias H or Z.  The call synchronises the
+ * context's stream before it returns. */
+int zfact_congruence(zfact_ctx* ctx, const double* H, const double* Z, int64_t N, int precision,
+                     int refine_mode, double* Hp);
+
 /* ---- allocation-free residual -------------------------------------------------------
  * d = I - Z^T S Z (FP64 CUDA cores) and ||d||_F, without allocating any device memory.
  * The paper has no counterpart: this entry point exists for callers that cannot call

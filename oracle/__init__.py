@@ -13,6 +13,8 @@ Contents, each following arXiv:2404.19163 (Habib, Finkelstein, Niklasson):
                         the dense loops are plain C (``zfact_oracle.c``).
 * ``refine_alg3``       Algorithm 3: the stop of Algorithm 2 followed by the
                         refinement update(s).
+* ``congruence``        H_perp = Z^T H Z (Sec. 2, Eq. standard_form), the transform
+                        the factor exists for.
 * ``coeffs``            c_k = binom(2k,k)/4^k, exact rationals (Sec. 3; the
                         m = 2 case equals Appendix A's a_k after X = I - d).
 * ``split16``           Eq. splitStyle: A^(h) = FP16[A], A^(l) = FP16[A - FP32[A^(h)]]
@@ -67,6 +69,7 @@ def _load():
         lib.zo_matmul.argtypes = [P, P, P, I64]
         lib.zo_atb_sym.argtypes = [P, P, P, I64]
         lib.zo_residual.argtypes = [P, P, P, I64]
+        lib.zo_congruence.argtypes = [P, P, P, I64]
         lib.zo_residual.restype = ctypes.c_double
         lib.zo_poly.argtypes = [P, ctypes.c_int, P, I64]
         lib.zo_update.argtypes = [P, P, I64]
@@ -114,6 +117,16 @@ def residual(S, Z):
     d = np.empty((n, n))
     err = _load().zo_residual(ps, pz, d.ctypes.data, n)
     return d, err
+
+
+def congruence(H, Z):
+    """H_perp = Z^T H Z, upper triangle mirrored (Sec. 2, Eq. standard_form)."""
+    H, ph = _c(H)
+    Z, pz = _c(Z)
+    n = H.shape[0]
+    Hp = np.empty((n, n))
+    _load().zo_congruence(ph, pz, Hp.ctypes.data, n)
+    return Hp
 
 
 def poly(d, m):

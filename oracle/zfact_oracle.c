@@ -93,6 +93,16 @@ double zo_residual(const double* S, const double* Z, double* d, int64_t n) {
     return sqrt(ss);
 }
 
+/* H_perp = Z^T H Z (upper triangle mirrored): the congruence transform of Sec. 2
+ * (Eq. standard_form, H_perp = Z^T H Z) that turns H C = S C e into a standard
+ * eigenproblem once Z^T S Z = I. */
+void zo_congruence(const double* H, const double* Z, double* Hp, int64_t n) {
+    double* A = (double*)malloc(sizeof(double) * n * n);
+    zo_matmul(H, Z, A, n);           /* A = H Z */
+    zo_atb_sym(Z, A, Hp, n);         /* Z^T A */
+    free(A);
+}
+
 /* c_k = binom(2k, k) / 4^k, k = 0..m (Taylor coefficients of (1-t)^{-1/2}). */
 void zo_coeffs(int m, double* c) {
     c[0] = 1.0;

@@ -103,6 +103,7 @@ int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s = 0);
 int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop);
 int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax);
 int oz_update_slices(int n, double q);
+int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, int n);
 
 // Algorithm 3 with FP64-accurate sliced products, from the FP64 iterate Z64 (mixed.cu)
 int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o, int iters,

@@ -211,6 +211,23 @@ int oz_update_slices(int n, double q) {
   return s;
 }
 
+// H_perp = Z^T H Z to FP64 accuracy (H symmetric), upper tiles mirrored.  Row-scaled slicing errs
+// relative to |Z|^T |H| |Z|, the scale of FP64 GEMM's own error, and H_perp does not cancel the
+// way d = I - Z^T S Z does, so the residual's base slice count (54 bits) is the right one.
+int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, int n) {
+  int st = ZFACT_OK;
+  const int s = kOzSlicesResid;
+  OzOperand Hop, Zt, At;
+  double* A64 = (double*)ctx_buf(c, lane_name(c, "oz.At64").c_str(), sizeof(double) * (size_t)n * n, &st);
+  if (!A64) return st;
+  if ((st = oz_make(c, "H", H, n, n, false, s, &Hop))) return st;
+  if ((st = oz_make(c, "Zt", Z, n, n, true, s, &Zt))) return st;
+  // A^T = Z^T H (H symmetric: B operand rows are rows of H), then Z^T (H Z) on upper tiles
+  if ((st = oz_product(c, Zt, Hop, n, false, A64, n, 0))) return st;
+  if ((st = oz_make(c, "At", A64, n, n, false, s, &At))) return st;
+  return oz_product(c, Zt, At, n, true, out, n, 0);
+}
+
 // Z <- Z + Z Q to FP64 accuracy (Q symmetric: B operand rows are rows of Q); qmax bounds |Q_ij|.
 int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax) {
   int st = ZFACT_OK;

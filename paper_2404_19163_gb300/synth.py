@@ -247,6 +247,33 @@ def paper_synthetic(n: int, gamma: float = 0.5):
     return S
 
 
+def paper_synthetic_torch(n: int, gamma: float = 0.5, device="cuda"):
+    """``paper_synthetic`` built on a torch device (FP64; lambda_min from torch.linalg.eigvalsh)."""
+    import torch
+    i = torch.arange(1, n + 1, dtype=torch.float64, device=device)
+    T = torch.exp(-(i[:, None] - i[None, :]).abs() / 2.0) * torch.sin(i + 1.0)[:, None]
+    S = 0.5 * (T + T.T)
+    del T
+    lmin = float(torch.linalg.eigvalsh(S)[0])
+    S.diagonal().add_(gamma - lmin)
+    return S.contiguous()
+
+
+def paper_start_torch(S, alpha: float = 0.005, seed: int = 0, chunk: int = 2048):
+    """Sec. 5.1's start Z0 = S^{-1/2} + alpha U, U_ij ~ U(-0.5, 0.5), on S's device.  S^{-1/2} is
+    V diag(lambda^{-1/2}) V^T from torch.linalg.eigh (the paper builds it with cuSOLVER too)."""
+    import torch
+    lam, V = torch.linalg.eigh(S)
+    Z0 = (V * lam.rsqrt()) @ V.T
+    del V
+    n = S.shape[0]
+    g = rng(6, seed)
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        Z0[r0:r1] += torch.as_tensor(alpha * g.uniform(-0.5, 0.5, (r1 - r0, n)), device=S.device)
+    return Z0.contiguous()
+
+
 def random_warm_start(n: int, alpha: float, seed: int = 0, workload: int = 6):
     """alpha * U with U_ij ~ U(-0.5, 0.5) (Sec. 5.1's perturbation of S^{-1/2})."""
     return alpha * rng(workload, seed).uniform(-0.5, 0.5, (n, n))

@@ -30,7 +30,7 @@ EXPORTED = (
     "zfact_default_opts", "zfact_create", "zfact_destroy", "zfact_last_error", "zfact_refine",
     "zfact_refine_batched", "zfact_features", "zfact_mlp_forward", "zfact_mlp_backward",
     "zfact_mlp_adam", "zfact_propose", "zfact_gemm", "zfact_split", "zfact_residual",
-    "zfact_set_profiling", "zfact_kernel_stats", "zfact_residual_noalloc",
+    "zfact_set_profiling", "zfact_kernel_stats", "zfact_residual_noalloc", "zfact_congruence",
 )
 
 
@@ -93,6 +93,7 @@ def load(path: Optional[str] = None):
     lib.zfact_set_profiling.argtypes = [P, I]
     lib.zfact_kernel_stats.argtypes = [P, P, I, ctypes.POINTER(I), I]
     lib.zfact_residual_noalloc.argtypes = [P, P, I64, P, P, P]
+    lib.zfact_congruence.argtypes = [P, P, P, I64, I, I, P]
     for name in EXPORTED:
         if getattr(lib, name).restype is ctypes.c_int or name in ("zfact_default_opts", "zfact_destroy",
                                                                       "zfact_last_error"):
@@ -294,6 +295,20 @@ class Context:
         rc = self.lib.zfact_residual(self.h, REFINE_MODE[mode], _ptr(S), _ptr(Z), n, _ptr(D), ctypes.byref(err))
         self._raise(rc)
         return err.value
+
+    def congruence(self, H, Z, precision: str = "fp64", mode: str = "ozaki", Hp=None):
+        """zfact_congruence: H_perp = Z^T H Z (H symmetric), device or host operands."""
+        n = int(H.shape[0])
+        _check_f64(H, n, "H")
+        _check_f64(Z, n, "Z")
+        if Hp is None:
+            Hp = H.new_empty((n, n)) if hasattr(H, "new_empty") else np.empty((n, n))
+        _check_f64(Hp, n, "Hp")
+        self._ready(H, Z, Hp)
+        rc = self.lib.zfact_congruence(self.h, _ptr(H), _ptr(Z), n, PRECISION[precision], REFINE_MODE[mode],
+                                       _ptr(Hp))
+        self._raise(rc)
+        return Hp
 
     # ------------------------------------------------------------ learned start
     def features(self, S):

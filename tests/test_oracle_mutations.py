@@ -89,3 +89,22 @@ def test_gradient_mutant_is_caught():
 
     with pytest.raises(AssertionError):
         pins.check_mlp_gradient(bad_backward)
+
+
+CONGRUENCE_MUTANTS = {
+    "transposed_operand": lambda H, Z: oracle.matmul(Z, oracle.matmul(H, Z.T)),
+    "missing_right_factor": lambda H, Z: oracle.matmul(Z.T, H),
+    "transpose_dropped": lambda H, Z: oracle.matmul(Z, oracle.matmul(H, Z)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CONGRUENCE_MUTANTS))
+def test_congruence_mutant_is_caught(name):
+    bad = CONGRUENCE_MUTANTS[name]
+    caught = 0
+    for check in (pins.check_congruence_exact, pins.check_congruence_generalized_eigs):
+        try:
+            check(bad)
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, name

@@ -344,3 +344,46 @@ def test_adam_first_step_is_sign():
     G = g.standard_normal(50)
     P1, m, v = oracle.adam_step(P, G, np.zeros(50), np.zeros(50), 1, lr=1e-2, eps=0.0)
     assert np.allclose(P1 - P, -1e-2 * np.sign(G), rtol=1e-12)
+
+
+# ------------------------------------------------------------------ congruence transform (Sec. 2)
+def check_congruence_exact(cong_fn):
+    """Brute force in exact rational arithmetic on a tiny non-symmetric Z and symmetric H."""
+    g = np.random.default_rng(11)
+    n = 5
+    Z = g.standard_normal((n, n))
+    B = g.standard_normal((n, n))
+    H = B + B.T
+    Hp = cong_fn(H, Z)
+    Zf = [[Fraction(float(v)) for v in r] for r in Z]
+    Hf = [[Fraction(float(v)) for v in r] for r in H]
+    for i in range(n):
+        for j in range(n):
+            ex = sum(Zf[k][i] * Hf[k][l] * Zf[l][j] for k in range(n) for l in range(n))
+            mag = sum(abs(Zf[k][i] * Hf[k][l] * Zf[l][j]) for k in range(n) for l in range(n))
+            assert abs(Fraction(float(Hp[i, j])) - ex) <= Fraction(2.0 ** -50) * mag, (i, j)
+
+
+def check_congruence_generalized_eigs(cong_fn):
+    """With Z Z^T = S^-1 (here Z = S^-1/2 from the generator's own factors), Z^T H Z has the
+    eigenvalues of the generalized problem H c = e S c (Sec. 2): compare with LAPACK's sygv."""
+    n = 60
+    S, Q, lam = synth.householder_spd(n, seed=3)
+    Z = (Q * lam ** -0.5) @ Q.T
+    B = np.random.default_rng(4).standard_normal((n, n))
+    H = B + B.T
+    Hp = cong_fn(H, Z)
+    assert np.array_equal(Hp, Hp.T)
+    e_gen = scipy.linalg.eigh(H, S, eigvals_only=True)
+    e = np.linalg.eigvalsh(Hp)
+    assert np.allclose(e, e_gen, rtol=0, atol=1e-11 * np.max(np.abs(e_gen))), np.max(np.abs(e - e_gen))
+    # H = S: the transform of the overlap itself is the identity (Eq. Def_Z)
+    assert np.max(np.abs(cong_fn(S, Z) - np.eye(n))) <= 1e-12
+
+
+def test_congruence_exact():
+    check_congruence_exact(oracle.congruence)
+
+
+def test_congruence_generalized_eigenvalues():
+    check_congruence_generalized_eigs(oracle.congruence)
