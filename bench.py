@@ -278,11 +278,14 @@ def run_ours(args, rank, ws, local):
                       "refined_iters": r32r.info["refine_iters"]})
 
     # diagonalization comparator (cuSOLVER), once warm: time and the residual of its S^{-1/2}
-    eigh_inverse_sqrt(S)
-    Ze, eigh_ms = eigh_inverse_sqrt(S)
-    eigh_info = {"ms": round(eigh_ms, 3), "resid": ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n),
-                 "how": "torch.linalg.eigh (cuSOLVER syevd, FP64) + V diag(lambda^-1/2) V^T (cuBLAS)"}
-    del Ze
+    try:
+        eigh_inverse_sqrt(S)
+        Ze, eigh_ms = eigh_inverse_sqrt(S)
+        eigh_info = {"ms": round(eigh_ms, 3), "resid": ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n),
+                     "how": "torch.linalg.eigh (cuSOLVER syevd, FP64) + V diag(lambda^-1/2) V^T (cuBLAS)"}
+        del Ze
+    except RuntimeError as e:  # e.g. torch's linalg library cannot be loaded (seen under a profiler)
+        eigh_info = {"unavailable": str(e).splitlines()[0][:200]}
 
     # e2e: host (pinned) buffers through the public C ABI, copies inside the call
     S_pin = torch.from_numpy(S_host).pin_memory()
@@ -354,7 +357,7 @@ def run_ours(args, rank, ws, local):
             "fp32_path": fp32_info,
             "eigh_comparator": eigh_info,
             "speedup_vs_fp64_path": round(fp64_ms / ms, 2),
-            "speedup_vs_eigh": round(eigh_info["ms"] / ms, 2),
+            "speedup_vs_eigh": round(eigh_info["ms"] / ms, 2) if "ms" in eigh_info else None,
             "tc_tflops": round(tc_fl / (tc_ms * 1e-3) / 1e12, 1) if tc_ms > 0 else None,
             "kernels": sorted([{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
                                for s in stats], key=lambda s: -s["ms"]),
@@ -526,12 +529,15 @@ def run_ill(args):
         e1.synchronize()
         out["fp64_path"] = {"ms": e0.elapsed_time(e1), "iters": r64.info["iters"],
                             "resid": r64.info["resid_f"] / math.sqrt(n), "hist": [float(h) for h in r64.hist]}
-        with torch.cuda.stream(stream):
-            eigh_inverse_sqrt(S[:256, :256].contiguous())  # warm the solver
-            Ze, eigh_ms = eigh_inverse_sqrt(S)
-        out["eigh_comparator"] = {"ms": round(eigh_ms, 1),
-                                  "resid": ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n)}
-        del Ze
+        try:
+            with torch.cuda.stream(stream):
+                eigh_inverse_sqrt(S[:256, :256].contiguous())  # warm the solver
+                Ze, eigh_ms = eigh_inverse_sqrt(S)
+            out["eigh_comparator"] = {"ms": round(eigh_ms, 1),
+                                      "resid": ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n)}
+            del Ze
+        except RuntimeError as e:
+            out["eigh_comparator"] = {"unavailable": str(e).splitlines()[0][:200]}
     ctx.close()
     print(json.dumps(out), flush=True)
 
@@ -569,11 +575,15 @@ def run_paper(args):
             r64 = ctx.refine(S, Z0, order=2, precision="fp64", Z=Z, raise_on_error=False)
             row["fp64_iters"] = r64.info["iters"]
             row["fp64_hist"] = [float(x) for x in r64.hist]
-        with torch.cuda.stream(stream):
-            Ze, eigh_ms = eigh_inverse_sqrt(S)
-        row["eigh_ms"] = round(eigh_ms, 2)
-        row["eigh_resid"] = ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n)
-        del Ze, S, Z0, Z
+        try:
+            with torch.cuda.stream(stream):
+                Ze, eigh_ms = eigh_inverse_sqrt(S)
+            row["eigh_ms"] = round(eigh_ms, 2)
+            row["eigh_resid"] = ctx.residual(S, Ze.contiguous(), "ozaki") / math.sqrt(n)
+            del Ze
+        except RuntimeError as e:
+            row["eigh_unavailable"] = str(e).splitlines()[0][:200]
+        del S, Z0, Z
         torch.cuda.empty_cache()
         rows.append(row)
         print(json.dumps(row), file=sys.stderr, flush=True)
