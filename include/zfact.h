@@ -75,11 +75,15 @@ typedef enum zfact_precision {
 /* How the refinement (Algorithm 3) forms d = I - Z^T S Z in FP64 accuracy. */
 typedef enum zfact_refine_mode {
     ZFACT_R_NATIVE = 0,      /* FP64 CUDA-core products */
-    ZFACT_R_OZAKI = 1        /* error-free slicing of Z and S into BF16 integer slices with exact
+    ZFACT_R_OZAKI = 1,       /* error-free slicing of Z and S into BF16 integer slices with exact
                                 FP32 tensor-core accumulation (Ozaki, Ogita, Oishi, Rump,
                                 "Error-free transformations of matrix multiplication by using
                                 fast routines of matrix multiplication and its applications",
                                 Numer. Algorithms 59 (2012)) */
+    ZFACT_R_FP32 = 2         /* single precision, Table I's "(h)(h)+refi" step: d, Q and Z + Z Q by
+                                FP32 CUDA-core products (reaches the FP32 floor only); the final
+                                residual of the returned Z is still formed to FP64 accuracy.
+                                Mixed bulks only (zfact_refine with a 16-bit precision) */
 } zfact_refine_mode;
 
 typedef struct zfact_opts {

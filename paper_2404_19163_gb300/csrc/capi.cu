@@ -294,6 +294,8 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   if (o.nmax < 1) o.nmax = 1;
   if (o.refine_steps < 0) o.refine_steps = (precision == ZFACT_P_FP64 || precision == ZFACT_P_FP32) ? 0 : 3;
   if (o.refine_mode < 0) o.refine_mode = ZFACT_R_OZAKI;
+  if (o.refine_mode != ZFACT_R_NATIVE && o.refine_mode != ZFACT_R_OZAKI && o.refine_mode != ZFACT_R_FP32)
+    return ctx_fail(c, ZFACT_ERR_ARG, "unknown refine mode %d", o.refine_mode);
   const int n = (int)N;
   const size_t nn = (size_t)n * n, bytes = nn * sizeof(double);
   zfact_info inf;

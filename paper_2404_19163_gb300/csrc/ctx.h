@@ -108,6 +108,8 @@ int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, i
 // Algorithm 3 with FP64-accurate sliced products, from the FP64 iterate Z64 (mixed.cu)
 int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o, int iters,
                  int* ridx_out, zfact_info* inf);
+int refine_fp32(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o, int iters,
+                int* ridx_out, zfact_info* inf);
 // The paper's "single": every bulk product in FP32 on the CUDA cores (single.cu)
 int single_refine(zfact_ctx* c, const double* S, double* Za64, int n, int order, const zfact_opts& o, int* iters_out,
                   int* ridx_out, zfact_info* inf);

@@ -522,6 +522,8 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   }
   if (o.refine_mode == ZFACT_R_OZAKI) {
     if ((st = refine_ozaki(c, S, Z64, n, order, o, iters, &ridx, inf))) return st;
+  } else if (o.refine_mode == ZFACT_R_FP32) {
+    if ((st = refine_fp32(c, S, Z64, n, order, o, iters, &ridx, inf))) return st;
   } else {
     if ((st = refine_native(c, S, Z64, n, order, o, iters, &ridx, inf, D32, ld, bn))) return st;
   }

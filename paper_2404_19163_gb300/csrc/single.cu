@@ -110,3 +110,82 @@ int single_refine(zfact_ctx* c, const double* S, double* Za64, int n, int order,
   }
   return refine_ozaki(c, S, Za64, n, order, o, iters, ridx_out, inf);
 }
+
+// Algorithm 3's refinement in single precision (Table I "(h)(h)+refi" with its FP32 step): up to
+// refine_steps updates of the bulk's Z with d, Q and Z + Z Q formed by FP32 CUDA-core products
+// (their Err, FP32-accurate, goes to the history), then the FP64-accurate residual of the result.
+int refine_fp32(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o, int iters,
+                int* ridx_out, zfact_info* inf) {
+  int st = ZFACT_OK;
+  const size_t nn = (size_t)n * n;
+  const char* names[6] = {"r32.S", "r32.Za", "r32.Zb", "r32.A", "r32.D", "r32.Q"};
+  float* b[6];
+  for (int k = 0; k < 6; ++k) {
+    b[k] = (float*)ctx_buf(c, names[k], sizeof(float) * nn, &st);
+    if (!b[k]) return st;
+  }
+  float *S32 = b[0], *Zc = b[1], *Zn = b[2], *A = b[3], *D = b[4], *Q = b[5];
+  float *P = nullptr, *P2 = nullptr;
+  if (order > 2) {
+    P = (float*)ctx_buf(c, "r32.P", sizeof(float) * nn, &st);
+    if (!P) return st;
+    P2 = (float*)ctx_buf(c, "r32.P2", sizeof(float) * nn, &st);
+    if (!P2) return st;
+  }
+  const int nb = f64_num_blocks(n, true);
+  double* partials = (double*)ctx_buf(c, "partials", sizeof(double) * (size_t)(nb + 1024), &st);
+  if (!partials) return st;
+  const double n2 = (double)n * n, n3 = n2 * n;
+  double coef[8];
+  coef[0] = 1.0;
+  for (int k = 1; k <= order; ++k) coef[k] = coef[k - 1] * (2.0 * k - 1.0) / (2.0 * k);
+  auto elem = [&](const char* w, auto&& f) { return ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, f), w); };
+  if ((st = elem("S32", [&] { return launch_f64_to_f32(S, n, n, S32, n, c->stream); }))) return st;
+  if ((st = elem("Z32", [&] { return launch_f64_to_f32(Z64, n, n, Zc, n, c->stream); }))) return st;
+  int idx = iters, ridx = 0;
+  for (int r = 0; r < o.refine_steps && idx + 2 < kHistMax; ++r) {
+    ++idx;
+    F32Gemm g1{S32, Zc, A, nullptr, nullptr, 0.0, 1.0, nullptr, n, false, false, false};
+    F32Gemm g2{Zc, A, D, nullptr, nullptr, 0.0, 1.0, partials, n, true, true, true};
+    if ((st = ctx_cuda(c, klaunch(c, "f32_gemm.sz", 2 * n3, 12 * n2, 1, [&] { return launch_f32_gemm(g1, c->stream); }),
+                       "f32 S*Z")))
+      return st;
+    if ((st = ctx_cuda(c, klaunch(c, "f32_gemm.resid", n3, 12 * n2, 1, [&] { return launch_f32_gemm(g2, c->stream); }),
+                       "f32 residual")))
+      return st;
+    if ((st = ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
+                         return launch_finish_err(partials, nb, c->st_dev, idx, o.stop_rule, o.tol, n, 0, c->stream);
+                       }),
+                       "finish err")))
+      return st;
+    if ((st = ctx_read_state(c))) return st;
+    if (c->st_host->nonfinite) break;
+    if (o.tol > 0 && c->st_host->hist[idx] / sqrt((double)n) <= o.tol) break;
+    F32Gemm gp{D, D, Q, D, order > 2 ? P : nullptr, coef[1], coef[2], nullptr, n, false, true, false};
+    if ((st = ctx_cuda(c, klaunch(c, "f32_gemm.poly", n3, 12 * n2, 1, [&] { return launch_f32_gemm(gp, c->stream); }),
+                       "f32 poly")))
+      return st;
+    float *Pa = P, *Pb = P2;
+    for (int k = 3; k <= order; ++k) {
+      F32Gemm gk{Pa, D, Q, Q, k < order ? Pb : nullptr, 1.0, coef[k], nullptr, n, false, true, false};
+      if ((st = ctx_cuda(c, klaunch(c, "f32_gemm.poly", n3, 16 * n2, 1, [&] { return launch_f32_gemm(gk, c->stream); }),
+                         "f32 poly chain")))
+        return st;
+      std::swap(Pa, Pb);
+    }
+    F32Gemm gu{Zc, Q, Zn, Zc, nullptr, 1.0, 1.0, nullptr, n, false, false, false};
+    if ((st = ctx_cuda(c, klaunch(c, "f32_gemm.update", 2 * n3, 12 * n2, 1, [&] { return launch_f32_gemm(gu, c->stream); }),
+                       "f32 update")))
+      return st;
+    std::swap(Zc, Zn);
+    ++ridx;
+  }
+  *ridx_out = ridx;
+  if (ridx > 0 && (st = elem("Z to FP64", [&] { return launch_f32_to_f64(Zc, n, n, Z64, n, c->stream); }))) return st;
+  if (!o.final_residual || c->st_host->nonfinite) return ZFACT_OK;
+  // the FP64-accurate residual of the returned Z, after the FP32 entries of the history
+  zfact_opts of = o;
+  of.refine_steps = 0;
+  int unused = 0;
+  return refine_ozaki(c, S, Z64, n, order, of, idx, &unused, inf);
+}

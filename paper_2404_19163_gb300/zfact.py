@@ -23,7 +23,7 @@ ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR
 WARN_NONCONTRACTIVE = 100
 
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 3, "fp16": 4, "fp16_split": 5, "bf16_split": 6}
-REFINE_MODE = {"native": 0, "ozaki": 1}
+REFINE_MODE = {"native": 0, "ozaki": 1, "fp32": 2}
 MLP_NPARAMS = 5573
 
 EXPORTED = (

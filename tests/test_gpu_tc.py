@@ -190,3 +190,27 @@ def test_fp32_single_path_reaches_its_floor_and_refines(ctx):
     r2 = ctx.refine(dev(S), None, order=2, precision="fp32", refine_steps=2, tol=1e-12)
     _, e2 = oracle.residual(S, r2.Z.cpu().numpy())
     assert e2 / math.sqrt(200) <= 1e-12
+
+
+def test_hh_with_single_precision_refinement(ctx):
+    """Table I's "(h)(h)+refi" with its FP32 step: from the BF16 (h)(h) bulk, one refinement update
+    with d, Q and Z + ZQ in FP32 takes the residual far below the bulk's floor but not to FP64's;
+    the history holds the step's FP32 Err and then the FP64-accurate residual of the returned Z."""
+    S = synth.cubic_overlap(n_side=10)
+    n = S.shape[0]
+    rb = ctx.refine(dev(S), None, order=2, precision="bf16", refine_steps=0)
+    r = ctx.refine(dev(S), None, order=2, precision="bf16", refine_mode="fp32", refine_steps=1)
+    assert r.info["iters"] == rb.info["iters"] and r.info["refine_iters"] == 1
+    assert len(r.hist) == r.info["iters"] + 3 and r.hist[-1] == r.info["resid_f"]
+    _, e = oracle.residual(S, r.Z.cpu().numpy())
+    assert abs(r.info["resid_f"] - e) <= 1e-3 * e
+    assert e < 1e-2 * rb.info["resid_f"]
+    assert 1e-10 <= e / math.sqrt(n) <= 1e-5
+
+
+def test_unknown_refine_mode_rejected(ctx):
+    from paper_2404_19163_gb300.zfact import ZfactError
+    S, Q, lam = synth.householder_spd(64, seed=2)
+    with pytest.raises(ZfactError) as ei:
+        ctx.refine(dev(S), None, order=2, precision="bf16", refine_mode=7)
+    assert ei.value.code == 1
