@@ -337,6 +337,36 @@ __global__ void __launch_bounds__(NT) k_oz_rowslice_reg(const double* __restrict
     slice_digits_offset((er > -1000) ? fixed_point(last, er, T) : 0, D, T, s, b, orow + (n - 1), stride);
 }
 
+// The exact groups of four rows of one column: T_t = sum_c G[t * nch + c] as int32 (below nch 2^24 <= 2^31),
+// folded into I (t < k0) and J (k0 <= t < k1).  NCH > 0 fixes the chunk count at compile time so the
+// chunk loop unrolls; with the group loop unrolled twice, 2 NCH 4 loads are in flight per thread.
+template <int NCH>
+__device__ __forceinline__ void exact_groups(const float* __restrict__ G, size_t gstride, int nch_rt, int k0, int k1,
+                                             int b, const bool (&ok)[4], const size_t (&off)[4], long long (&I)[4],
+                                             long long (&J)[4]) {
+  const int nch = NCH > 0 ? NCH : nch_rt;
+  const long long w = 1ll << b;
+#pragma unroll 2
+  for (int t = 0; t < k1; ++t) {
+    const float* g = G + (size_t)t * nch * gstride;
+    int tt[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int c = 0; c < (NCH > 0 ? NCH : nch); ++c) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (ok[q]) tt[q] += __float2int_rn(__ldcs(g + off[q]));
+      g += gstride;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (t < k0)
+        I[q] = I[q] * w + tt[q];
+      else
+        J[q] = J[q] * w + tt[q];
+    }
+  }
+}
+
 // Sum of the groups with the scales: val = 2^{eA_i + eB_j} 2^{-2b} sum_t 2^{-bt} T_t,
 // T_t = sum_c G[t * nch + c] (exact integers, |T_t| < 2^30).  Two 64-bit integers hold the
 // groups exactly: I = sum_{t<k0} T_t 2^{b(k0-1-t)} and J = sum_{k0<=t<k1} T_t 2^{b(k1-1-t)}
@@ -375,36 +405,13 @@ __global__ void k_oz_combine(const float* __restrict__ G, size_t gstride, int ld
       ok[q] = i < n && j < n;
       off[q] = ok[q] ? (size_t)i * ld32 + j : 0;
     }
-    long long I[4] = {0, 0, 0, 0}, J[4] = {0, 0, 0, 0}, tt[4] = {0, 0, 0, 0};
-    // the exact groups' slots u = t * nch + c in order, four slots (sixteen loads) in flight
-    const int nu = k1 * nch;
-    int t = 0, c = 0;
-    for (int u0 = 0; u0 < nu; u0 += 4) {
-      float v[4][4];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        const float* g = G + (size_t)(u0 + x) * gstride;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[x][q] = (u0 + x < nu && ok[q]) ? __ldcs(g + off[q]) : 0.0f;
-      }
-#pragma unroll
-      for (int x = 0; x < 4; ++x) {
-        if (u0 + x >= nu) break;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) tt[q] += __float2int_rn(v[x][q]);
-        if (++c == nch) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            if (t < k0)
-              I[q] = I[q] * (1ll << b) + tt[q];
-            else
-              J[q] = J[q] * (1ll << b) + tt[q];
-            tt[q] = 0;
-          }
-          c = 0;
-          ++t;
-        }
-      }
+    long long I[4] = {0, 0, 0, 0}, J[4] = {0, 0, 0, 0};
+    switch (nch) {
+      case 1: exact_groups<1>(G, gstride, nch, k0, k1, b, ok, off, I, J); break;
+      case 2: exact_groups<2>(G, gstride, nch, k0, k1, b, ok, off, I, J); break;
+      case 3: exact_groups<3>(G, gstride, nch, k0, k1, b, ok, off, I, J); break;
+      case 4: exact_groups<4>(G, gstride, nch, k0, k1, b, ok, off, I, J); break;
+      default: exact_groups<0>(G, gstride, nch, k0, k1, b, ok, off, I, J); break;
     }
     float F[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int t = s - 1; t >= k1; --t) {
