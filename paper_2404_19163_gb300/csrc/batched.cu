@@ -405,6 +405,24 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
     for (int l = 0; l < L; ++l)
       if (!c->lane_stream[l] && cudaStreamCreateWithFlags(&c->lane_stream[l], cudaStreamNonBlocking) != cudaSuccess)
         return ctx_fail(c, ZFACT_ERR_CUDA, "lane stream");
+    // every instance's slice count from its dynamic range, as in the single-instance refinement
+    unsigned long long* rng = (unsigned long long*)ctx_buf(c, "b.ranges", 16 * (size_t)count, &st);
+    if (!rng) return st;
+    std::vector<unsigned long long> hr(2 * (size_t)count);
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
+                         return launch_b_ranges(t, count, max_n, rng, rng + count, c->stream);
+                       }),
+                       "batch ranges")))
+      return st;
+    cudaMemcpyAsync(hr.data(), rng, 16 * (size_t)count, cudaMemcpyDeviceToHost, c->stream);
+    if ((st = ctx_cuda(c, cudaStreamSynchronize(c->stream), "ranges read-back"))) return st;
+    std::vector<int> slices(count);
+    for (int i = 0; i < count; ++i) {
+      double g, z;
+      memcpy(&g, &hr[i], 8);
+      memcpy(&z, &hr[count + i], 8);
+      slices[i] = oz_slices_for(z, g);
+    }
     cudaEvent_t fork = ev_get(c);
     cudaEvent_t join[zfact_ctx::kLanes];
     for (int l = 0; l < L; ++l) join[l] = ev_get(c);
@@ -421,7 +439,7 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
           c->lane = -1;
           return st;
         }
-        st = oz_prepare_S(c, S[i], n[i]);
+        st = oz_prepare_S(c, S[i], n[i], slices[i]);
         if (!st) st = oz_residual(c, Z[i], D64, n[i], l, 0, 0.0, 0);
         cudaEventRecord(join[l], c->lane_stream[l]);
         c->lane = -1;

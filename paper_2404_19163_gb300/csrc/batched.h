@@ -27,6 +27,9 @@ struct BatchState {
 
 cudaError_t launch_b_gersh(const BatchTables& t, int count, int max_n, unsigned long long* gmax_bits,
                            cudaStream_t s);
+// g_i (largest absolute row sum of S_i) and z_i (largest |Z_i|) as FP64 bits, for every instance.
+cudaError_t launch_b_ranges(const BatchTables& t, int count, int max_n, unsigned long long* gmax_bits,
+                            unsigned long long* zmax_bits, cudaStream_t s);
 cudaError_t launch_b_pack(const BatchTables& t, int count, int max_n, int mode, const unsigned long long* gmax_bits,
                           int ld, bool bf16, uint16_t* h16, uint16_t* l16, uint16_t* th16, uint16_t* tl16, float* m32,
                           cudaStream_t s);

@@ -37,7 +37,10 @@ void* ctx_buf(zfact_ctx* c, const char* name, size_t bytes, int* status) {
   auto it = c->bufs.find(name);
   if (it != c->bufs.end() && it->second.bytes >= bytes) return it->second.ptr;
   if (it != c->bufs.end()) {
+    // the old buffer may still be read by queued work: the context's stream, or the current lane's
+    // (lane buffers are private to their lane)
     cudaStreamSynchronize(c->stream);
+    if (c->lane >= 0 && c->lane_stream[c->lane]) cudaStreamSynchronize(c->lane_stream[c->lane]);
     cudaFree(it->second.ptr);
     c->bufs.erase(it);
   }

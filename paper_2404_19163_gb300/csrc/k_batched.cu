@@ -31,6 +31,32 @@ __global__ void k_b_rowabs(const BatchTables t, unsigned long long* gmax_bits) {
   if (lane == 0) atomicMax(&gmax_bits[i], (unsigned long long)__double_as_longlong(s));
 }
 
+// Dynamic range of every instance for its FP64-accurate residual: g_i = max_r sum_c |S_i[r][c]|
+// and z_i = max |Z_i| (the returned FP64 Z).  One warp per row, grid.y = instance.
+__global__ void k_b_ranges(const BatchTables t, unsigned long long* gmax_bits, unsigned long long* zmax_bits) {
+  const int i = blockIdx.y;
+  const int n = t.n[i];
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* S = t.S[i] + (size_t)row * n;
+  const double* Z = t.Z[i] + (size_t)row * n;
+  double g = 0.0, z = 0.0;
+  for (int c = lane; c < n; c += 32) {
+    g += fabs(S[c]);
+    z = fmax(z, fabs(Z[c]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    g += __shfl_xor_sync(0xffffffffu, g, o);
+    z = fmax(z, __shfl_xor_sync(0xffffffffu, z, o));
+  }
+  if (lane == 0) {
+    atomicMax(&gmax_bits[i], (unsigned long long)__double_as_longlong(g));
+    atomicMax(&zmax_bits[i], (unsigned long long)__double_as_longlong(z));
+  }
+}
+
 // Pack instance i (grid.z) into the stacked buffers, 32 x 32 tiles through shared memory:
 //   mode 0: S16 (hi[, lo]) from S_i
 //   mode 1: Z master (FP32) + Z16 and Zt16 (hi[, lo]) from Z0_i, or from s_i I when Z0_i is null
@@ -134,6 +160,15 @@ cudaError_t launch_b_gersh(const BatchTables& t, int count, int max_n, unsigned 
   cudaMemsetAsync(gmax_bits, 0, sizeof(unsigned long long) * count, s);
   dim3 grid((max_n + 7) / 8, count);
   k_b_rowabs<<<grid, 256, 0, s>>>(t, gmax_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_b_ranges(const BatchTables& t, int count, int max_n, unsigned long long* gmax_bits,
+                            unsigned long long* zmax_bits, cudaStream_t s) {
+  cudaMemsetAsync(gmax_bits, 0, sizeof(unsigned long long) * count, s);
+  cudaMemsetAsync(zmax_bits, 0, sizeof(unsigned long long) * count, s);
+  dim3 grid((max_n + 7) / 8, count);
+  k_b_ranges<<<grid, 256, 0, s>>>(t, gmax_bits, zmax_bits);
   return cudaGetLastError();
 }
 

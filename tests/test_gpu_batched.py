@@ -83,3 +83,17 @@ def test_batched_fixed_iters_and_errors(ctx):
     Sn[3, 4] = Sn[4, 3] = np.nan
     with pytest.raises(ZfactError):
         ctx.refine_batched([Ss[0], torch.from_numpy(Sn).cuda()], None, precision="bf16")
+
+
+def test_batched_residuals_of_mixed_conditioning(ctx):
+    """Every instance gets the slice count of its own dynamic range (as the single-instance path
+    does), so the reported residual of an ill-conditioned member (fcc block, cond ~7e4) agrees with
+    the oracle's FP64 residual of the returned Z as closely as the well-conditioned members'."""
+    import torch
+    Ss = [synth.fcc_overlap(cells=(2, 2, 4)), synth.householder_spd(300, seed=5)[0],
+          synth.gaussian_overlap(synth.cluster_sites(200, 7)), synth.fcc_overlap(cells=(2, 2, 2))]
+    St = [torch.from_numpy(S).cuda() for S in Ss]
+    Z, hist, info, status = ctx.refine_batched(St, None, precision="bf16_split")
+    for S, z, inf in zip(Ss, Z, info):
+        _, e = oracle.residual(S, z.cpu().numpy())
+        assert abs(inf["resid_f"] - e) <= 1e-6 * e, (inf["resid_f"], e)
