@@ -119,3 +119,23 @@ def test_workload2_full_size_against_oracle(ctx):
     Zo, ho, ito = oracle.refine(S, None, m=2, nmax=50, fixed_iters=it)
     assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
     assert r.info["resid_f"] / math.sqrt(n) < 1e-13
+
+
+def test_inputs_written_on_another_stream_are_ordered(ctx):
+    """S produced by a long torch product on a non-default current stream, passed at once: the binding
+    waits for that stream, so the factorization reads the finished S (the context works on its own
+    stream, which is not ordered after torch's)."""
+    import torch
+    n = 1500
+    side = torch.cuda.Stream()
+    g = torch.Generator(device="cuda").manual_seed(3)
+    with torch.cuda.stream(side):
+        B = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+        S = B @ B.T / n
+        for _ in range(6):          # keep the stream busy well past the call below
+            S = 0.5 * (S + S @ S.T / torch.linalg.matrix_norm(S, 2))
+        S.diagonal().add_(1.0)
+        r = ctx.refine(S, None, order=2, precision="fp64")
+    torch.cuda.synchronize()
+    _, e = oracle.residual(S.cpu().numpy(), r.Z.cpu().numpy())
+    assert abs(r.info["resid_f"] - e) <= 1e-12 and e / math.sqrt(n) <= 1e-12
