@@ -544,37 +544,46 @@ def run_ill(args):
 
 def run_paper(args):
     """The paper's synthetic overlap (Sec. 5.1): S = (T + T^T)/2 shifted to lambda_min = 0.5,
-    Z0 = S^{-1/2} + 0.005 U, solved with the (h)(h)+(h)(l)+(l)(h) method (FP16 hi/lo split,
-    Table I) under Algorithm 2's stop and Algorithm 3's refinement: iterations, the Frobenius
-    history and the stop ratios Err_n / Err_{n-1}^3 of Fig. 1, time, the FP64 path's iterations
-    (N <= 4096) and the diagonalization comparator.  One JSON line."""
+    Z0 = S^{-1/2} + 0.005 U.  For every N, each method of Table I that the library offers runs from
+    that Z0 under Algorithm 2's stop (Fig. 2): the (h)(h)+(h)(l)+(l)(h) split with and without the
+    FP64-accurate refinement, (h)(h) with and without a single-precision refinement step, single,
+    and double (N <= 4096).  Per method: iterations, the Frobenius history, the stop ratios
+    Err_n / Err_{n-1}^3 (Fig. 1, Fig. 2 top), the FP64-accurate residual of the result and the time
+    (Fig. 3), with cuSOLVER's eigh as the diagonalization comparator.  One JSON line."""
     import torch
     from paper_2404_19163_gb300 import Context, synth, build as zbuild
     zbuild.build()
     stream = torch.cuda.Stream()
     ctx = Context(0, stream=stream)
+    methods = [("split+refi", dict(precision="fp16_split", tol=TOL)),
+               ("split", dict(precision="fp16_split", refine_steps=0)),
+               ("hh+refi_fp32", dict(precision="fp16", refine_mode="fp32", refine_steps=1)),
+               ("hh", dict(precision="fp16", refine_steps=0)),
+               ("single", dict(precision="fp32")),
+               ("double", dict(precision="fp64"))]
     rows = []
     for n in [int(x) for x in args.paper_sizes.split(",")]:
         S = synth.paper_synthetic_torch(n)
         Z0 = synth.paper_start_torch(S, 0.005, seed=0)
         Z = torch.empty_like(S)
-        kw = dict(order=2, precision="fp16_split", tol=TOL, Z=Z, raise_on_error=False)
-        ctx.refine(S, Z0, **kw)  # warm-up
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r = ctx.refine(S, Z0, **kw)
-        e1.record(stream)
-        e1.synchronize()
-        h = [float(x) for x in r.hist]
-        it = r.info["iters"]
-        row = {"N": n, "iters": it, "refine_iters": r.info["refine_iters"], "status": r.status,
-               "ms": round(e0.elapsed_time(e1), 3), "resid": r.info["resid_f"] / math.sqrt(n), "hist": h,
-               "stop_ratios": [h[i] / h[i - 1] ** 3 for i in range(1, it + 1)]}
-        if n <= 4096:
-            r64 = ctx.refine(S, Z0, order=2, precision="fp64", Z=Z, raise_on_error=False)
-            row["fp64_iters"] = r64.info["iters"]
-            row["fp64_hist"] = [float(x) for x in r64.hist]
+        row = {"N": n, "methods": {}}
+        for name, kw in methods:
+            if name == "double" and n > 4096:
+                continue
+            kw = dict(order=2, Z=Z, raise_on_error=False, **kw)
+            ctx.refine(S, Z0, **kw)  # warm-up
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = ctx.refine(S, Z0, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            h = [float(x) for x in r.hist]
+            it = r.info["iters"]
+            row["methods"][name] = {
+                "iters": it, "refine_iters": r.info["refine_iters"], "status": r.status,
+                "ms": round(e0.elapsed_time(e1), 3), "resid": r.info["resid_f"] / math.sqrt(n), "hist": h,
+                "stop_ratios": [h[i] / h[i - 1] ** 3 for i in range(1, it + 1)]}
         try:
             with torch.cuda.stream(stream):
                 Ze, eigh_ms = eigh_inverse_sqrt(S)
@@ -586,10 +595,11 @@ def run_paper(args):
         del S, Z0, Z
         torch.cuda.empty_cache()
         rows.append(row)
-        print(json.dumps(row), file=sys.stderr, flush=True)
+        print(json.dumps({"N": n, **{k: (v["iters"], v["ms"], v["resid"]) for k, v in row["methods"].items()},
+                          "eigh_ms": row.get("eigh_ms")}), file=sys.stderr, flush=True)
     ctx.close()
-    print(json.dumps({"workload": "paper_synthetic_sweep", "alpha": 0.005, "gamma": 0.5,
-                      "precision": "fp16_split", "tol": TOL, "rows": rows}), flush=True)
+    print(json.dumps({"workload": "paper_synthetic_sweep", "alpha": 0.005, "gamma": 0.5, "tol": TOL,
+                      "rows": rows}), flush=True)
 
 
 def main():
