@@ -239,6 +239,21 @@ int zfact_residual(zfact_ctx* ctx, int refine_mode, const double* S, const doubl
 int zfact_congruence(zfact_ctx* ctx, const double* H, const double* Z, int64_t N, int precision,
                      int refine_mode, double* Hp);
 
+/* ---- workspace cap ------------------------------------------------------------------
+ * Caps the device workspace the context may hold at `bytes` (0 = no cap, the default).  A call that
+ * would grow the workspace past the cap fails with ZFACT_ERR_NOMEM before allocating, and the
+ * context stays usable (raise the cap, or call again with a smaller problem).  Buffers already held
+ * are not freed.  No counterpart in the paper: it bounds what a context takes from a shared GPU. */
+int zfact_set_workspace_limit(zfact_ctx* ctx, int64_t bytes);
+
+/* ---- bounded-wait self-test -----------------------------------------------------------
+ * Launches one block whose mbarrier wait, the bounded wait every tensor-core kernel uses, can never
+ * complete: nothing arrives at the barrier.  The wait gives up after a short poll limit, records
+ * the timeout in the context's device state and returns, and the kernel exits normally.  The call
+ * returns ZFACT_ERR_TIMEOUT (how a real timeout is reported) and the context stays usable.  No
+ * counterpart in the paper: it checks the failure path without faulting or hanging a GPU. */
+int zfact_selftest_timeout(zfact_ctx* ctx);
+
 /* ---- allocation-free residual -------------------------------------------------------
  * d = I - Z^T S Z (FP64 CUDA cores) and ||d||_F, without allocating any device memory.
  * The paper has no counterpart: this entry point exists for callers that cannot call

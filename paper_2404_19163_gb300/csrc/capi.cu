@@ -36,7 +36,14 @@ int ctx_cuda(zfact_ctx* c, cudaError_t e, const char* what) {
 void* ctx_buf(zfact_ctx* c, const char* name, size_t bytes, int* status) {
   auto it = c->bufs.find(name);
   if (it != c->bufs.end() && it->second.bytes >= bytes) return it->second.ptr;
+  const size_t need = bytes < 256 ? 256 : bytes;
+  const size_t held = (it != c->bufs.end()) ? (it->second.bytes < 256 ? 256 : it->second.bytes) : 0;
+  if (c->ws_limit && c->ws_bytes - held + need > c->ws_limit) {
+    *status = ctx_fail(c, ZFACT_ERR_NOMEM, "%s: workspace limit of %zu bytes reached", name, c->ws_limit);
+    return nullptr;
+  }
   if (it != c->bufs.end()) {
+    c->ws_bytes -= held;
     // the old buffer may still be read by queued work: the context's stream, or the current lane's
     // (lane buffers are private to their lane)
     cudaStreamSynchronize(c->stream);
@@ -45,11 +52,12 @@ void* ctx_buf(zfact_ctx* c, const char* name, size_t bytes, int* status) {
     c->bufs.erase(it);
   }
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes < 256 ? 256 : bytes);
+  cudaError_t e = cudaMalloc(&p, need);
   if (e != cudaSuccess) {
     *status = ctx_cuda(c, e, name);
     return nullptr;
   }
+  c->ws_bytes += need;
   c->bufs[name] = DevBuf{p, bytes};
   return p;
 }
@@ -410,4 +418,36 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
     return ctx_fail(c, ZFACT_ERR_NOT_CONVERGED, "final residual %.3e > tol %.3e", inf.resid_f / sqrt((double)n),
                     o.tol);
   return inf.warn ? ZFACT_WARN_NONCONTRACTIVE : ZFACT_OK;
+}
+
+// ----------------------------------------------------------------- workspace cap and self-test
+extern "C" int zfact_set_workspace_limit(zfact_ctx* c, int64_t bytes) {
+  if (!c) return ZFACT_ERR_ARG;
+  if (bytes < 0) return ctx_fail(c, ZFACT_ERR_ARG, "negative workspace limit");
+  c->ws_limit = (size_t)bytes;
+  return ZFACT_OK;
+}
+
+namespace {
+// One mbarrier that nothing arrives at: the production bounded wait must give up, raise the
+// timeout flag and return, leaving the kernel to exit normally.
+__global__ void k_selftest_wait(int* err_flag, uint32_t limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&bar, 0, err_flag, 7, limit);
+}
+}  // namespace
+
+extern "C" int zfact_selftest_timeout(zfact_ctx* c) {
+  if (!c) return ZFACT_ERR_ARG;
+  cudaSetDevice(c->device);
+  cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
+  k_selftest_wait<<<1, 32, 0, c->stream>>>(&c->st_dev->error, 1u << 12);
+  int st = ctx_cuda(c, cudaGetLastError(), "self-test launch");
+  if (st) return st;
+  return ctx_read_state(c);
 }

@@ -69,9 +69,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait: gives up after `limit` polls (each try_wait itself blocks for a
 // hardware-defined interval), raises kErrTimeout and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err_flag, int where) {
-  constexpr uint32_t kLimit = 1u << 24;
-  for (uint32_t i = 0; i < kLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err_flag, int where,
+                                          uint32_t limit = 1u << 24) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if (err_flag && (i & 1023u) == 1023u && *(volatile int*)err_flag & kErrTimeout) return false;
   }

@@ -52,6 +52,8 @@ struct zfact_ctx {
   int oz_s = 9;  // slices per operand of the current residual products
   cudaStream_t lane_stream[kLanes] = {};
   int lane = -1;
+  size_t ws_limit = 0;  // cap on the workspace bytes (0 = none), zfact_set_workspace_limit
+  size_t ws_bytes = 0;  // workspace bytes allocated now
   // encoded TMA descriptors keyed by (address, rows, cols, ld, box rows, type)
   std::map<std::string, CUtensorMap> map_cache;
   // batched mode

@@ -31,6 +31,7 @@ EXPORTED = (
     "zfact_refine_batched", "zfact_features", "zfact_mlp_forward", "zfact_mlp_backward",
     "zfact_mlp_adam", "zfact_propose", "zfact_gemm", "zfact_split", "zfact_residual",
     "zfact_set_profiling", "zfact_kernel_stats", "zfact_residual_noalloc", "zfact_congruence",
+    "zfact_set_workspace_limit", "zfact_selftest_timeout",
 )
 
 
@@ -94,6 +95,8 @@ def load(path: Optional[str] = None):
     lib.zfact_kernel_stats.argtypes = [P, P, I, ctypes.POINTER(I), I]
     lib.zfact_residual_noalloc.argtypes = [P, P, I64, P, P, P]
     lib.zfact_congruence.argtypes = [P, P, P, I64, I, I, P]
+    lib.zfact_set_workspace_limit.argtypes = [P, I64]
+    lib.zfact_selftest_timeout.argtypes = [P]
     for name in EXPORTED:
         if getattr(lib, name).restype is ctypes.c_int or name in ("zfact_default_opts", "zfact_destroy",
                                                                       "zfact_last_error"):
@@ -256,6 +259,15 @@ class Context:
         if raise_on_error or rc not in (OK, WARN_NONCONTRACTIVE, ERR_NONFINITE, ERR_NOT_CONVERGED):
             self._raise(rc)
         return Z_list, hist, [i.as_dict() for i in infos], status
+
+    # ------------------------------------------------------------ workspace cap, self-test
+    def set_workspace_limit(self, nbytes: int = 0):
+        """zfact_set_workspace_limit: cap the device workspace (0 = no cap)."""
+        self._raise(self.lib.zfact_set_workspace_limit(self.h, int(nbytes)))
+
+    def selftest_timeout(self) -> int:
+        """zfact_selftest_timeout: returns the status (ZFACT_ERR_TIMEOUT = 6 when the path works)."""
+        return int(self.lib.zfact_selftest_timeout(self.h))
 
     # ------------------------------------------------------------ per-kernel timing
     def set_profiling(self, on: bool = True):

@@ -139,3 +139,36 @@ def test_inputs_written_on_another_stream_are_ordered(ctx):
     torch.cuda.synchronize()
     _, e = oracle.residual(S.cpu().numpy(), r.Z.cpu().numpy())
     assert abs(r.info["resid_f"] - e) <= 1e-12 and e / math.sqrt(n) <= 1e-12
+
+
+def test_tolerance_not_reached_within_nmax(ctx):
+    """A forced tiny nmax with an unreachable tolerance (Algorithm 1's rule): NOT_CONVERGED, with the
+    history valid up to the failure."""
+    S, Q, lam = synth.householder_spd(64, seed=4)
+    r = ctx.refine(dev(S), None, order=2, precision="fp64", stop_rule=1, tol=1e-30, nmax=2,
+                   raise_on_error=False)
+    assert r.status == 5 and r.info["iters"] == 2 and len(r.hist) >= 3
+
+
+def test_workspace_limit_fails_cleanly(ctx):
+    """A workspace cap below what the call needs: NOMEM before allocating, the context still usable."""
+    from paper_2404_19163_gb300 import Context, ZfactError
+    S, Q, lam = synth.householder_spd(300, seed=6)
+    with Context(0) as c2:
+        c2.set_workspace_limit(1 << 20)
+        with pytest.raises(ZfactError) as e:
+            c2.refine(dev(S), None, order=2, precision="bf16_split")
+        assert e.value.code == 3 and "workspace limit" in c2.last_error()
+        c2.set_workspace_limit(0)
+        r = c2.refine(dev(S), None, order=2, precision="bf16_split", tol=1e-12)
+        assert r.info["resid_f"] / math.sqrt(300) <= 1e-12
+
+
+def test_bounded_wait_times_out_and_context_survives(ctx):
+    """The bounded mbarrier wait of the tensor-core kernels, on a barrier nothing arrives at, gives up
+    and is reported as ZFACT_ERR_TIMEOUT; the next call on the same context works."""
+    assert ctx.selftest_timeout() == 6
+    assert "bounded device wait" in ctx.last_error()
+    S, Q, lam = synth.householder_spd(128, seed=8)
+    r = ctx.refine(dev(S), None, order=2, precision="bf16_split", tol=1e-12)
+    assert r.status in (0, 100) and r.info["resid_f"] / math.sqrt(128) <= 1e-12
