@@ -15,6 +15,7 @@ __global__ void k_rowabs_max(const double* __restrict__ S, int n, IterState* st)
   if (warp >= n) return;
   const double* row = S + (size_t)warp * n;
   double s = 0.0;
+#pragma unroll 4
   for (int j = lane; j < n; j += 32) s += fabs(row[j]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -79,7 +80,10 @@ __global__ void k_cvt16(const T* __restrict__ src, int n, int ld_src, uint16_t* 
   __shared__ uint16_t th[32][33], tl[32][33];
   const double sc = scale_ptr ? (double)*scale_ptr : scale;
   const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+  // blockDim is (32, 8): four rows per thread, unrolled so that their loads are in flight together
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) {
+    const int r = threadIdx.y + 8 * rr;
     const int i = bi + r, j = bj + threadIdx.x;
     uint16_t h = 0, l = 0;
     if (i < n && j < n) {
@@ -91,7 +95,9 @@ __global__ void k_cvt16(const T* __restrict__ src, int n, int ld_src, uint16_t* 
     tl[r][threadIdx.x] = l;
   }
   __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) {
+    const int r = threadIdx.y + 8 * rr;
     int oi, oj;
     uint16_t h, l;
     if (transpose) {
@@ -122,24 +128,28 @@ __global__ void k_split_flat(const double* __restrict__ A, int64_t n, double sca
   }
 }
 
+// Row-by-row copies (grid.y strides over rows, grid.x * blockDim over columns): no per-element division.
 __global__ void k_f64_to_f32(const double* __restrict__ src, int n, int ld64, float* dst, int ld32) {
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = e / n, j = e % n;
-    dst[i * ld32 + j] = (float)src[i * ld64 + j];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const double* s = src + (size_t)i * ld64;
+    float* d = dst + (size_t)i * ld32;
+#pragma unroll 4
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) d[j] = (float)s[j];
   }
 }
 
 __global__ void k_f32_to_f64(const float* __restrict__ src, int n, int ld32, double* dst, int ld64) {
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = e / n, j = e % n;
-    dst[i * ld64 + j] = (double)src[i * ld32 + j];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const float* s = src + (size_t)i * ld32;
+    double* d = dst + (size_t)i * ld64;
+#pragma unroll 4
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) d[j] = (double)s[j];
   }
 }
 
 __global__ void k_amax_f64(const double* __restrict__ A, size_t total, IterState* st, int slot) {
   double m = 0.0;
+#pragma unroll 4
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
     m = fmax(m, fabs(A[e]));
 #pragma unroll
@@ -222,13 +232,18 @@ cudaError_t launch_split_flat(const double* A, int64_t n, double scale, uint16_t
 
 static int grid_for(size_t total) { return (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192); }
 
+static dim3 rows_grid(int n) {
+  const int gx = (n + 255) / 256 < 4 ? (n + 255) / 256 : 4;
+  return dim3(gx > 0 ? gx : 1, n < 2048 ? (n > 0 ? n : 1) : 2048);
+}
+
 cudaError_t launch_f64_to_f32(const double* src, int n, int ld64, float* dst, int ld32, cudaStream_t s) {
-  k_f64_to_f32<<<grid_for((size_t)n * n), 256, 0, s>>>(src, n, ld64, dst, ld32);
+  k_f64_to_f32<<<rows_grid(n), 256, 0, s>>>(src, n, ld64, dst, ld32);
   return cudaGetLastError();
 }
 
 cudaError_t launch_f32_to_f64(const float* src, int n, int ld32, double* dst, int ld64, cudaStream_t s) {
-  k_f32_to_f64<<<grid_for((size_t)n * n), 256, 0, s>>>(src, n, ld32, dst, ld64);
+  k_f32_to_f64<<<rows_grid(n), 256, 0, s>>>(src, n, ld32, dst, ld64);
   return cudaGetLastError();
 }
 
