@@ -12,7 +12,11 @@
 namespace zf {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
+
+// Tile edge: 64 x 64 tiles (4 x 4 outputs per thread) in general; 32 x 32 tiles (2 x 2 per thread) up
+// to N = 1024, where 64-wide tiles leave most SMs idle (N = 256: 16 tiles on 152 SMs).
+inline int tile_for(int n) { return n <= 1024 ? 32 : 64; }
 
 __device__ __forceinline__ void sym_tile_of(int b, int T, int& bi, int& bj) {
   // b-th tile of the upper triangle, row-major over (bi, bj >= bi)
@@ -25,8 +29,9 @@ __device__ __forceinline__ void sym_tile_of(int b, int T, int& bi, int& bj) {
   bj = row + rem;
 }
 
-template <typename T, typename G>
+template <typename T, typename G, int TE>
 __global__ void __launch_bounds__(NT) k64_gemm(G g) {
+  constexpr int BM = TE, BN = TE, R = TE / 16;  // R x R outputs per thread
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   __shared__ double red[NT / 32];
@@ -42,7 +47,7 @@ __global__ void __launch_bounds__(NT) k64_gemm(G g) {
   const int i0 = bi * BM, j0 = bj * BN;
   const int t = threadIdx.x;
   const int ty = t / 16, tx = t % 16;
-  T acc[4][4] = {};
+  T acc[R][R] = {};
   for (int k0 = 0; k0 < n; k0 += BK) {
 #pragma unroll
     for (int e = 0; e < (BM * BK) / NT; ++e) {
@@ -72,26 +77,26 @@ __global__ void __launch_bounds__(NT) k64_gemm(G g) {
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      T a[R], b[R];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+      for (int r = 0; r < R; ++r) a[r] = As[kk][ty * R + r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+      for (int c = 0; c < R; ++c) b[c] = Bs[kk][tx * R + c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < R; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
     }
     __syncthreads();
   }
   double ss = 0.0;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = i0 + ty * 4 + r;
+  for (int r = 0; r < R; ++r) {
+    const int i = i0 + ty * R + r;
     if (i >= n) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = j0 + tx * 4 + c;
+    for (int c = 0; c < R; ++c) {
+      const int j = j0 + tx * R + c;
       if (j >= n) continue;
       if (g.sym && j < i) continue;  // the (j, i) entry is written by the tile that owns it
       T v;
@@ -126,22 +131,25 @@ __global__ void __launch_bounds__(NT) k64_gemm(G g) {
 }  // namespace
 
 int f64_num_blocks(int n, bool sym) {
-  const int T = (n + BM - 1) / BM;
+  const int te = tile_for(n);
+  const int T = (n + te - 1) / te;
   return sym ? T * (T + 1) / 2 : T * T;
 }
 
-cudaError_t launch_f64_gemm(const F64Gemm& g, cudaStream_t s) {
-  const int T = (g.n + BM - 1) / BM;
-  dim3 grid = g.sym ? dim3(T * (T + 1) / 2) : dim3(T, T);
-  k64_gemm<double, F64Gemm><<<grid, NT, 0, s>>>(g);
+template <typename T, typename G>
+static cudaError_t launch_k64(const G& g, cudaStream_t s) {
+  const int te = tile_for(g.n);
+  const int tb = (g.n + te - 1) / te;
+  dim3 grid = g.sym ? dim3(tb * (tb + 1) / 2) : dim3(tb, tb);
+  if (te == 32)
+    k64_gemm<T, G, 32><<<grid, NT, 0, s>>>(g);
+  else
+    k64_gemm<T, G, 64><<<grid, NT, 0, s>>>(g);
   return cudaGetLastError();
 }
 
-cudaError_t launch_f32_gemm(const F32Gemm& g, cudaStream_t s) {
-  const int T = (g.n + BM - 1) / BM;
-  dim3 grid = g.sym ? dim3(T * (T + 1) / 2) : dim3(T, T);
-  k64_gemm<float, F32Gemm><<<grid, NT, 0, s>>>(g);
-  return cudaGetLastError();
-}
+cudaError_t launch_f64_gemm(const F64Gemm& g, cudaStream_t s) { return launch_k64<double, F64Gemm>(g, s); }
+
+cudaError_t launch_f32_gemm(const F32Gemm& g, cudaStream_t s) { return launch_k64<float, F32Gemm>(g, s); }
 
 }  // namespace zf
