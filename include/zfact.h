@@ -145,8 +145,12 @@ int zfact_refine(zfact_ctx* ctx, const double* S, const double* Z0, int64_t N, i
  * NULL, Z[i] may alias Z0[i]); orders[i] in 2..5.  hist is a host array of
  * count * hist_cap doubles (row i for instance i), info a host array of count
  * entries (may be NULL), status a host array of count ints (per-instance
- * zfact_status, may be NULL).  Motivated by the warm starts of Sec. 6
- * (molecular-dynamics frames, geometry optimisation). */
+ * zfact_status, may be NULL).  Every instance runs the bulk under the stop rule of opts; then, by
+ * default (refine_steps < 0 or 0), the FP64-accurate residual of every returned Z is formed
+ * (opts->final_residual) on concurrent streams.  With refine_steps > 0 every instance also gets
+ * Algorithm 3's refinement (refine_mode ZFACT_R_OZAKI or ZFACT_R_FP32; ZFACT_R_NATIVE returns
+ * ZFACT_ERR_UNSUPPORTED), one instance after another, its Err entries appended to its history.
+ * Motivated by the warm starts of Sec. 6 (molecular-dynamics frames, geometry optimisation). */
 int zfact_refine_batched(zfact_ctx* ctx, int count, const double* const* S,
                          const double* const* Z0, const int64_t* N, const int* orders,
                          int precision, const zfact_opts* opts, double* const* Z,

@@ -400,7 +400,35 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
   // ---- FP64-accurate final residual of every returned Z (error-free slicing), kLanes instances
   // at a time on concurrent streams (each lane with its own workspace and Err slot)
   std::vector<double> resid(count, NAN);
-  if (o.final_residual) {
+  std::vector<int> rit(count, 0);
+  if (o.refine_steps > 0) {
+    // Algorithm 3 for every instance, on request only (the default certifies the bulk result): the
+    // single-instance refinement on the returned FP64 Z, its Err entries appended to the instance's
+    // history; its last residual is the FP64-accurate residual of the returned Z.
+    if (o.refine_mode == ZFACT_R_NATIVE)
+      return ctx_fail(c, ZFACT_ERR_UNSUPPORTED, "batched refinement offers the sliced and FP32 modes");
+    for (int i = 0; i < count; ++i) {
+      if (hnf[i]) continue;
+      zfact_opts oi = o;
+      oi.refine_steps = std::min(o.refine_steps, kHistMax - 3 - hits[i]);
+      if (oi.refine_steps < 0) oi.refine_steps = 0;
+      const int ord = orders ? orders[i] : 2;
+      zfact_info inf;
+      memset(&inf, 0, sizeof(inf));
+      int ridx = 0;
+      cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
+      st = (o.refine_mode == ZFACT_R_FP32) ? refine_fp32(c, S[i], Z[i], n[i], ord, oi, hits[i], &ridx, &inf)
+                                           : refine_ozaki(c, S[i], Z[i], n[i], ord, oi, hits[i], &ridx, &inf);
+      if (st) return st;
+      if ((st = ctx_read_state(c))) return st;
+      const int end = std::min(c->st_host->hist_len, cap);
+      for (int k = hits[i] + 1; k < end; ++k) hh[(size_t)i * cap + k] = c->st_host->hist[k];
+      hlen[i] = std::max(hlen[i], end);
+      if (c->st_host->nonfinite) hnf[i] = 1;
+      resid[i] = inf.resid_f;
+      rit[i] = ridx;
+    }
+  } else if (o.final_residual) {
     const int L = zfact_ctx::kLanes;
     for (int l = 0; l < L; ++l)
       if (!c->lane_stream[l] && cudaStreamCreateWithFlags(&c->lane_stream[l], cudaStreamNonBlocking) != cudaSuccess)
@@ -471,6 +499,7 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
     if (info) {
       memset(&info[i], 0, sizeof(zfact_info));
       info[i].iters = hits[i];
+      info[i].refine_iters = rit[i];
       info[i].hist_len = hl;
       info[i].warn = (sti == ZFACT_WARN_NONCONTRACTIVE) ? ZFACT_WARN_NONCONTRACTIVE : 0;
       info[i].resid_f = resid[i];

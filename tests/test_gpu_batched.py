@@ -97,3 +97,18 @@ def test_batched_residuals_of_mixed_conditioning(ctx):
     for S, z, inf in zip(Ss, Z, info):
         _, e = oracle.residual(S, z.cpu().numpy())
         assert abs(inf["resid_f"] - e) <= 1e-6 * e, (inf["resid_f"], e)
+
+
+def test_batched_with_refinement_reaches_fp64(ctx):
+    """refine_steps > 0: every instance gets Algorithm 3's sliced refinement after the grouped bulk and
+    reaches 1e-12, checked with the oracle's residual of the returned Z."""
+    import torch
+    Ss = mats([100, 257, 300, 64])
+    St = [torch.from_numpy(S).cuda() for S in Ss]
+    Z, hist, info, status = ctx.refine_batched(St, None, precision="bf16_split", refine_steps=2, tol=1e-12)
+    for S, z, h, inf in zip(Ss, Z, hist, info):
+        n = S.shape[0]
+        _, e = oracle.residual(S, z.cpu().numpy())
+        assert inf["refine_iters"] >= 1 and inf["resid_f"] / math.sqrt(n) <= 1e-12
+        assert e / math.sqrt(n) <= 1e-12 and abs(inf["resid_f"] - e) <= 1e-12
+        assert inf["hist_len"] > inf["iters"] + 1
