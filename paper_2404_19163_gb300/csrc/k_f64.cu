@@ -15,8 +15,9 @@ namespace {
 constexpr int BK = 16, NT = 256;
 
 // Tile edge: 64 x 64 tiles (4 x 4 outputs per thread) in general; 32 x 32 tiles (2 x 2 per thread) up
-// to N = 1024, where 64-wide tiles leave most SMs idle (N = 256: 16 tiles on 152 SMs).
-inline int tile_for(int n) { return n <= 1024 ? 32 : 64; }
+// to N = 1024, where 64-wide tiles leave most SMs idle (N = 256: 16 tiles on 152 SMs).  FP32 from
+// N = 2048 on takes 128 x 128 tiles (8 x 8 per thread): the FP32 pipe needs that much reuse per load.
+inline int tile_for(int n, bool fp32 = false) { return n <= 1024 ? 32 : (fp32 && n >= 2048 ? 128 : 64); }
 
 __device__ __forceinline__ void sym_tile_of(int b, int T, int& bi, int& bj) {
   // b-th tile of the upper triangle, row-major over (bi, bj >= bi)
@@ -130,21 +131,23 @@ __global__ void __launch_bounds__(NT) k64_gemm(G g) {
 
 }  // namespace
 
-int f64_num_blocks(int n, bool sym) {
-  const int te = tile_for(n);
+int f64_num_blocks(int n, bool sym, bool fp32) {
+  const int te = tile_for(n, fp32);
   const int T = (n + te - 1) / te;
   return sym ? T * (T + 1) / 2 : T * T;
 }
 
 template <typename T, typename G>
 static cudaError_t launch_k64(const G& g, cudaStream_t s) {
-  const int te = tile_for(g.n);
+  const int te = tile_for(g.n, sizeof(T) == 4);
   const int tb = (g.n + te - 1) / te;
   dim3 grid = g.sym ? dim3(tb * (tb + 1) / 2) : dim3(tb, tb);
   if (te == 32)
     k64_gemm<T, G, 32><<<grid, NT, 0, s>>>(g);
-  else
+  else if (te == 64)
     k64_gemm<T, G, 64><<<grid, NT, 0, s>>>(g);
+  else if constexpr (sizeof(T) == 4)
+    k64_gemm<T, G, 128><<<grid, NT, 0, s>>>(g);
   return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ struct F64Gemm {
   int n;
   bool transA, sym, resid;
 };
-int f64_num_blocks(int n, bool sym);
+int f64_num_blocks(int n, bool sym, bool fp32 = false);  // blocks of launch_f64_gemm / launch_f32_gemm (fp32)
 cudaError_t launch_f64_gemm(const F64Gemm& g, cudaStream_t s);
 // The same product in FP32 (the paper's "single"); Err partials stay FP64.
 struct F32Gemm {

@@ -33,7 +33,7 @@ int single_refine(zfact_ctx* c, const double* S, double* Za64, int n, int order,
     P2 = (float*)ctx_buf(c, "s.P2", sizeof(float) * nn, &st);
     if (!P2) return st;
   }
-  const int nb = f64_num_blocks(n, true);
+  const int nb = f64_num_blocks(n, true, true);
   double* partials = (double*)ctx_buf(c, "partials", sizeof(double) * (size_t)(nb + 1024), &st);
   if (!partials) return st;
   const double n2 = (double)n * n, n3 = n2 * n;
@@ -132,7 +132,7 @@ int refine_fp32(zfact_ctx* c, const double* S, double* Z64, int n, int order, co
     P2 = (float*)ctx_buf(c, "r32.P2", sizeof(float) * nn, &st);
     if (!P2) return st;
   }
-  const int nb = f64_num_blocks(n, true);
+  const int nb = f64_num_blocks(n, true, true);
   double* partials = (double*)ctx_buf(c, "partials", sizeof(double) * (size_t)(nb + 1024), &st);
   if (!partials) return st;
   const double n2 = (double)n * n, n3 = n2 * n;

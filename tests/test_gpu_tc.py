@@ -168,7 +168,7 @@ def test_fp16_split_bulk_floor_below_bf16(ctx):
     assert b2 < 1e-2 * b1, (r1.hist, r2.hist)
 
 
-@pytest.mark.parametrize("n", [64, 129, 300])
+@pytest.mark.parametrize("n", [64, 129, 300, 2049])
 def test_fp32_gemm_parity(ctx, n):
     """The paper's "single" product: FP32 operands, FP32 CUDA-core accumulation."""
     g = np.random.default_rng(40 + n)
