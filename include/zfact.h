@@ -250,6 +250,23 @@ int zfact_congruence(zfact_ctx* ctx, const double* H, const double* Z, int64_t N
  * are not freed.  No counterpart in the paper: it bounds what a context takes from a shared GPU. */
 int zfact_set_workspace_limit(zfact_ctx* ctx, int64_t bytes);
 
+/* ---- FP64-accurate product scheme ----------------------------------------------------
+ * How ZFACT_R_OZAKI forms its FP64-accurate products (the refinement's d = I - Z^T S Z and
+ * Z + Z Q, zfact_residual's ozaki mode, zfact_congruence).  Both keep the same bits of every row
+ * of the operands (rows rounded to T-bit fixed point, relative to the row's largest entry):
+ *   ZFACT_EMU_AUTO (default): modular residues (Ozaki, Uchino, Imamura, "Ozaki Scheme II: A
+ *     GEMM-oriented emulation of floating-point matrix multiplication using an integer modular
+ *     technique", 2025): one BF16 tensor-core product per modulus (<= 127, pairwise coprime)
+ *     and a Chinese-remainder reconstruction, wherever the bound N 2^(T_A + T_B) on the integer
+ *     product fits the twenty moduli (product just below 2^127); error-free slices otherwise;
+ *   ZFACT_EMU_SLICES: error-free slices always (the Ozaki et al. 2012 scheme above).
+ * Other values return ZFACT_ERR_ARG.  No counterpart in the paper, which refines in FP64. */
+typedef enum zfact_emulation {
+    ZFACT_EMU_AUTO = 0,
+    ZFACT_EMU_SLICES = 1
+} zfact_emulation;
+int zfact_set_emulation(zfact_ctx* ctx, int scheme);
+
 /* ---- bounded-wait self-test -----------------------------------------------------------
  * Launches one block whose mbarrier wait, the bounded wait every tensor-core kernel uses, can never
  * complete: nothing arrives at the barrier.  The wait gives up after a short poll limit, records

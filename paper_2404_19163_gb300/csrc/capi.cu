@@ -428,6 +428,14 @@ extern "C" int zfact_set_workspace_limit(zfact_ctx* c, int64_t bytes) {
   return ZFACT_OK;
 }
 
+extern "C" int zfact_set_emulation(zfact_ctx* c, int scheme) {
+  if (!c) return ZFACT_ERR_ARG;
+  if (scheme != ZFACT_EMU_AUTO && scheme != ZFACT_EMU_SLICES)
+    return ctx_fail(c, ZFACT_ERR_ARG, "unknown emulation scheme %d", scheme);
+  c->oz_scheme = scheme;
+  return ZFACT_OK;
+}
+
 namespace {
 // One mbarrier that nothing arrives at: the production bounded wait must give up, raise the
 // timeout flag and return, leaving the kernel to exit normally.

@@ -1,0 +1,230 @@
+// Modular (Chinese remainder) arithmetic of the residue products in k_ozmod.cu, shared by the
+// host planner and the device kernels.  Plain C++ outside nvcc, so the arithmetic can be
+// checked on the host.
+#pragma once
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#ifdef __CUDACC__
+#define ZF_HD __host__ __device__
+#else
+#define ZF_HD
+#endif
+
+namespace zf {
+
+constexpr int kCrtMax = 20;       // moduli available; their product is just below 2^127
+constexpr int kCrtMaxChunks = 4;  // K-chunks summed per reconstruction (|sum| < 2^26)
+constexpr int kCrtMaxResidue = 63;  // largest |residue|: chunks of K <= 2^24 / 63^2 stay exact
+
+// Pairwise coprime moduli, largest first: primes and prime powers up to 127, and 17 last so
+// that all twenty multiply to less than 2^127 (about 126.97 bits).
+ZF_HD constexpr int crt_modulus(int i) {
+  switch (i) {
+    case 0: return 127;
+    case 1: return 125;
+    case 2: return 121;
+    case 3: return 113;
+    case 4: return 109;
+    case 5: return 107;
+    case 6: return 103;
+    case 7: return 101;
+    case 8: return 97;
+    case 9: return 89;
+    case 10: return 83;
+    case 11: return 81;
+    case 12: return 79;
+    case 13: return 73;
+    case 14: return 71;
+    case 15: return 67;
+    case 16: return 64;
+    case 17: return 61;
+    case 18: return 59;
+    case 19: return 17;
+    default: return 1;
+  }
+}
+
+// Symmetric residue of +-a (a < 2^62) modulo m <= 127: in [-(m-1)/2, (m-1)/2] for odd m and
+// within [-m/2, m/2] for m = 64, so |r| <= 63.
+ZF_HD inline int crt_sym_residue(unsigned long long a, bool neg, int m) {
+  const unsigned um = (unsigned)m;
+  const unsigned hi = (unsigned)(a >> 32), lo = (unsigned)a;
+  const unsigned c32 = (unsigned)(4294967296ull % um);
+  const unsigned r = ((hi % um) * c32 + lo % um) % um;
+  int v = (int)r;
+  if (2 * v >= m) v -= m;
+  return neg ? -v : v;
+}
+
+// R mod m in [0, m) for |R| < 2^26 and m >= 17: the float quotient is off by at most one.
+ZF_HD inline int crt_mod(int R, int m, float inv) {
+  const int q = (int)floorf((float)R * inv);
+  int y = R - q * m;
+  if (y < 0) y += m;
+  if (y >= m) y -= m;
+  return y;
+}
+
+ZF_HD inline float crt_bits_f(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+ZF_HD inline unsigned crt_f_bits(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  memcpy(&u, &f, 4);
+  return u;
+#endif
+}
+
+// Nearest integer (ties to even) of |x| < 2^22 with two FP32 additions: adding 1.5 * 2^23 leaves
+// no fraction bits.
+ZF_HD inline float crt_rint(float x) {
+  const float C = 12582912.0f;
+  return (x + C) - C;
+}
+
+// 2^e mod m in symmetric form (|c| <= m/2).
+ZF_HD constexpr int crt_pow2_sym(int m, int e) {
+  int r = 1 % m;
+  for (int i = 0; i < e; ++i) r = (2 * r) % m;
+  return 2 * r > m ? r - m : r;
+}
+
+// The five 14-bit parts of a fixed-point value F (|F| <= 2^62), signed, as floats:
+// F = sum_k a_k 2^(14k), |a_k| < 2^14.
+ZF_HD inline void crt_parts(long long F, float (&a)[5]) {
+  const unsigned long long u = F < 0 ? 0ull - (unsigned long long)F : (unsigned long long)F;
+  const float sg = F < 0 ? -1.0f : 1.0f;
+  // a 14-bit integer v as a float: the bits of 2^23 + v, minus 2^23
+  for (int k = 0; k < 5; ++k)
+    a[k] = sg * (crt_bits_f(0x4B000000u | (unsigned)((u >> (14 * k)) & 0x3FFFu)) - 8388608.0f);
+}
+
+// Symmetric residue of F modulo m from its parts, in FP32: x = sum_k a_k (2^(14k) mod m) is an
+// integer below 2^22 (exact), x - m rint(x / m) is congruent to F, and the float quotient errs
+// by less than 0.04, so one fix-up brings it into [-(m-1)/2, (m-1)/2] (|r| <= 32 for m = 64).
+ZF_HD inline float crt_residue_f(const float (&a)[5], int m) {
+  const float fm = (float)m;
+  const float x = fmaf(a[4], (float)crt_pow2_sym(m, 56),
+                       fmaf(a[3], (float)crt_pow2_sym(m, 42),
+                            fmaf(a[2], (float)crt_pow2_sym(m, 28), fmaf(a[1], (float)crt_pow2_sym(m, 14), a[0]))));
+  float r = fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
+  const float h = (float)(m / 2);
+  if (r > h)
+    r -= fm;
+  else if (r < -h)
+    r += fm;
+  return r;
+}
+
+// x mod m for an integer-valued float |x| <= 2^24, m >= 17 (|x / m| < 2^20): congruent, within
+// about 0.62 m of 0.
+ZF_HD inline float crt_fmod_sym(float x, float m, float inv) { return fmaf(-m, crt_rint(x * inv), x); }
+
+// Reconstruction constants of the first nmod moduli: M = prod m_i, P_i = M / m_i as four
+// 32-bit limbs, w_i = P_i^-1 mod m_i.
+struct CrtPlan {
+  int nmod;
+  int m[kCrtMax];
+  int w[kCrtMax];
+  float inv[kCrtMax];
+  float fm[kCrtMax], fw[kCrtMax];  // m and w as floats
+  unsigned P[kCrtMax][4];
+  unsigned M[4];
+};
+
+// Accumulates sum_i y_i P_i (y_i = (C mod m_i) w_i mod m_i) per 32-bit limb without carries
+// (each limb sum stays below 2^44) and sum_i y_i / m_i in FP32.  That sum equals q + C / M for
+// an integer q; with |C| < M / 4 and an FP32 error far below 1/4, q = round(sum) and
+// C = sum_i y_i P_i - q M, formed modulo 2^128 (exact, since |C| < 2^125).
+struct CrtAcc {
+  unsigned long long L[4];
+  float S;
+  ZF_HD void clear() {
+    L[0] = L[1] = L[2] = L[3] = 0ull;
+    S = 0.0f;
+  }
+  ZF_HD void add(const CrtPlan& p, int t, int R) {
+    const int m = p.m[t];
+    const float inv = p.inv[t];
+    int y = crt_mod(R, m, inv);
+    y = crt_mod(y * p.w[t], m, inv);
+    S = fmaf((float)y, inv, S);
+    for (int l = 0; l < 4; ++l) L[l] += (unsigned long long)(unsigned)y * p.P[t][l];
+  }
+  // The same from r = C mod m given as an integer-valued float with |r| <= 2^9 (a sum of up to
+  // kCrtMaxChunks outputs of crt_fmod_sym): r w_t stays below 2^16, so the FP32 reduction is exact.
+  ZF_HD void add_f(const CrtPlan& p, int t, float r) {
+    const float m = p.fm[t], inv = p.inv[t];
+    float y = crt_fmod_sym(r * p.fw[t], m, inv);
+    if (y < 0.0f) y += m;  // [0, m)
+    S = fmaf(y, inv, S);
+    const unsigned yi = crt_f_bits(y + 8388608.0f) & 0x7FFFFFu;  // the integer y < 2^23
+    for (int l = 0; l < 4; ++l) L[l] += (unsigned long long)yi * p.P[t][l];
+  }
+  // C 2^sc in FP64 (two roundings).
+  ZF_HD double value(const CrtPlan& p, int sc) const {
+    const long long q = (long long)rintf(S);
+    long long t0 = (long long)L[0] - q * (long long)p.M[0];
+    long long t1 = (long long)L[1] - q * (long long)p.M[1] + (t0 >> 32);
+    long long t2 = (long long)L[2] - q * (long long)p.M[2] + (t1 >> 32);
+    long long t3 = (long long)L[3] - q * (long long)p.M[3] + (t2 >> 32);
+    const unsigned l0 = (unsigned)t0, l1 = (unsigned)t1, l2 = (unsigned)t2, l3 = (unsigned)t3;
+    unsigned long long hi = ((unsigned long long)l3 << 32) | l2, lo = ((unsigned long long)l1 << 32) | l0;
+    const bool neg = (l3 >> 31) != 0u;
+    if (neg) {
+      lo = ~lo + 1ull;
+      hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const double v = ldexp((double)hi, 64 + sc) + ldexp((double)lo, sc);
+    return neg ? -v : v;
+  }
+};
+
+// The moduli count that makes M = m_0 ... m_{k-1} exceed 2^bits (0 if all twenty do not), with
+// the reconstruction constants.
+inline int crt_plan(double bits, CrtPlan* p) {
+  unsigned __int128 M = 1;
+  int k = 0;
+  double lb = 0.0;
+  while (k < kCrtMax && lb <= bits) {
+    M *= (unsigned)crt_modulus(k);
+    lb += log2((double)crt_modulus(k));
+    ++k;
+  }
+  if (lb <= bits) return 0;
+  p->nmod = k;
+  for (int i = 0; i < kCrtMax; ++i) {
+    const unsigned m = i < k ? (unsigned)crt_modulus(i) : 1u;
+    p->m[i] = (int)m;
+    p->inv[i] = 1.0f / (float)m;
+    p->fm[i] = (float)m;
+    p->w[i] = 0;
+    p->fw[i] = 0.0f;
+    for (int l = 0; l < 4; ++l) p->P[i][l] = 0u;
+    if (i >= k) continue;
+    const unsigned __int128 P = M / m;
+    for (int l = 0; l < 4; ++l) p->P[i][l] = (unsigned)(P >> (32 * l));
+    const unsigned pm = (unsigned)(P % m);
+    for (unsigned x = 1; x < m; ++x)
+      if ((pm * x) % m == 1u) {
+        p->w[i] = (int)x;
+        p->fw[i] = (float)x;
+        break;
+      }
+  }
+  for (int l = 0; l < 4; ++l) p->M[l] = (unsigned)(M >> (32 * l));
+  return k;
+}
+
+}  // namespace zf

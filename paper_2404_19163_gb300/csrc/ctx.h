@@ -50,6 +50,9 @@ struct zfact_ctx {
   // its work on lane_stream[lane] and uses workspace buffers suffixed with the lane
   static constexpr int kLanes = 8;
   int oz_s = 9;  // slices per operand of the current residual products
+  int oz_T = 54;     // fixed-point bits per operand of the current residual products
+  int oz_nmod = 0;   // > 0: those products use this many CRT residues instead of slices
+  int oz_scheme = 0;  // zfact_emulation: 0 residues where they fit, 1 slices always
   cudaStream_t lane_stream[kLanes] = {};
   int lane = -1;
   size_t ws_limit = 0;  // cap on the workspace bytes (0 = none), zfact_set_workspace_limit
@@ -105,6 +108,7 @@ int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s = 0);
 int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop);
 int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax);
 int oz_update_slices(int n, double q);
+int oz_update_bits(int n, double q);
 int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, int n);
 
 // Algorithm 3 with FP64-accurate sliced products, from the FP64 iterate Z64 (mixed.cu)

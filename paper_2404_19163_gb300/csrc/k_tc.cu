@@ -86,9 +86,15 @@ __device__ __forceinline__ UnitPlan plan_unit(int u, const TcArgs& a, int kblock
     pl.tile = u % a.oz_tiles;
     pl.t = pl.group / a.oz_nch;
     const int c = pl.group % a.oz_nch;
-    pl.p0 = pl.t - (a.oz_s - 1) > 0 ? pl.t - (a.oz_s - 1) : 0;
-    const int p1 = pl.t < a.oz_s - 1 ? pl.t : a.oz_s - 1;
-    pl.npairs = p1 - pl.p0 + 1;
+    if (a.oz_diag) {
+      // residue products: group t is the single pair (t, t)
+      pl.p0 = pl.t;
+      pl.npairs = 1;
+    } else {
+      pl.p0 = pl.t - (a.oz_s - 1) > 0 ? pl.t - (a.oz_s - 1) : 0;
+      const int p1 = pl.t < a.oz_s - 1 ? pl.t : a.oz_s - 1;
+      pl.npairs = p1 - pl.p0 + 1;
+    }
     pl.kb0 = (a.oz_c0 + c) * a.oz_chunk_kb;
     pl.kb1 = pl.kb0 + a.oz_chunk_kb < kblocks ? pl.kb0 + a.oz_chunk_kb : kblocks;
   } else {
@@ -400,7 +406,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
         for (int pi = 0; pi < pl.npairs && ok; ++pi) {
           int mi = pi, ya = pl.row0 + bm * BM, yb = pl.row0 + bn * BN;
           if (a.oz_s > 0) {
-            const int p = pl.p0 + pi, q = pl.t - p;
+            const int p = pl.p0 + pi, q = a.oz_diag ? p : pl.t - p;
             mi = 0;
             ya += p * a.oz_ra;
             yb += q * a.oz_rb;

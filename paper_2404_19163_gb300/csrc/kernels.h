@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "crt.h"
 
 namespace zf {
 
@@ -79,6 +80,18 @@ cudaError_t launch_amax_f64(const double* A, int n, IterState* st, int slot, cud
 // Power-of-two scales for FP16 operands: st->scale[k] = 2^e with bound_k * 2^e in (2^13, 2^14],
 // bound_0 = amax[1] (d), bound_1 = c1*amax[1] + c2*hist[idx]^2 (Q), bound_2 = amax[2] (Z).
 cudaError_t launch_pow2_scales(IterState* st, int idx, float c1, float c2, cudaStream_t s);
+
+// ---- modular residues (k_ozmod.cu)
+// Residue planes of X's rows (trans = false; e[r] written) or columns (trans = true; e from
+// launch_oz_exp): round(x 2^(T - e_r)) modulo crt_modulus(0..nmod-1), symmetric, as BF16; plane t
+// of operand row r at out[(t * Rp + r) * ld16 + k]; rows n..Rp-1 of every plane are zeroed.
+cudaError_t launch_ozm_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
+                                int ld16, int Rp, cudaStream_t s);
+// C' from the residue products G[t * nch + c] (FP32 exact integers) by the CRT, scaled by
+// 2^(eA_i + eB_j - TA - TB); modes, sym and partials as launch_oz_combine; nch <= kCrtMaxChunks.
+cudaError_t launch_ozm_combine(const float* G, size_t gstride, int ld32, int nch, const CrtPlan& plan, const int* eA,
+                               const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
+                               double* partials, cudaStream_t s);
 
 // ---- error-free slicing (k_ozaki.cu)
 // e[r] = exponent bounding row r (cols = false) or column r (cols = true) of X.

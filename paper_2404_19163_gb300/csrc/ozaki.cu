@@ -23,8 +23,12 @@ constexpr size_t kOzGBudget = (size_t)6 << 30;  // bytes of FP32 group partials 
 struct OzOperand {
   uint16_t* sl = nullptr;
   int* e = nullptr;
-  int Rp = 0, s = 0;
+  int Rp = 0, s = 0;  // s planes: slices, or CRT residues when nmod > 0
+  int T = 0, nmod = 0;  // residues: fixed-point bits of the rows, moduli count (= s)
 };
+
+// K-blocks per residue chunk: |residue| <= 63, so a chunk of K terms sums below K 63^2 <= 2^24.
+constexpr int kCrtChunkKb = (int)((1 << 24) / (kCrtMaxResidue * kCrtMaxResidue) / 64);
 
 int ld16_of(int n) { return (n + 63) / 64 * 64; }
 int rp_of(int n) { return (n + 255) / 256 * 256; }
@@ -60,9 +64,117 @@ int oz_make(zfact_ctx* c, const char* name, const double* X, int n, int ldx, boo
   return ZFACT_OK;
 }
 
+// Residue count for the product of T_A- and T_B-bit operands over K = n terms: the integer
+// product is below n 2^(T_A + T_B), and M must exceed four times that.  0 = use slices (the
+// context asks for them, or the bound needs more than the twenty moduli give).
+int oz_mod_count(const zfact_ctx* c, int TA, int TB, int n) {
+  if (c->oz_scheme != ZFACT_EMU_AUTO || TA < 1 || TB < 1 || TA > 62 || TB > 62) return 0;
+  CrtPlan p;
+  return crt_plan(TA + TB + log2((double)n) + 2.0, &p);
+}
+
+int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx, bool trans, int T, int nmod,
+                OzOperand* op) {
+  int st = ZFACT_OK;
+  const int ld16 = ld16_of(n), Rp = rp_of(n);
+  std::string ns = lane_name(c, (std::string("oz.") + name + ".sl").c_str()),
+              ne = lane_name(c, (std::string("oz.") + name + ".e").c_str());
+  op->sl = (uint16_t*)ctx_buf(c, ns.c_str(), sizeof(uint16_t) * (size_t)nmod * Rp * ld16, &st);
+  if (!op->sl) return st;
+  op->e = (int*)ctx_buf(c, ne.c_str(), sizeof(int) * (size_t)n, &st);
+  if (!op->e) return st;
+  op->Rp = Rp;
+  op->s = nmod;
+  op->T = T;
+  op->nmod = nmod;
+  if ((st = ctx_cuda(c, klaunch(c, "oz_residues", 0, 8.0 * n * n + 2.0 * nmod * n * n, 2, [&] {
+                       cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, cur_stream(c));
+                       if (e != cudaSuccess) return e;
+                       return launch_ozm_residues(X, n, ldx, trans, op->e, T, nmod, op->sl, ld16, Rp, cur_stream(c));
+                     }),
+                     "oz residues")))
+    return st;
+  return ZFACT_OK;
+}
+
+// out (mode 0: =, 1: +=, fused 2: I - .) A B^T to FP64 accuracy from the CRT residues of A and B:
+// one tensor-core product per modulus (group t = pair (t, t)), then the reconstruction.
+int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool sym, double* out, int ld64,
+                   int mode, double* partials = nullptr, bool* fused_resid = nullptr) {
+  int st = ZFACT_OK;
+  CrtPlan plan;
+  const int k = crt_plan(A.T + B.T + log2((double)n) + 2.0, &plan);
+  if (k < 1 || k != A.nmod || k != B.nmod)
+    return ctx_fail(c, ZFACT_ERR_ARG, "residue operands do not match (%d, %d, %d moduli)", k, A.nmod, B.nmod);
+  const int ld = ld16_of(n);
+  const int kblocks = (n + 63) / 64;
+  const int nch_total = (kblocks + kCrtChunkKb - 1) / kCrtChunkKb;
+  const size_t slot_bytes = sizeof(float) * (size_t)n * ld;
+  int nch_b = (int)(kOzGBudget / (slot_bytes * k));
+  if (nch_b < 1) nch_b = 1;
+  if (nch_b > kCrtMaxChunks) nch_b = kCrtMaxChunks;
+  if (nch_b > nch_total) nch_b = nch_total;
+  float* G = (float*)ctx_buf(c, lane_name(c, "oz.G").c_str(), slot_bytes * k * nch_b, &st);
+  if (!G) return st;
+  TcMaps maps;
+  memset(&maps, 0, sizeof(maps));
+  const int bn = 256;
+  int r1 = ctx_make_map(c, &maps.a[0], A.sl, k * A.Rp, n, ld, 128, true);
+  int r2 = ctx_make_map(c, &maps.b[0], B.sl, k * B.Rp, n, ld, bn, true);
+  if (r1 || r2) return ctx_fail(c, ZFACT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d, %d)", r1, r2);
+  for (int c0 = 0; c0 < nch_total; c0 += nch_b) {
+    const int nch = (nch_total - c0) < nch_b ? (nch_total - c0) : nch_b;
+    TcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.M = a.N = a.K = n;
+    a.nseg = 1;
+    a.sym = sym ? 1 : 0;
+    a.epi = kEpiG32;
+    a.bf16 = 1;
+    a.unscale = 1.0f;
+    a.f32 = G;
+    a.ld32 = ld;
+    a.g_stride = (size_t)n * ld;
+    a.oz_s = k;
+    a.oz_diag = 1;
+    a.oz_nch = nch;
+    a.oz_chunk_kb = kCrtChunkKb;
+    a.oz_c0 = c0;
+    a.oz_ra = A.Rp;
+    a.oz_rb = B.Rp;
+    a.oz_tiles = tc_num_units(a, bn) / (k * nch);
+    a.err_flag = &c->st_dev->error;
+    // algorithmic work: k residue products over this launch's share of K
+    const int kb_lo = c0 * kCrtChunkKb,
+              kb_hi = (c0 + nch) * kCrtChunkKb < kblocks ? (c0 + nch) * kCrtChunkKb : kblocks;
+    const double kk = (double)(kb_hi - kb_lo) * 64.0 < n ? (double)(kb_hi - kb_lo) * 64.0 : (double)n;
+    const double flops = k * 2.0 * n * n * kk * (sym ? 0.5 : 1.0);
+    const double bytes = k * 2.0 * 2.0 * n * kk + 4.0 * k * nch * (double)n * n;
+    if ((st = ctx_cuda(c, klaunch(c, "tc_gemm.crt", flops, bytes, 1,
+                                  [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, cur_stream(c)); }),
+                       "tcgen05 residue products")))
+      return st;
+    int md = (c0 == 0) ? mode : 1;
+    const bool fuse = partials && fused_resid && sym && c0 == 0 && nch == nch_total;
+    if (fuse) {
+      md = 2;
+      *fused_resid = true;
+    }
+    const double cbytes = 4.0 * k * nch * n * (double)n + 16.0 * n * n;
+    if ((st = ctx_cuda(c, klaunch(c, "oz_crt", 0, cbytes, 1, [&] {
+                         return launch_ozm_combine(G, (size_t)n * ld, ld, nch, plan, A.e, B.e, A.T, B.T, n, out, ld64,
+                                                   md, sym, partials, cur_stream(c));
+                       }),
+                       "oz crt combine")))
+      return st;
+  }
+  return ZFACT_OK;
+}
+
 // out (mode 0: =, 1: +=) A B^T to FP64 accuracy, A and B given by their row slices.
 int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool sym, double* out, int ld64,
                int mode, double* partials = nullptr, bool* fused_resid = nullptr) {
+  if (A.nmod > 0 || B.nmod > 0) return oz_product_mod(c, A, B, n, sym, out, ld64, mode, partials, fused_resid);
   int st = ZFACT_OK;
   const int s = A.s < B.s ? A.s : B.s;
   const int ld = ld16_of(n);
@@ -145,11 +257,24 @@ int oz_slices_for(double zmax, double g_hi) {
   return s;
 }
 
+// The residual's operands keep T = b s bits either way: as s slices, or as CRT residues of the
+// T-bit rows where the product bound fits the moduli (then c->oz_nmod > 0).
 int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s) {
   OzOperand op;
   c->oz_s = s > 0 ? s : kOzSlicesResid;
+  c->oz_T = kOzBits * c->oz_s;
+  c->oz_nmod = oz_mod_count(c, c->oz_T, c->oz_T, n);
+  if (c->oz_nmod > 0) return oz_make_mod(c, "S", S, n, n, false, c->oz_T, c->oz_nmod, &op);
   return oz_make(c, "S", S, n, n, false, c->oz_s, &op);
 }
+
+namespace {
+// An operand of the current residual products (slices or residues, as oz_prepare_S chose).
+int oz_make_resid(zfact_ctx* c, const char* name, const double* X, int n, bool trans, OzOperand* op) {
+  if (c->oz_nmod > 0) return oz_make_mod(c, name, X, n, n, trans, c->oz_T, c->oz_nmod, op);
+  return oz_make(c, name, X, n, n, trans, c->oz_s, op);
+}
+}  // namespace
 
 // d = I - Z^T S Z to FP64 accuracy; Err -> hist[idx].  oz_prepare_S must have run for this S.
 int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop) {
@@ -159,6 +284,10 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   Sop.e = (int*)ctx_buf(c, lane_name(c, "oz.S.e").c_str(), 0, &st);
   Sop.Rp = rp_of(n);
   Sop.s = c->oz_s;
+  if (c->oz_nmod > 0) {
+    Sop.s = Sop.nmod = c->oz_nmod;
+    Sop.T = c->oz_T;
+  }
   double* A64 = (double*)ctx_buf(c, lane_name(c, "oz.At64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!A64) return st;
   double* X64 = (double*)ctx_buf(c, lane_name(c, "oz.X64").c_str(), sizeof(double) * (size_t)n * n, &st);
@@ -169,10 +298,10 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
                        sizeof(double) * (size_t)(nb_fused > nb_sep ? nb_fused : nb_sep), &st);
   if (!partials) return st;
   // rows of Z^T = columns of Z
-  if ((st = oz_make(c, "Zt", Z, n, n, true, Sop.s, &Zt))) return st;
+  if ((st = oz_make_resid(c, "Zt", Z, n, true, &Zt))) return st;
   // A^T = Z^T S  (S symmetric: B operand rows are rows of S)
   if ((st = oz_product(c, Zt, Sop, n, false, A64, n, 0))) return st;
-  if ((st = oz_make(c, "At", A64, n, n, false, Sop.s, &At))) return st;
+  if ((st = oz_make_resid(c, "At", A64, n, false, &At))) return st;
   // X = Z^T A = Z^T (A^T)^T, symmetric tiles; d = I - X fused into the combine when possible
   bool fused = false;
   double* Xout = X64;
@@ -202,6 +331,13 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
 // T = 53 + log2(4 sqrt(N) q) keeps that sum a factor 4 below 2^-53 2^ez_i, the rounding unit of row
 // i's largest entry: below what storing Z + Z Q in FP64 costs anyway.  A small correction needs
 // few bits.
+int oz_update_bits(int n, double q) {
+  double T = 53.0 + log2(4.0 * sqrt((double)n) * q);
+  if (!(T > 0)) T = 0;
+  const int t = (int)ceil(T), tmin = kOzBits * kOzSlicesUpdateMin;
+  return t < tmin ? tmin : t;
+}
+
 int oz_update_slices(int n, double q) {
   double T = 53.0 + log2(4.0 * sqrt((double)n) * q);
   if (!(T > 0)) T = 0;
@@ -216,15 +352,19 @@ int oz_update_slices(int n, double q) {
 // way d = I - Z^T S Z does, so the residual's base slice count (54 bits) is the right one.
 int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, int n) {
   int st = ZFACT_OK;
-  const int s = kOzSlicesResid;
+  const int s = kOzSlicesResid, T = kOzBits * s;
+  const int nm = oz_mod_count(c, T, T, n);
   OzOperand Hop, Zt, At;
   double* A64 = (double*)ctx_buf(c, lane_name(c, "oz.At64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!A64) return st;
-  if ((st = oz_make(c, "H", H, n, n, false, s, &Hop))) return st;
-  if ((st = oz_make(c, "Zt", Z, n, n, true, s, &Zt))) return st;
+  auto make = [&](const char* name, const double* X, bool trans, OzOperand* op) {
+    return nm > 0 ? oz_make_mod(c, name, X, n, n, trans, T, nm, op) : oz_make(c, name, X, n, n, trans, s, op);
+  };
+  if ((st = make("H", H, false, &Hop))) return st;
+  if ((st = make("Zt", Z, true, &Zt))) return st;
   // A^T = Z^T H (H symmetric: B operand rows are rows of H), then Z^T (H Z) on upper tiles
   if ((st = oz_product(c, Zt, Hop, n, false, A64, n, 0))) return st;
-  if ((st = oz_make(c, "At", A64, n, n, false, s, &At))) return st;
+  if ((st = make("At", A64, false, &At))) return st;
   return oz_product(c, Zt, At, n, true, out, n, 0);
 }
 
@@ -233,6 +373,15 @@ int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax) {
   int st = ZFACT_OK;
   OzOperand Zr, Qr;
   if (qmax == 0.0) return ZFACT_OK;  // Q = 0: Z is unchanged
+  if (qmax > 0.0 && isfinite(qmax)) {
+    // T = 53 + log2(4 sqrt(N) q) bits as below, kept exactly by CRT residues where they fit
+    const int Tu = oz_update_bits(n, qmax), nm = oz_mod_count(c, Tu, Tu, n);
+    if (nm > 0) {
+      if ((st = oz_make_mod(c, "Zr", Z, n, n, false, Tu, nm, &Zr))) return st;
+      if ((st = oz_make_mod(c, "Qr", Q, n, n, false, Tu, nm, &Qr))) return st;
+      return oz_product(c, Zr, Qr, n, false, Z, n, 1);
+    }
+  }
   const int su = (qmax > 0.0 && isfinite(qmax)) ? oz_update_slices(n, qmax) : kOzSlicesMax;
   if ((st = oz_make(c, "Zr", Z, n, n, false, su, &Zr))) return st;
   if ((st = oz_make(c, "Qr", Q, n, n, false, su, &Qr))) return st;

@@ -49,6 +49,8 @@ struct TcArgs {
   // (tile, group g) with g = t * oz_nch + c: all slice pairs p + q = t over K-chunk c.
   int oz_s, oz_nch, oz_chunk_kb, oz_ra, oz_rb, oz_c0;  // oz_c0: first K-chunk of this launch
   int oz_tiles;                 // output tiles of the product (units = oz_tiles * oz_s * oz_nch)
+  int oz_diag;                  // residue mode: group t holds the one pair (t, t), i.e. oz_s
+                                // independent products A_t B_t^T (CRT residues)
   size_t g_stride;              // kEpiG32: elements between group slots
   // Grouped mode (ninst > 0): independent square problems stacked along the rows of every
   // operand and output buffer (common leading dimensions).  Scheduling slot j covers units

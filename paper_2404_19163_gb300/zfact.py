@@ -24,6 +24,7 @@ WARN_NONCONTRACTIVE = 100
 
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 3, "fp16": 4, "fp16_split": 5, "bf16_split": 6}
 REFINE_MODE = {"native": 0, "ozaki": 1, "fp32": 2}
+EMULATION = {"auto": 0, "slices": 1}
 MLP_NPARAMS = 5573
 
 EXPORTED = (
@@ -31,7 +32,7 @@ EXPORTED = (
     "zfact_refine_batched", "zfact_features", "zfact_mlp_forward", "zfact_mlp_backward",
     "zfact_mlp_adam", "zfact_propose", "zfact_gemm", "zfact_split", "zfact_residual",
     "zfact_set_profiling", "zfact_kernel_stats", "zfact_residual_noalloc", "zfact_congruence",
-    "zfact_set_workspace_limit", "zfact_selftest_timeout",
+    "zfact_set_workspace_limit", "zfact_selftest_timeout", "zfact_set_emulation",
 )
 
 
@@ -97,6 +98,7 @@ def load(path: Optional[str] = None):
     lib.zfact_congruence.argtypes = [P, P, P, I64, I, I, P]
     lib.zfact_set_workspace_limit.argtypes = [P, I64]
     lib.zfact_selftest_timeout.argtypes = [P]
+    lib.zfact_set_emulation.argtypes = [P, I]
     for name in EXPORTED:
         if getattr(lib, name).restype is ctypes.c_int or name in ("zfact_default_opts", "zfact_destroy",
                                                                       "zfact_last_error"):
@@ -264,6 +266,10 @@ class Context:
     def set_workspace_limit(self, nbytes: int = 0):
         """zfact_set_workspace_limit: cap the device workspace (0 = no cap)."""
         self._raise(self.lib.zfact_set_workspace_limit(self.h, int(nbytes)))
+
+    def set_emulation(self, scheme: str = "auto"):
+        """zfact_set_emulation: "auto" (CRT residues where they fit, else slices) or "slices"."""
+        self._raise(self.lib.zfact_set_emulation(self.h, EMULATION[scheme] if isinstance(scheme, str) else int(scheme)))
 
     def selftest_timeout(self) -> int:
         """zfact_selftest_timeout: returns the status (ZFACT_ERR_TIMEOUT = 6 when the path works)."""

@@ -1,0 +1,149 @@
+// Host check of the CRT arithmetic of the residue products (paper_2404_19163_gb300/csrc/crt.h)
+// against exact 128-bit integer products: residues, exact chunked residue dot products, and the
+// reconstruction, including the extreme bound N 2^(2T) where the moduli are used up.
+#include <math.h>
+#include <stdio.h>
+
+#include <random>
+#include <vector>
+
+#include "../../paper_2404_19163_gb300/csrc/crt.h"
+
+using namespace zf;
+
+static double to_double(__int128 x) {
+  const bool neg = x < 0;
+  const unsigned __int128 a = neg ? -(unsigned __int128)x : (unsigned __int128)x;
+  const long double v =
+      (long double)(unsigned long long)(a >> 64) * 18446744073709551616.0L + (long double)(unsigned long long)a;
+  return (double)(neg ? -v : v);
+}
+
+int main() {
+  std::mt19937_64 rng(7);
+  int fails = 0;
+  long cases = 0;
+  const int Ts[] = {24, 40, 47, 53, 54};
+  const int Ks[] = {1, 2, 64, 1000, 4096, 4224, 4225, 8448, 16384};
+  const int chunk = 4224;
+  for (int T : Ts)
+    for (int K : Ks) {
+      CrtPlan p;
+      const int k = crt_plan(2.0 * T + log2((double)K) + 2.0, &p);
+      if (!k) {
+        printf("no plan for T=%d K=%d\n", T, K);
+        return 1;
+      }
+      for (int mode = 0; mode < 4; ++mode) {
+        std::vector<long long> a(K), b(K);
+        const long long lim = 1ll << T;
+        for (int l = 0; l < K; ++l) {
+          if (mode == 0) {
+            a[l] = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+            b[l] = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+          } else if (mode == 1) {  // the largest positive product
+            a[l] = lim;
+            b[l] = lim;
+          } else if (mode == 2) {  // the largest negative product
+            a[l] = lim;
+            b[l] = -lim;
+          } else {  // -1
+            a[l] = l == 0 ? -1 : 0;
+            b[l] = l == 0 ? 1 : 0;
+          }
+        }
+        __int128 exact = 0;
+        for (int l = 0; l < K; ++l) exact += (__int128)a[l] * b[l];
+        // two reconstructions: integer residues with integer reduction (add), and the FP32 path of
+        // the kernels (crt_residue_f, per-chunk crt_fmod_sym, add_f)
+        CrtAcc acc, accf;
+        acc.clear();
+        accf.clear();
+        for (int t = 0; t < k; ++t) {
+          const int m = p.m[t];
+          long long R = 0;
+          float rsum = 0.0f;
+          for (int c0 = 0; c0 < K; c0 += chunk) {
+            long long part = 0, partf = 0;
+            for (int l = c0; l < K && l < c0 + chunk; ++l) {
+              const int ra = crt_sym_residue((unsigned long long)(a[l] < 0 ? -a[l] : a[l]), a[l] < 0, m);
+              const int rb = crt_sym_residue((unsigned long long)(b[l] < 0 ? -b[l] : b[l]), b[l] < 0, m);
+              float pa[5], pb[5];
+              crt_parts(a[l], pa);
+              crt_parts(b[l], pb);
+              const float fa = crt_residue_f(pa, m), fb = crt_residue_f(pb, m);
+              if (ra > kCrtMaxResidue || ra < -kCrtMaxResidue || rb > kCrtMaxResidue || rb < -kCrtMaxResidue ||
+                  fabsf(fa) > (float)(m / 2) || fabsf(fb) > (float)(m / 2) || fa != floorf(fa) ||
+                  ((long long)fa - ra) % m != 0 || ((long long)fb - rb) % m != 0) {
+                printf("residue wrong or out of range (m=%d: %d %g, %d %g)\n", m, ra, fa, rb, fb);
+                return 1;
+              }
+              part += (long long)ra * rb;
+              partf += (long long)fa * (long long)fb;
+            }
+            if (part > (1ll << 24) || part < -(1ll << 24) || partf > (1ll << 24) || partf < -(1ll << 24)) {
+              printf("chunk sum %lld / %lld exceeds 2^24\n", part, partf);
+              return 1;
+            }
+            R += part;
+            rsum += crt_fmod_sym((float)partf, (float)m, p.inv[t]);
+          }
+          acc.add(p, t, (int)R);
+          accf.add_f(p, t, rsum);
+        }
+        const double want = to_double(exact);
+        for (const CrtAcc* A : {&acc, &accf}) {
+          const double got = A->value(p, 0);
+          const double rel = want != 0 ? fabs(got - want) / fabs(want) : fabs(got);
+          ++cases;
+          if (!(rel <= 2.3e-16)) {
+            ++fails;
+            printf("FAIL T=%d K=%d mode=%d moduli=%d %s: %.17g vs %.17g\n", T, K, mode, k, A == &acc ? "int" : "fp32",
+                   got, want);
+          }
+        }
+      }
+    }
+  for (int it = 0; it < 400000; ++it) {  // residues are congruent to the value and in range
+    long long F = (long long)(rng() >> 1) - (1ll << 62);
+    if (it % 4 == 1) F >>= (it / 4) % 62;  // all magnitudes
+    const int m = crt_modulus(it % kCrtMax);
+    const int r = crt_sym_residue((unsigned long long)(F < 0 ? -F : F), F < 0, m);
+    float pa[5];
+    crt_parts(F, pa);
+    const float rf = crt_residue_f(pa, m);
+    if ((F - r) % m != 0 || (F - (long long)rf) % m != 0 || fabsf(rf) > (float)(m / 2) || rf != floorf(rf)) {
+      printf("residue of %lld mod %d wrong: %d / %g\n", F, m, r, rf);
+      return 1;
+    }
+  }
+  for (int i = 0; i < kCrtMax; ++i) {  // crt_fmod_sym over |x| <= 2^24
+    const int m = crt_modulus(i);
+    const float inv = 1.0f / (float)m;
+    for (long long x = -(1ll << 24); x <= (1ll << 24); x += (x > -(1ll << 24) + 5000 && x < (1ll << 24) - 5000) ? 331 : 1) {
+      const float r = crt_fmod_sym((float)x, (float)m, inv);
+      if (r != floorf(r) || ((long long)r - x) % m != 0 || fabsf(r) > 0.62f * m) {
+        printf("crt_fmod_sym(%lld, %d) = %g\n", x, m, r);
+        return 1;
+      }
+    }
+  }
+  for (int i = 0; i < kCrtMax; ++i) {  // crt_mod over |R| < 2^26
+    const int m = crt_modulus(i);
+    const float inv = 1.0f / (float)m;
+    for (long long R = -(1ll << 26) + 1; R < (1ll << 26); R += 997) {
+      const int y = crt_mod((int)R, m, inv);
+      if (y < 0 || y >= m || (R - y) % m != 0) {
+        printf("crt_mod(%lld, %d) = %d\n", R, m, y);
+        return 1;
+      }
+    }
+  }
+  CrtPlan p;
+  if (crt_plan(122.0, &p) != 19 || crt_plan(124.0, &p) != 20 || crt_plan(127.0, &p) != 0) {
+    printf("moduli counts wrong\n");
+    return 1;
+  }
+  printf("cases %ld fails %d\n", cases, fails);
+  return fails != 0;
+}

@@ -10,12 +10,14 @@ from paper_2404_19163_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["auto", "slices"])
+def ctx(request):
+    """Both FP64-accurate product schemes: CRT residues (the default) and error-free slices."""
     from paper_2404_19163_gb300 import Context, build
     build.build()
     oracle.build()
     c = Context(0)
+    c.set_emulation(request.param)
     yield c
     c.close()
 

@@ -16,11 +16,15 @@ from paper_2404_19163_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["auto", "slices"])
+def ctx(request):
+    """Every test runs under both FP64-accurate product schemes: CRT residues where they fit
+    (the default) and error-free slices."""
     from paper_2404_19163_gb300 import Context, build
     build.build()
     c = Context(0)
+    c.set_emulation(request.param)
+    c.emu = request.param
     yield c
     c.close()
 
@@ -30,7 +34,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("n", [5, 64, 200, 777, 1500, 3001, 4097])
+@pytest.mark.parametrize("n", [5, 64, 200, 777, 1500, 3001, 4097, 4300])
 def test_ozaki_residual_matches_oracle(ctx, n):
     import torch
     g = np.random.default_rng(n)
@@ -69,6 +73,31 @@ def test_ozaki_residual_exact_on_integer_inputs(ctx, n, zbits, sbits):
     D = torch.empty((n, n), dtype=torch.float64, device="cuda")
     ctx.residual(dev(S), dev(Z), "ozaki", D=D)
     assert np.array_equal(D.cpu().numpy(), np.eye(n) - X)
+
+
+@pytest.mark.parametrize("n", [300, 4300, 8192])
+def test_residual_exact_on_scaled_integer_inputs(ctx, n):
+    """Integer Z scaled by 2^-20 and integer S, so max|Z|^2 times S's largest row sum is below one
+    and the residual keeps 54 bits per operand: CRT residues under the default scheme (19 moduli
+    and two K-chunks at N = 4300; 20 moduli at N = 8192, whose chunks take two launches and an
+    unfused d = I - X).  Every product is an integer times a power of two that FP64 holds, so d
+    must equal I - Z^T S Z bit for bit (columns sampled above N = 300)."""
+    import torch
+    g = np.random.default_rng(n)
+    Zi = g.integers(-2 ** 8, 2 ** 8, (n, n)).astype(np.float64)
+    A = g.integers(-8, 8, (n, n)).astype(np.float64)
+    S = A + A.T
+    cols = np.arange(n) if n <= 300 else np.unique(np.concatenate([g.choice(n, 24, replace=False), [0, n - 1]]))
+    X = (Zi.T @ (S @ Zi[:, cols])) * 2.0 ** -40   # exact: integers below 2^47, then a power of two
+    assert np.abs(Zi.T @ (S @ Zi[:, cols[:1]])).max() < 2.0 ** 52
+    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    ctx.set_profiling(True)
+    ctx.kernel_stats(reset=True)
+    ctx.residual(dev(S), dev(Zi * 2.0 ** -20), "ozaki", D=D)
+    names = {k["name"] for k in ctx.kernel_stats()}
+    ctx.set_profiling(False)
+    assert ("tc_gemm.crt" if ctx.emu == "auto" else "tc_gemm.ozaki") in names, names
+    assert np.array_equal(D[:, cols].cpu().numpy(), np.eye(n)[:, cols] - X)
 
 
 def test_ozaki_residual_unaligned_operand_bit_identical(ctx):
