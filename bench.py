@@ -33,9 +33,12 @@ sys.path.insert(0, ROOT)
 METRIC = "ms to ||I−ZᵀSZ||_F/√N≤tol per factorization; TFLOP/s & tensor-pipe % vs FP64 path"
 UNIT = "ms"
 TOL = 1e-12
-# DRAM bytes per launch of the dominant kernel from one ncu capture (profiles/ozaki_product_N4096.md),
-# valid only while the kernel's source is the one that was captured
-TRAFFIC = {"tc_gemm.ozaki": {"bytes_per_launch": 7.32e9, "source": "paper_2404_19163_gb300/csrc/k_tc.cu",
+# DRAM bytes per launch of the dominant kernel from one ncu capture, valid only while the kernel's
+# source is the one that was captured: the CRT residue products (profiles/crt_products_N4096.md, mean
+# of the residual's full and symmetric product) and the slicing products (profiles/ozaki_product_N4096.md)
+TRAFFIC = {"tc_gemm.crt": {"bytes_per_launch": 2.34e9, "source": "paper_2404_19163_gb300/csrc/k_tc.cu",
+                           "sha1": "93c2ac99c4c1604b8be282eaa5201be6b8210638"},
+           "tc_gemm.ozaki": {"bytes_per_launch": 7.32e9, "source": "paper_2404_19163_gb300/csrc/k_tc.cu",
                              "sha1": "b4f7e57d908ea369ec1c020d960a1317e36ba946"}}
 FP64_ITERS_WORKLOAD2 = 4   # updates the FP64 recursion needs on workload 2 (counted by the FP64 GPU path)
 
