@@ -75,11 +75,13 @@ typedef enum zfact_precision {
 /* How the refinement (Algorithm 3) forms d = I - Z^T S Z in FP64 accuracy. */
 typedef enum zfact_refine_mode {
     ZFACT_R_NATIVE = 0,      /* FP64 CUDA-core products */
-    ZFACT_R_OZAKI = 1,       /* error-free slicing of Z and S into BF16 integer slices with exact
-                                FP32 tensor-core accumulation (Ozaki, Ogita, Oishi, Rump,
-                                "Error-free transformations of matrix multiplication by using
-                                fast routines of matrix multiplication and its applications",
-                                Numer. Algorithms 59 (2012)) */
+    ZFACT_R_OZAKI = 1,       /* FP64-accurate products on the BF16 tensor cores with exact FP32
+                                accumulation: CRT residues of the fixed-point rows (Ozaki scheme
+                                II) where they fit, else error-free slices (Ozaki, Ogita, Oishi,
+                                Rump, "Error-free transformations of matrix multiplication by
+                                using fast routines of matrix multiplication and its
+                                applications", Numer. Algorithms 59 (2012)); see
+                                zfact_set_emulation */
     ZFACT_R_FP32 = 2         /* single precision, Table I's "(h)(h)+refi" step: d, Q and Z + Z Q by
                                 FP32 CUDA-core products (reaches the FP32 floor only); the final
                                 residual of the returned Z is still formed to FP64 accuracy.
@@ -232,8 +234,9 @@ int zfact_residual(zfact_ctx* ctx, int refine_mode, const double* S, const doubl
  * H_perp C_perp = C_perp e, C = Z C_perp.  H_perp is symmetric by definition: its upper
  * triangle is formed and mirrored (as X = Z^T S Z is).
  *   precision ZFACT_P_FP64: FP64 accuracy by the method of refine_mode (ZFACT_R_NATIVE: FP64
- *     CUDA-core products; ZFACT_R_OZAKI: error-free slicing on the BF16 tensor cores, 9 slices,
- *     errors on the scale of FP64 products relative to |Z|^T |H| |Z|);
+ *     CUDA-core products; ZFACT_R_OZAKI: CRT residues or error-free slices on the BF16 tensor
+ *     cores, 54 bits per operand row, errors on the scale of FP64 products relative to
+ *     |Z|^T |H| |Z|);
  *   ZFACT_P_BF16 / ZFACT_P_BF16_SPLIT: BF16 (hi, or hi/lo) operands with FP32 accumulation
  *     (refine_mode ignored);
  *   FP32 and the FP16 precisions return ZFACT_ERR_UNSUPPORTED.

@@ -397,7 +397,7 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
   kstats_flush(c);
   const int bulk_launches = c->launches;
 
-  // ---- FP64-accurate final residual of every returned Z (error-free slicing), kLanes instances
+  // ---- FP64-accurate final residual of every returned Z (CRT residues or slices), kLanes instances
   // at a time on concurrent streams (each lane with its own workspace and Err slot)
   std::vector<double> resid(count, NAN);
   std::vector<int> rit(count, 0);

@@ -1,7 +1,8 @@
 // The congruence transform H_perp = Z^T H Z (Sec. 2, Eq. standard_form): with Z^T S Z = I it
 // turns the generalized eigenproblem H C = S C e into the standard one H_perp C_perp = C_perp e,
 // C = Z C_perp.  Both products reuse the factorization's kernels: FP64 CUDA-core products,
-// error-free slicing on the BF16 tensor cores, or BF16 (hi/lo) tensor-core products.
+// FP64-accurate products on the BF16 tensor cores (CRT residues or error-free slices), or BF16
+// (hi/lo) tensor-core products.
 #include <string.h>
 
 #include "ctx.h"

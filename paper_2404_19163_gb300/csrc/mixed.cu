@@ -192,8 +192,9 @@ static int refine_native(zfact_ctx* c, const double* S, double* Z64, int n, int 
   return ZFACT_OK;
 }
 
-// Algorithm 3 with d = I - Z^T S Z and Z + Z Q formed to FP64 accuracy by error-free slicing on
-// the BF16 tensor cores; the polynomial's powers d^k (k >= 2) by FP16 hi/lo products.
+// Algorithm 3 with d = I - Z^T S Z and Z + Z Q formed to FP64 accuracy on the BF16 tensor cores
+// (CRT residues or error-free slices, ozaki.cu); the polynomial's powers d^k (k >= 2) by FP16
+// hi/lo products.
 int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, const zfact_opts& o, int iters,
                  int* ridx_out, zfact_info* inf) {
   int st = ZFACT_OK;

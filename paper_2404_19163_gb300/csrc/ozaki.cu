@@ -1,6 +1,7 @@
-// Host driver of the FP64-accurate products (error-free slicing, k_ozaki.cu) used
-// by the refinement of Algorithm 3: d = I - Z^T S Z and Z <- Z + Z Q formed to
-// FP64 accuracy on the BF16 tensor cores instead of GB300's ~1.1 TFLOP/s FP64 pipe.
+// Host driver of the FP64-accurate products used by the refinement of Algorithm 3:
+// d = I - Z^T S Z and Z <- Z + Z Q formed to FP64 accuracy on the BF16 tensor cores instead
+// of GB300's ~1.1 TFLOP/s FP64 pipe, by CRT residues (k_ozmod.cu) where the product bound fits
+// the moduli, else by error-free slices (k_ozaki.cu).
 #include <math.h>
 #include <string.h>
 
