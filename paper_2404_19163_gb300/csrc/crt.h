@@ -46,27 +46,6 @@ ZF_HD constexpr int crt_modulus(int i) {
   }
 }
 
-// Symmetric residue of +-a (a < 2^62) modulo m <= 127: in [-(m-1)/2, (m-1)/2] for odd m and
-// within [-m/2, m/2] for m = 64, so |r| <= 63.
-ZF_HD inline int crt_sym_residue(unsigned long long a, bool neg, int m) {
-  const unsigned um = (unsigned)m;
-  const unsigned hi = (unsigned)(a >> 32), lo = (unsigned)a;
-  const unsigned c32 = (unsigned)(4294967296ull % um);
-  const unsigned r = ((hi % um) * c32 + lo % um) % um;
-  int v = (int)r;
-  if (2 * v >= m) v -= m;
-  return neg ? -v : v;
-}
-
-// R mod m in [0, m) for |R| < 2^26 and m >= 17: the float quotient is off by at most one.
-ZF_HD inline int crt_mod(int R, int m, float inv) {
-  const int q = (int)floorf((float)R * inv);
-  int y = R - q * m;
-  if (y < 0) y += m;
-  if (y >= m) y -= m;
-  return y;
-}
-
 ZF_HD inline float crt_bits_f(unsigned u) {
 #ifdef __CUDA_ARCH__
   return __uint_as_float(u);
@@ -154,16 +133,9 @@ struct CrtAcc {
     L[0] = L[1] = L[2] = L[3] = 0ull;
     S = 0.0f;
   }
-  ZF_HD void add(const CrtPlan& p, int t, int R) {
-    const int m = p.m[t];
-    const float inv = p.inv[t];
-    int y = crt_mod(R, m, inv);
-    y = crt_mod(y * p.w[t], m, inv);
-    S = fmaf((float)y, inv, S);
-    for (int l = 0; l < 4; ++l) L[l] += (unsigned long long)(unsigned)y * p.P[t][l];
-  }
-  // The same from r = C mod m given as an integer-valued float with |r| <= 2^9 (a sum of up to
-  // kCrtMaxChunks outputs of crt_fmod_sym): r w_t stays below 2^16, so the FP32 reduction is exact.
+  // Adds modulus t's digit from r = C mod m_t, given as an integer-valued float with |r| <= 2^9 (a
+  // sum of up to kCrtMaxChunks outputs of crt_fmod_sym): r w_t stays below 2^16, so the FP32
+  // reduction is exact.
   ZF_HD void add_f(const CrtPlan& p, int t, float r) {
     const float m = p.fm[t], inv = p.inv[t];
     float y = crt_fmod_sym(r * p.fw[t], m, inv);

@@ -11,6 +11,26 @@
 
 using namespace zf;
 
+// Integer reference, independent of the FP32 arithmetic under test.
+// Symmetric residue of +-a (a < 2^62) modulo m: |r| <= m / 2.
+static int ref_sym_residue(unsigned long long a, bool neg, int m) {
+  int v = (int)(a % (unsigned long long)m);
+  if (2 * v >= m) v -= m;
+  return neg ? -v : v;
+}
+// R mod m in [0, m).
+static int ref_mod(long long R, int m) {
+  const long long y = R % m;
+  return (int)(y < 0 ? y + m : y);
+}
+// CrtAcc's sums from an exact integer residue R of C: y = (R mod m) w mod m, y P limbs, y / m.
+static void ref_add(CrtAcc& acc, const CrtPlan& p, int t, long long R) {
+  const int m = p.m[t];
+  const int y = ref_mod((long long)ref_mod(R, m) * p.w[t], m);
+  acc.S = fmaf((float)y, p.inv[t], acc.S);
+  for (int l = 0; l < 4; ++l) acc.L[l] += (unsigned long long)(unsigned)y * p.P[t][l];
+}
+
 static double to_double(__int128 x) {
   const bool neg = x < 0;
   const unsigned __int128 a = neg ? -(unsigned __int128)x : (unsigned __int128)x;
@@ -54,8 +74,8 @@ int main() {
         }
         __int128 exact = 0;
         for (int l = 0; l < K; ++l) exact += (__int128)a[l] * b[l];
-        // two reconstructions: integer residues with integer reduction (add), and the FP32 path of
-        // the kernels (crt_residue_f, per-chunk crt_fmod_sym, add_f)
+        // two reconstructions: the integer reference (exact residues and reductions), and the FP32
+        // path of the kernels (crt_residue_f, per-chunk crt_fmod_sym, add_f)
         CrtAcc acc, accf;
         acc.clear();
         accf.clear();
@@ -66,8 +86,8 @@ int main() {
           for (int c0 = 0; c0 < K; c0 += chunk) {
             long long part = 0, partf = 0;
             for (int l = c0; l < K && l < c0 + chunk; ++l) {
-              const int ra = crt_sym_residue((unsigned long long)(a[l] < 0 ? -a[l] : a[l]), a[l] < 0, m);
-              const int rb = crt_sym_residue((unsigned long long)(b[l] < 0 ? -b[l] : b[l]), b[l] < 0, m);
+              const int ra = ref_sym_residue((unsigned long long)(a[l] < 0 ? -a[l] : a[l]), a[l] < 0, m);
+              const int rb = ref_sym_residue((unsigned long long)(b[l] < 0 ? -b[l] : b[l]), b[l] < 0, m);
               float pa[5], pb[5];
               crt_parts(a[l], pa);
               crt_parts(b[l], pb);
@@ -88,7 +108,7 @@ int main() {
             R += part;
             rsum += crt_fmod_sym((float)partf, (float)m, p.inv[t]);
           }
-          acc.add(p, t, (int)R);
+          ref_add(acc, p, t, R);
           accf.add_f(p, t, rsum);
         }
         const double want = to_double(exact);
@@ -108,7 +128,7 @@ int main() {
     long long F = (long long)(rng() >> 1) - (1ll << 62);
     if (it % 4 == 1) F >>= (it / 4) % 62;  // all magnitudes
     const int m = crt_modulus(it % kCrtMax);
-    const int r = crt_sym_residue((unsigned long long)(F < 0 ? -F : F), F < 0, m);
+    const int r = ref_sym_residue((unsigned long long)(F < 0 ? -F : F), F < 0, m);
     float pa[5];
     crt_parts(F, pa);
     const float rf = crt_residue_f(pa, m);
@@ -124,17 +144,6 @@ int main() {
       const float r = crt_fmod_sym((float)x, (float)m, inv);
       if (r != floorf(r) || ((long long)r - x) % m != 0 || fabsf(r) > 0.62f * m) {
         printf("crt_fmod_sym(%lld, %d) = %g\n", x, m, r);
-        return 1;
-      }
-    }
-  }
-  for (int i = 0; i < kCrtMax; ++i) {  // crt_mod over |R| < 2^26
-    const int m = crt_modulus(i);
-    const float inv = 1.0f / (float)m;
-    for (long long R = -(1ll << 26) + 1; R < (1ll << 26); R += 997) {
-      const int y = crt_mod((int)R, m, inv);
-      if (y < 0 || y >= m || (R - y) % m != 0) {
-        printf("crt_mod(%lld, %d) = %d\n", R, m, y);
         return 1;
       }
     }
