@@ -15,7 +15,7 @@
 namespace zf {
 
 constexpr int kCrtMax = 20;       // moduli available; their product is just below 2^127
-constexpr int kCrtMaxChunks = 4;  // K-chunks summed per reconstruction (|sum| < 2^26)
+constexpr int kCrtMaxChunks = 4;  // K-chunks per reconstruction: their reduced sums stay below 2^9
 constexpr int kCrtMaxResidue = 63;  // largest |residue|: chunks of K <= 2^24 / 63^2 stay exact
 
 // Pairwise coprime moduli, largest first: primes and prime powers up to 127, and 17 last so
