@@ -1,0 +1,170 @@
+// Wider CRT arithmetic for residue products whose bound passes the twenty moduli of crt.h:
+// up to 31 pairwise coprime moduli (M below 2^183) in six 32-bit limbs, and fixed-point rows of
+// up to 84 bits as six 14-bit parts.  The first twenty moduli are crt.h's, in the same order,
+// so a plan of at most twenty moduli is the same plan.  Every modulus is at most 127, so the
+// residues, the K-chunk length (4224) and the FP32 reductions are those of crt.h.
+//
+// Not used by a kernel yet: checked on the host against exact big-integer products
+// (tests/test_crt_host.py).
+#pragma once
+#include "crt.h"
+
+namespace zf {
+namespace crtw {
+
+constexpr int kMax = 31;    // moduli
+constexpr int kLimbs = 6;   // 32-bit limbs of M and of the digit sums
+constexpr int kParts = 6;   // 14-bit parts of a fixed-point row value (|F| <= 2^84)
+
+// crt.h's twenty moduli, then the primes and prime powers left below 64 that are coprime to them.
+ZF_HD constexpr int modulus(int i) {
+  if (i < kCrtMax) return crt_modulus(i);
+  switch (i) {
+    case 20: return 53;
+    case 21: return 49;
+    case 22: return 47;
+    case 23: return 43;
+    case 24: return 41;
+    case 25: return 37;
+    case 26: return 31;
+    case 27: return 29;
+    case 28: return 23;
+    case 29: return 19;
+    case 30: return 13;
+    default: return 1;
+  }
+}
+
+// The six signed 14-bit parts of F (|F| <= 2^84), as floats: F = sum_k a_k 2^(14k).
+ZF_HD inline void parts(unsigned long long mag_hi, unsigned long long mag_lo, bool neg, float (&a)[kParts]) {
+  const float sg = neg ? -1.0f : 1.0f;
+  for (int k = 0; k < kParts; ++k) {
+    const int sh = 14 * k;
+    unsigned long long v;
+    if (sh + 14 <= 64)
+      v = mag_lo >> sh;
+    else if (sh >= 64)
+      v = mag_hi >> (sh - 64);
+    else
+      v = (mag_lo >> sh) | (mag_hi << (64 - sh));
+    a[k] = sg * (crt_bits_f(0x4B000000u | (unsigned)(v & 0x3FFFu)) - 8388608.0f);
+  }
+}
+
+// Symmetric residue of F modulo m from its six parts: x = sum_k a_k (2^(14k) mod m) stays below
+// 2^23 in magnitude (exact in FP32); the rest is crt_residue_f's reduction.
+ZF_HD inline float residue_f(const float (&a)[kParts], int m) {
+  const float fm = (float)m;
+  float x = a[kParts - 1] * (float)crt_pow2_sym(m, 14 * (kParts - 1));
+  for (int k = kParts - 2; k >= 1; --k) x = fmaf(a[k], (float)crt_pow2_sym(m, 14 * k), x);
+  x += a[0];
+  float r = fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
+  const float h = (float)(m / 2);
+  if (r > h)
+    r -= fm;
+  else if (r < -h)
+    r += fm;
+  return r;
+}
+
+struct Plan {
+  int nmod;
+  int m[kMax];
+  int w[kMax];
+  float inv[kMax], fm[kMax], fw[kMax];
+  unsigned P[kMax][kLimbs];
+  unsigned M[kLimbs];
+};
+
+// sum_t y_t P_t per 32-bit limb (each limb sum below 2^44) and sum_t y_t / m_t in FP32 (error far
+// below 1/4 for 31 terms); C = sum_t y_t P_t - q M modulo 2^192, exact while |C| < M / 4 < 2^181.
+struct Acc {
+  unsigned long long L[kLimbs];
+  float S;
+  ZF_HD void clear() {
+    for (int l = 0; l < kLimbs; ++l) L[l] = 0ull;
+    S = 0.0f;
+  }
+  ZF_HD void add_f(const Plan& p, int t, float r) {
+    const float m = p.fm[t], inv = p.inv[t];
+    float y = crt_fmod_sym(r * p.fw[t], m, inv);
+    if (y < 0.0f) y += m;
+    S = fmaf(y, inv, S);
+    const unsigned yi = crt_f_bits(y + 8388608.0f) & 0x7FFFFFu;
+    for (int l = 0; l < kLimbs; ++l) L[l] += (unsigned long long)yi * p.P[t][l];
+  }
+  // C 2^sc in FP64: the magnitude's three 64-bit words converted and added from the top.
+  ZF_HD double value(const Plan& p, int sc) const {
+    const long long q = (long long)rintf(S);
+    unsigned l[kLimbs];
+    long long carry = 0;
+    for (int k = 0; k < kLimbs; ++k) {
+      const long long t = (long long)L[k] - q * (long long)p.M[k] + carry;
+      l[k] = (unsigned)t;
+      carry = t >> 32;
+    }
+    unsigned long long w0 = ((unsigned long long)l[1] << 32) | l[0], w1 = ((unsigned long long)l[3] << 32) | l[2],
+                       w2 = ((unsigned long long)l[5] << 32) | l[4];
+    const bool neg = (l[5] >> 31) != 0u;
+    if (neg) {
+      w0 = ~w0 + 1ull;
+      const unsigned long long c1 = w0 == 0ull ? 1ull : 0ull;
+      w1 = ~w1 + c1;
+      const unsigned long long c2 = (c1 && w1 == 0ull) ? 1ull : 0ull;
+      w2 = ~w2 + c2;
+    }
+    const double v = ldexp((double)w2, 128 + sc) + (ldexp((double)w1, 64 + sc) + ldexp((double)w0, sc));
+    return neg ? -v : v;
+  }
+};
+
+// The moduli count that makes M exceed 2^bits (0 if all 31 do not), with the constants.  M and
+// M / m_i are formed in 32-bit limbs (products and quotients by small integers only).
+inline int plan(double bits, Plan* p) {
+  unsigned M[kLimbs + 1] = {1u};
+  int k = 0;
+  double lb = 0.0;
+  while (k < kMax && lb <= bits) {
+    const unsigned m = (unsigned)modulus(k);
+    unsigned long long c = 0;
+    for (int l = 0; l <= kLimbs; ++l) {
+      const unsigned long long t = (unsigned long long)M[l] * m + c;
+      M[l] = (unsigned)t;
+      c = t >> 32;
+    }
+    lb += log2((double)m);
+    ++k;
+  }
+  if (lb <= bits || M[kLimbs] != 0u) return 0;
+  p->nmod = k;
+  for (int l = 0; l < kLimbs; ++l) p->M[l] = M[l];
+  for (int i = 0; i < kMax; ++i) {
+    const unsigned m = i < k ? (unsigned)modulus(i) : 1u;
+    p->m[i] = (int)m;
+    p->inv[i] = 1.0f / (float)m;
+    p->fm[i] = (float)m;
+    p->w[i] = 0;
+    p->fw[i] = 0.0f;
+    for (int l = 0; l < kLimbs; ++l) p->P[i][l] = 0u;
+    if (i >= k) continue;
+    // P = M / m from the top limb down; the remainder of M / m is 0, and P mod m follows from P's limbs
+    unsigned long long rem = 0;
+    for (int l = kLimbs - 1; l >= 0; --l) {
+      const unsigned long long cur = (rem << 32) | M[l];
+      p->P[i][l] = (unsigned)(cur / m);
+      rem = cur % m;
+    }
+    unsigned long long pm = 0;
+    for (int l = kLimbs - 1; l >= 0; --l) pm = ((pm << 32) | p->P[i][l]) % m;
+    for (unsigned x = 1; x < m; ++x)
+      if ((pm * x) % m == 1u) {
+        p->w[i] = (int)x;
+        p->fw[i] = (float)x;
+        break;
+      }
+  }
+  return k;
+}
+
+}  // namespace crtw
+}  // namespace zf

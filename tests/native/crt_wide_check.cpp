@@ -1,0 +1,83 @@
+// Host check of the wider CRT arithmetic (paper_2404_19163_gb300/csrc/crt_wide.h).  Reads cases
+// (T, K, then K pairs of fixed-point values as sign, high and low 64-bit words of the magnitude),
+// forms the residue products as the tensor cores would (exact chunk sums of K <= 4224 terms, each
+// below 2^24) and prints the reconstructed product; the Python side compares it with the exact
+// big-integer product.  Also checks every residue against the magnitude modulo m.
+#include <math.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "../../paper_2404_19163_gb300/csrc/crt_wide.h"
+
+using namespace zf;
+
+int main(int argc, char** argv) {
+  if (argc < 2) return 2;
+  FILE* f = fopen(argv[1], "r");
+  if (!f) return 2;
+  int T, K;
+  const int chunk = 4224;
+  while (fscanf(f, "%d %d", &T, &K) == 2) {
+    std::vector<float> pa((size_t)K * crtw::kParts), pb((size_t)K * crtw::kParts);
+    std::vector<unsigned __int128> ma(K), mb(K);
+    std::vector<int> na(K), nb(K);
+    for (int l = 0; l < K; ++l) {
+      int sa, sb;
+      unsigned long long ah, al, bh, bl;
+      if (fscanf(f, "%d %llu %llu %d %llu %llu", &sa, &ah, &al, &sb, &bh, &bl) != 6) return 3;
+      float a[crtw::kParts], b[crtw::kParts];
+      crtw::parts(ah, al, sa < 0, a);
+      crtw::parts(bh, bl, sb < 0, b);
+      for (int k = 0; k < crtw::kParts; ++k) {
+        pa[(size_t)l * crtw::kParts + k] = a[k];
+        pb[(size_t)l * crtw::kParts + k] = b[k];
+      }
+      ma[l] = ((unsigned __int128)ah << 64) | al;
+      mb[l] = ((unsigned __int128)bh << 64) | bl;
+      na[l] = sa < 0;
+      nb[l] = sb < 0;
+    }
+    crtw::Plan p;
+    const int k = crtw::plan(2.0 * T + log2((double)K) + 2.0, &p);
+    if (!k) {
+      printf("noplan %d %d\n", T, K);
+      continue;
+    }
+    crtw::Acc acc;
+    acc.clear();
+    for (int t = 0; t < k; ++t) {
+      const int m = p.m[t];
+      float rsum = 0.0f;
+      for (int c0 = 0; c0 < K; c0 += chunk) {
+        long long part = 0;
+        for (int l = c0; l < K && l < c0 + chunk; ++l) {
+          float a[crtw::kParts], b[crtw::kParts];
+          for (int q = 0; q < crtw::kParts; ++q) {
+            a[q] = pa[(size_t)l * crtw::kParts + q];
+            b[q] = pb[(size_t)l * crtw::kParts + q];
+          }
+          const float ra = crtw::residue_f(a, m), rb = crtw::residue_f(b, m);
+          // congruence with the exact value and the symmetric range
+          const long long ea = (long long)(ma[l] % (unsigned)m) * (na[l] ? -1 : 1);
+          const long long eb = (long long)(mb[l] % (unsigned)m) * (nb[l] ? -1 : 1);
+          if ((((long long)ra - ea) % m) != 0 || (((long long)rb - eb) % m) != 0 || fabsf(ra) > (float)(m / 2) ||
+              fabsf(rb) > (float)(m / 2) || ra != floorf(ra) || rb != floorf(rb)) {
+            printf("badresidue %d %d %d\n", T, K, m);
+            return 1;
+          }
+          part += (long long)ra * (long long)rb;
+        }
+        if (part > (1ll << 24) || part < -(1ll << 24)) {
+          printf("chunk %lld\n", part);
+          return 1;
+        }
+        rsum += crt_fmod_sym((float)part, (float)m, p.inv[t]);
+      }
+      acc.add_f(p, t, rsum);
+    }
+    printf("%d %d %d %.17g\n", T, K, k, acc.value(p, 0));
+  }
+  fclose(f);
+  return 0;
+}
