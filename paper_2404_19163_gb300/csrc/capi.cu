@@ -430,7 +430,7 @@ extern "C" int zfact_set_workspace_limit(zfact_ctx* c, int64_t bytes) {
 
 extern "C" int zfact_set_emulation(zfact_ctx* c, int scheme) {
   if (!c) return ZFACT_ERR_ARG;
-  if (scheme != ZFACT_EMU_AUTO && scheme != ZFACT_EMU_SLICES)
+  if (scheme != ZFACT_EMU_AUTO && scheme != ZFACT_EMU_SLICES && scheme != ZFACT_EMU_WIDE)
     return ctx_fail(c, ZFACT_ERR_ARG, "unknown emulation scheme %d", scheme);
   c->oz_scheme = scheme;
   return ZFACT_OK;

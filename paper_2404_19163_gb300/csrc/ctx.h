@@ -52,7 +52,8 @@ struct zfact_ctx {
   int oz_s = 9;  // slices per operand of the current residual products
   int oz_T = 54;     // fixed-point bits per operand of the current residual products
   int oz_nmod = 0;   // > 0: those products use this many CRT residues instead of slices
-  int oz_scheme = 0;  // zfact_emulation: 0 residues where they fit, 1 slices always
+  int oz_wide = 0;   // 1: those residues use the wider moduli of crt_wide.h
+  int oz_scheme = 0;  // zfact_emulation: 0 residues where they fit, 1 slices always, 2 also wide residues
   cudaStream_t lane_stream[kLanes] = {};
   int lane = -1;
   size_t ws_limit = 0;  // cap on the workspace bytes (0 = none), zfact_set_workspace_limit

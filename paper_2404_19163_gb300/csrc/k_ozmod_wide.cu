@@ -1,0 +1,260 @@
+// Wider CRT residue products (crt_wide.h): rows of up to 83 bits kept as 128-bit fixed point, up to
+// 31 moduli, six-limb reconstruction.  Reached only with zfact_set_emulation(ZFACT_EMU_WIDE), for
+// products whose bound passes the twenty moduli of k_ozmod.cu (an ill-conditioned Z, whose
+// residual asks for 60 to 83 bits per row).  Same layouts and epilogue modes as k_ozmod.cu.
+#include <math.h>
+
+#include "crt_wide.h"
+#include "kernels.h"
+
+namespace zf {
+namespace {
+
+__device__ __forceinline__ int exp_bound_w(double v) {
+  int e;
+  frexp(v, &e);
+  return e;
+}
+
+// round(x 2^(T - e)) for |x| < 2^e and T <= 83, as sign and 128-bit magnitude (hi, lo), from the
+// bits of x.  For a normal x the shift T - e + E is at most T - 53, so the magnitude stays below 2^84.
+__device__ __forceinline__ void parts_w(double x, int er, int T, float (&a)[crtw::kParts]) {
+  unsigned long long hi = 0, lo = 0;
+  bool neg = false;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  if (er > -1000 && !(eb == 0 && m == 0)) {
+    int E;
+    if (eb == 0) {
+      E = -1074;
+    } else {
+      m |= 1ull << 52;
+      E = eb - 1075;
+    }
+    const int sh = E - er + T;
+    unsigned __int128 F;
+    if (sh >= 0)
+      F = (unsigned __int128)m << (sh < 74 ? sh : 74);
+    else if (sh > -63)
+      F = (unsigned __int128)((m + (1ull << (-sh - 1))) >> (-sh));
+    else
+      F = 0;
+    hi = (unsigned long long)(F >> 64);
+    lo = (unsigned long long)F;
+    neg = (bits >> 63) != 0;
+  }
+  crtw::parts(hi, lo, neg, a);
+}
+
+template <int I>
+__device__ __forceinline__ void wres_pair(const float (&p0)[crtw::kParts], const float (&p1)[crtw::kParts], int nmod,
+                                          uint16_t* o, size_t stride) {
+  if constexpr (I < crtw::kMax) {
+    if (I < nmod) {
+      const float r0 = crtw::residue_f(p0, crtw::modulus(I)), r1 = crtw::residue_f(p1, crtw::modulus(I));
+      *reinterpret_cast<unsigned*>(o + (size_t)I * stride) =
+          __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
+      wres_pair<I + 1>(p0, p1, nmod, o, stride);
+    }
+  }
+}
+
+template <int I>
+__device__ __forceinline__ void wres_one(const float (&p0)[crtw::kParts], int nmod, uint16_t* o, size_t stride) {
+  if constexpr (I < crtw::kMax) {
+    if (I < nmod) {
+      o[(size_t)I * stride] = (uint16_t)(__float_as_uint(crtw::residue_f(p0, crtw::modulus(I))) >> 16);
+      wres_one<I + 1>(p0, nmod, o, stride);
+    }
+  }
+}
+
+// Residues of the rows of X: one block of 256 threads per row, exponent pass then residue pass.
+__global__ void __launch_bounds__(256) k_ozmw_rowres(const double* __restrict__ X, int n, int ld, int* __restrict__ e,
+                                                     int T, int nmod, uint16_t* __restrict__ out, int ld16, int Rp) {
+  __shared__ double red[8];
+  const int row = blockIdx.x;
+  const int tid = threadIdx.x;
+  const double* xr = X + (size_t)row * ld;
+  double m = 0.0;
+  for (int c = tid; c < n; c += 256) m = fmax(m, fabs(xr[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  m = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+  const int er = m > 0.0 ? exp_bound_w(m) : -2000000000;
+  if (tid == 0) e[row] = er;
+  const size_t stride = (size_t)Rp * ld16;
+  uint16_t* orow = out + (size_t)row * ld16;
+  const int npair = n / 2;
+  for (int c = tid; c < npair; c += 256) {
+    float p0[crtw::kParts], p1[crtw::kParts];
+    parts_w(xr[2 * c], er, T, p0);
+    parts_w(xr[2 * c + 1], er, T, p1);
+    wres_pair<0>(p0, p1, nmod, orow + 2 * c, stride);
+  }
+  if ((n & 1) && tid == 0) {
+    float p0[crtw::kParts];
+    parts_w(xr[n - 1], er, T, p0);
+    wres_one<0>(p0, nmod, orow + (n - 1), stride);
+  }
+}
+
+// Residues of X^T (operand rows = columns of X; exponents from launch_oz_exp(cols = true)), through a
+// 64 x 32 shared-memory tile as k_ozmod.cu's transposed kernel.
+__global__ void k_ozmw_tres(const double* __restrict__ X, int n, int ld, const int* __restrict__ e, int T, int nmod,
+                            uint16_t* __restrict__ out, int ld16, int Rp) {
+  __shared__ double te[32][33], to[32][33];
+  const int bi = blockIdx.y * 64, bj = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int rr = ty; rr < 64; rr += 8) {
+    const int i = bi + rr, j = bj + tx;
+    const double x = (i < n && j < n) ? X[(size_t)i * ld + j] : 0.0;
+    if (rr & 1)
+      to[rr >> 1][tx] = x;
+    else
+      te[rr >> 1][tx] = x;
+  }
+  __syncthreads();
+  const size_t stride = (size_t)Rp * ld16;
+  const int col = bi + 2 * tx;
+  for (int r = ty; r < 32; r += 8) {
+    const int row = bj + r;
+    if (row >= n || col >= n) continue;
+    const int er = e[row];
+    float p0[crtw::kParts], p1[crtw::kParts];
+    parts_w(te[tx][r], er, T, p0);
+    parts_w(to[tx][r], er, T, p1);
+    uint16_t* o = out + (size_t)row * ld16 + col;
+    if (col + 1 < n)
+      wres_pair<0>(p0, p1, nmod, o, stride);
+    else
+      wres_one<0>(p0, nmod, o, stride);
+  }
+}
+
+// C' from up to 31 residue products (crtw::Acc), modes as k_ozmod.cu's combine: 0 out = C, 1 out += C,
+// 2 (sym) d = I - C with the block's sum of d^2 in partials[block].  32 x 32 tiles, blockDim 32 x 8,
+// four rows per thread; with sym only tiles on or above the diagonal run, mirrored through shared memory.
+__global__ void __launch_bounds__(256) k_ozmw_combine(const float* __restrict__ G, size_t gstride, int ld32, int nch,
+                                                      crtw::Plan plan, const int* __restrict__ eA,
+                                                      const int* __restrict__ eB, int TA, int TB, int n, double* out,
+                                                      int ld64, int mode, int sym, double* partials) {
+  __shared__ double tile[32][33];
+  __shared__ double red[256];
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const bool active = !(sym && bj < bi);
+  const int nmod = plan.nmod;
+  double ss = 0.0;
+  if (active) {
+    const int j = bj + threadIdx.x;
+    const int eb = j < n ? eB[j] : -2000000000;
+    const size_t slot = (size_t)nch * gstride;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int i = bi + threadIdx.y + 8 * q;
+      const bool ok = i < n && j < n;
+      const size_t off = ok ? (size_t)i * ld32 + j : 0;
+      float r[crtw::kMax];
+#pragma unroll
+      for (int t = 0; t < crtw::kMax; ++t) r[t] = 0.0f;
+      for (int c = 0; c < nch; ++c) {
+        const float* g = G + (size_t)c * gstride + off;
+        float v[crtw::kMax];
+#pragma unroll
+        for (int t = 0; t < crtw::kMax; ++t) v[t] = (ok && t < nmod) ? __ldcs(g + (size_t)t * slot) : 0.0f;
+#pragma unroll
+        for (int t = 0; t < crtw::kMax; ++t) r[t] += crt_fmod_sym(v[t], plan.fm[t], plan.inv[t]);
+      }
+      crtw::Acc acc;
+      acc.clear();
+#pragma unroll
+      for (int t = 0; t < crtw::kMax; ++t)
+        if (t < nmod) acc.add_f(plan, t, r[t]);
+      double v = 0.0;
+      if (ok) {
+        const int ea = eA[i];
+        if (ea > -1000 && eb > -1000) v = acc.value(plan, ea + eb - TA - TB);
+        if (mode == 2) {
+          v = (i == j ? 1.0 : 0.0) - v;
+          if (j >= i) ss += (i == j ? 1.0 : 2.0) * v * v;
+        }
+      }
+      if (ok && (!sym || j >= i)) {
+        double* o = out + (size_t)i * ld64 + j;
+        if (mode == 1)
+          *o += v;
+        else
+          *o = v;
+      }
+      tile[threadIdx.y + 8 * q][threadIdx.x] = v;
+    }
+    if (sym && bj > bi) {
+      __syncthreads();
+      for (int r = threadIdx.y; r < 32; r += 8) {
+        const int oi = bj + r, oj = bi + threadIdx.x;
+        if (oi < n && oj < n) {
+          double* o = out + (size_t)oi * ld64 + oj;
+          if (mode == 1)
+            *o += tile[threadIdx.x][r];
+          else
+            *o = tile[threadIdx.x][r];
+        }
+      }
+    } else if (sym) {
+      __syncthreads();
+      for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = bi + r, j2 = bj + threadIdx.x;
+        if (i < n && j2 < n && j2 < i) {
+          double* o = out + (size_t)i * ld64 + j2;
+          if (mode == 1)
+            *o += tile[threadIdx.x][r];
+          else
+            *o = tile[threadIdx.x][r];
+        }
+      }
+    }
+  }
+  if (mode == 2) {
+    red[tid] = ss;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (tid < w) red[tid] += red[tid + w];
+      __syncthreads();
+    }
+    if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
+                                 int ld16, int Rp, cudaStream_t s) {
+  if (nmod < 1 || nmod > crtw::kMax || T < 1 || T > 83) return cudaErrorInvalidValue;
+  for (int p = 0; p < nmod; ++p)  // padding rows n..Rp-1 of every plane read as zero
+    if (Rp > n) cudaMemsetAsync(out + ((size_t)p * Rp + n) * ld16, 0, sizeof(uint16_t) * (size_t)(Rp - n) * ld16, s);
+  if (trans) {
+    dim3 grid((n + 31) / 32, (n + 63) / 64), block(32, 8);
+    k_ozmw_tres<<<grid, block, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
+  } else {
+    k_ozmw_rowres<<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozmw_combine(const float* G, size_t gstride, int ld32, int nch, const crtw::Plan& plan,
+                                const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
+                                bool sym, double* partials, cudaStream_t s) {
+  if (nch < 1 || nch > kCrtMaxChunks || plan.nmod < 1 || plan.nmod > crtw::kMax) return cudaErrorInvalidValue;
+  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
+  k_ozmw_combine<<<grid, block, 0, s>>>(G, gstride, ld32, nch, plan, eA, eB, TA, TB, n, out, ld64, mode, sym ? 1 : 0,
+                                        partials);
+  return cudaGetLastError();
+}
+
+}  // namespace zf

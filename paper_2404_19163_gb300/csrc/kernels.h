@@ -6,6 +6,7 @@
 
 #include "common.cuh"
 #include "crt.h"
+#include "crt_wide.h"
 
 namespace zf {
 
@@ -92,6 +93,14 @@ cudaError_t launch_ozm_residues(const double* X, int n, int ld, bool trans, int*
 cudaError_t launch_ozm_combine(const float* G, size_t gstride, int ld32, int nch, const CrtPlan& plan, const int* eA,
                                const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
                                double* partials, cudaStream_t s);
+
+// The same with the wider moduli of crt_wide.h (k_ozmod_wide.cu): rows of up to 83 bits, up to
+// crtw::kMax planes and moduli.
+cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
+                                 int ld16, int Rp, cudaStream_t s);
+cudaError_t launch_ozmw_combine(const float* G, size_t gstride, int ld32, int nch, const crtw::Plan& plan,
+                                const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
+                                bool sym, double* partials, cudaStream_t s);
 
 // ---- error-free slicing (k_ozaki.cu)
 // e[r] = exponent bounding row r (cols = false) or column r (cols = true) of X.

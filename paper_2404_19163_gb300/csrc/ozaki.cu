@@ -26,6 +26,7 @@ struct OzOperand {
   int* e = nullptr;
   int Rp = 0, s = 0;  // s planes: slices, or CRT residues when nmod > 0
   int T = 0, nmod = 0;  // residues: fixed-point bits of the rows, moduli count (= s)
+  int wide = 0;         // residues modulo the wider moduli of crt_wide.h
 };
 
 // K-blocks per residue chunk: |residue| <= 63, so a chunk of K terms sums below K 63^2 <= 2^24.
@@ -69,13 +70,29 @@ int oz_make(zfact_ctx* c, const char* name, const double* X, int n, int ldx, boo
 // product is below n 2^(T_A + T_B), and M must exceed four times that.  0 = use slices (the
 // context asks for them, or the bound needs more than the twenty moduli give).
 int oz_mod_count(const zfact_ctx* c, int TA, int TB, int n) {
-  if (c->oz_scheme != ZFACT_EMU_AUTO || TA < 1 || TB < 1 || TA > 62 || TB > 62) return 0;
+  if (c->oz_scheme == ZFACT_EMU_SLICES || TA < 1 || TB < 1 || TA > 62 || TB > 62) return 0;
   CrtPlan p;
   return crt_plan(TA + TB + log2((double)n) + 2.0, &p);
 }
 
+// The same with the wider moduli (only when the context asks for them), for rows of up to 83 bits.
+int oz_mod_count_wide(const zfact_ctx* c, int TA, int TB, int n) {
+  if (c->oz_scheme != ZFACT_EMU_WIDE || TA < 1 || TB < 1 || TA > 83 || TB > 83) return 0;
+  crtw::Plan p;
+  return crtw::plan(TA + TB + log2((double)n) + 2.0, &p);
+}
+
+// Residues modulo the twenty moduli where they fit, else the wider ones where asked for (*wide = 1),
+// else 0 (slices).
+int oz_mod_choice(const zfact_ctx* c, int TA, int TB, int n, int* wide) {
+  *wide = 0;
+  int k = oz_mod_count(c, TA, TB, n);
+  if (k == 0 && (k = oz_mod_count_wide(c, TA, TB, n)) > 0) *wide = 1;
+  return k;
+}
+
 int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx, bool trans, int T, int nmod,
-                OzOperand* op) {
+                int wide, OzOperand* op) {
   int st = ZFACT_OK;
   const int ld16 = ld16_of(n), Rp = rp_of(n);
   std::string ns = lane_name(c, (std::string("oz.") + name + ".sl").c_str()),
@@ -88,9 +105,12 @@ int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx,
   op->s = nmod;
   op->T = T;
   op->nmod = nmod;
+  op->wide = wide;
   if ((st = ctx_cuda(c, klaunch(c, "oz_residues", 0, 8.0 * n * n + 2.0 * nmod * n * n, 2, [&] {
                        cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, cur_stream(c));
                        if (e != cudaSuccess) return e;
+                       if (wide)
+                         return launch_ozmw_residues(X, n, ldx, trans, op->e, T, nmod, op->sl, ld16, Rp, cur_stream(c));
                        return launch_ozm_residues(X, n, ldx, trans, op->e, T, nmod, op->sl, ld16, Rp, cur_stream(c));
                      }),
                      "oz residues")))
@@ -104,8 +124,10 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
                    int mode, double* partials = nullptr, bool* fused_resid = nullptr) {
   int st = ZFACT_OK;
   CrtPlan plan;
-  const int k = crt_plan(A.T + B.T + log2((double)n) + 2.0, &plan);
-  if (k < 1 || k != A.nmod || k != B.nmod)
+  crtw::Plan wplan;
+  const double bits = A.T + B.T + log2((double)n) + 2.0;
+  const int k = A.wide ? crtw::plan(bits, &wplan) : crt_plan(bits, &plan);
+  if (k < 1 || k != A.nmod || k != B.nmod || A.wide != B.wide)
     return ctx_fail(c, ZFACT_ERR_ARG, "residue operands do not match (%d, %d, %d moduli)", k, A.nmod, B.nmod);
   const int ld = ld16_of(n);
   const int kblocks = (n + 63) / 64;
@@ -163,6 +185,9 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
     }
     const double cbytes = 4.0 * k * nch * n * (double)n + 16.0 * n * n;
     if ((st = ctx_cuda(c, klaunch(c, "oz_crt", 0, cbytes, 1, [&] {
+                         if (A.wide)
+                           return launch_ozmw_combine(G, (size_t)n * ld, ld, nch, wplan, A.e, B.e, A.T, B.T, n, out,
+                                                      ld64, md, sym, partials, cur_stream(c));
                          return launch_ozm_combine(G, (size_t)n * ld, ld, nch, plan, A.e, B.e, A.T, B.T, n, out, ld64,
                                                    md, sym, partials, cur_stream(c));
                        }),
@@ -264,15 +289,15 @@ int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s) {
   OzOperand op;
   c->oz_s = s > 0 ? s : kOzSlicesResid;
   c->oz_T = kOzBits * c->oz_s;
-  c->oz_nmod = oz_mod_count(c, c->oz_T, c->oz_T, n);
-  if (c->oz_nmod > 0) return oz_make_mod(c, "S", S, n, n, false, c->oz_T, c->oz_nmod, &op);
+  c->oz_nmod = oz_mod_choice(c, c->oz_T, c->oz_T, n, &c->oz_wide);
+  if (c->oz_nmod > 0) return oz_make_mod(c, "S", S, n, n, false, c->oz_T, c->oz_nmod, c->oz_wide, &op);
   return oz_make(c, "S", S, n, n, false, c->oz_s, &op);
 }
 
 namespace {
 // An operand of the current residual products (slices or residues, as oz_prepare_S chose).
 int oz_make_resid(zfact_ctx* c, const char* name, const double* X, int n, bool trans, OzOperand* op) {
-  if (c->oz_nmod > 0) return oz_make_mod(c, name, X, n, n, trans, c->oz_T, c->oz_nmod, op);
+  if (c->oz_nmod > 0) return oz_make_mod(c, name, X, n, n, trans, c->oz_T, c->oz_nmod, c->oz_wide, op);
   return oz_make(c, name, X, n, n, trans, c->oz_s, op);
 }
 }  // namespace
@@ -288,6 +313,7 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   if (c->oz_nmod > 0) {
     Sop.s = Sop.nmod = c->oz_nmod;
     Sop.T = c->oz_T;
+    Sop.wide = c->oz_wide;
   }
   double* A64 = (double*)ctx_buf(c, lane_name(c, "oz.At64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!A64) return st;
@@ -354,12 +380,13 @@ int oz_update_slices(int n, double q) {
 int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, int n) {
   int st = ZFACT_OK;
   const int s = kOzSlicesResid, T = kOzBits * s;
-  const int nm = oz_mod_count(c, T, T, n);
+  int wide = 0;
+  const int nm = oz_mod_choice(c, T, T, n, &wide);
   OzOperand Hop, Zt, At;
   double* A64 = (double*)ctx_buf(c, lane_name(c, "oz.At64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!A64) return st;
   auto make = [&](const char* name, const double* X, bool trans, OzOperand* op) {
-    return nm > 0 ? oz_make_mod(c, name, X, n, n, trans, T, nm, op) : oz_make(c, name, X, n, n, trans, s, op);
+    return nm > 0 ? oz_make_mod(c, name, X, n, n, trans, T, nm, wide, op) : oz_make(c, name, X, n, n, trans, s, op);
   };
   if ((st = make("H", H, false, &Hop))) return st;
   if ((st = make("Zt", Z, true, &Zt))) return st;
@@ -376,10 +403,11 @@ int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax) {
   if (qmax == 0.0) return ZFACT_OK;  // Q = 0: Z is unchanged
   if (qmax > 0.0 && isfinite(qmax)) {
     // T = 53 + log2(4 sqrt(N) q) bits as below, kept exactly by CRT residues where they fit
-    const int Tu = oz_update_bits(n, qmax), nm = oz_mod_count(c, Tu, Tu, n);
+    int wide = 0;
+    const int Tu = oz_update_bits(n, qmax), nm = oz_mod_choice(c, Tu, Tu, n, &wide);
     if (nm > 0) {
-      if ((st = oz_make_mod(c, "Zr", Z, n, n, false, Tu, nm, &Zr))) return st;
-      if ((st = oz_make_mod(c, "Qr", Q, n, n, false, Tu, nm, &Qr))) return st;
+      if ((st = oz_make_mod(c, "Zr", Z, n, n, false, Tu, nm, wide, &Zr))) return st;
+      if ((st = oz_make_mod(c, "Qr", Q, n, n, false, Tu, nm, wide, &Qr))) return st;
       return oz_product(c, Zr, Qr, n, false, Z, n, 1);
     }
   }

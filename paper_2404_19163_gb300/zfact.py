@@ -24,7 +24,7 @@ WARN_NONCONTRACTIVE = 100
 
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 3, "fp16": 4, "fp16_split": 5, "bf16_split": 6}
 REFINE_MODE = {"native": 0, "ozaki": 1, "fp32": 2}
-EMULATION = {"auto": 0, "slices": 1}
+EMULATION = {"auto": 0, "slices": 1, "wide": 2}
 MLP_NPARAMS = 5573
 
 EXPORTED = (
@@ -268,7 +268,8 @@ class Context:
         self._raise(self.lib.zfact_set_workspace_limit(self.h, int(nbytes)))
 
     def set_emulation(self, scheme: str = "auto"):
-        """zfact_set_emulation: "auto" (CRT residues where they fit, else slices) or "slices"."""
+        """zfact_set_emulation: "auto" (CRT residues where they fit, else slices), "slices", or "wide"
+        (as "auto", with up to 31 moduli before slices; not yet measured on a GPU)."""
         self._raise(self.lib.zfact_set_emulation(self.h, EMULATION[scheme] if isinstance(scheme, str) else int(scheme)))
 
     def selftest_timeout(self) -> int:
