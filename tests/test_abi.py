@@ -78,3 +78,19 @@ def test_product_path_does_not_import_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "zfact_oracle" not in txt and "liboracle" not in txt, f
+
+
+def header_enum(prefix):
+    src = open(os.path.join(ROOT, "include", "zfact.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {name: int(val) for name, val in re.findall(r"\b(%s[A-Z0-9_]+)\s*=\s*(\d+)" % prefix, src)}
+
+
+@pytest.mark.parametrize("table,prefix", [("PRECISION", "ZFACT_P_"), ("REFINE_MODE", "ZFACT_R_"),
+                                          ("EMULATION", "ZFACT_EMU_")])
+def test_binding_names_match_header_enums(table, prefix):
+    """The binding's name -> value tables are the header's enumerators, value for value."""
+    from paper_2404_19163_gb300 import zfact
+    enum = header_enum(prefix)
+    mapping = getattr(zfact, table)
+    assert enum and {prefix + k.upper(): v for k, v in mapping.items()} == enum
