@@ -2,6 +2,7 @@
 
 This shows the pins in test_oracle_pins.py are sharp enough to catch a
 dropped term, a wrong sign or a transposed operand anywhere in the oracle."""
+import math
 from fractions import Fraction
 
 import numpy as np
@@ -13,13 +14,21 @@ sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 import test_oracle_pins as pins
 
 
-def _refine_with(poly_fn=None, update_fn=None, residual_fn=None):
+def _paper_stop(err, prev):
+    """Algorithm 2's test with reading 2's guards."""
+    return err > prev ** 3 or err >= prev or not np.isfinite(err)
+
+
+def _refine_with(poly_fn=None, update_fn=None, residual_fn=None, stop_fn=None):
     """Algorithm 2 assembled from (possibly mutated) oracle steps, fixed or stopped."""
     poly_fn = poly_fn or oracle.poly
     update_fn = update_fn or oracle.update
     residual_fn = residual_fn or oracle.residual
+    stop_fn = stop_fn or _paper_stop
 
     def refine(S, Z0, m=2, nmax=50, fixed_iters=0):
+        if Z0 is None:
+            Z0 = oracle.gershgorin_scale(S) * np.eye(S.shape[0])
         Z = np.array(Z0, dtype=np.float64)
         d, err = residual_fn(S, Z)
         hist = [err]
@@ -30,7 +39,7 @@ def _refine_with(poly_fn=None, update_fn=None, residual_fn=None):
             d, err = residual_fn(S, Z)
             it += 1
             hist.append(err)
-            if not fixed_iters and (err > prev ** 3 or err >= prev or not np.isfinite(err)):
+            if not fixed_iters and stop_fn(err, prev):
                 break
         return Z, np.array(hist), it
     return refine
@@ -41,6 +50,7 @@ def test_unmutated_assembly_passes():
     pins.check_diagonal(r)
     pins.check_two_by_two(r)
     pins.check_scalar_map(r)
+    pins.check_stop_rule(r)
 
 
 MUTANTS = {
@@ -65,6 +75,40 @@ def test_mutant_is_caught(name):
         except (AssertionError, np.linalg.LinAlgError, FloatingPointError, ValueError):
             caught += 1
     assert caught >= 1, name
+
+
+STOP_MUTANTS = {
+    "square_instead_of_cube": lambda err, prev: err > prev ** 2 or err >= prev or not np.isfinite(err),
+    "monotone_guard_dropped": lambda err, prev: err > prev ** 3 or not np.isfinite(err),
+    "cube_test_dropped": lambda err, prev: err >= prev or not np.isfinite(err),
+}
+
+
+@pytest.mark.parametrize("name", sorted(STOP_MUTANTS))
+def test_stop_mutant_is_caught(name):
+    with pytest.raises(AssertionError):
+        pins.check_stop_rule(_refine_with(stop_fn=STOP_MUTANTS[name]))
+
+
+def test_feature_mutants_are_caught():
+    def swapped_bounds(S):
+        f = oracle.features(S)
+        f[2] = 1.0 / f[2] if f[2] else f[2]           # g_hi / g_lo instead of g_lo / g_hi
+        return f
+
+    def frobenius_squared(S):
+        f = oracle.features(S)
+        f[15] = 2.0 * f[15]                           # log ||d0||_F^2 instead of log ||d0||_F
+        return f
+
+    def row_sums_signed(S):
+        f = oracle.features(S)
+        f[5] = np.mean(np.asarray(S).sum(axis=1)) / math.exp(f[1])   # signed instead of absolute sums
+        return f
+
+    for bad in (swapped_bounds, frobenius_squared, row_sums_signed):
+        with pytest.raises(AssertionError):
+            pins.check_features_by_hand(bad)
 
 
 def test_coefficient_mutants_are_caught(golden):

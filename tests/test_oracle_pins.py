@@ -208,6 +208,90 @@ def test_warm_start_limit():
     assert np.linalg.norm(Z - lim) / np.linalg.norm(lim) < 1e-13
 
 
+# ------------------------------------------------------------------ the stop rule (Sec. 4.1, Algorithm 2)
+# The stop iteration is predicted without the oracle: the exact residual history E_n comes from
+# the scalar map on eig(X0) (mpmath), and the computed Err_n is only assumed to lie in an interval
+# around E_n:
+#   E_n >= 1e-9: within 1e-9 E_n + 1e-12 (the agreement check_scalar_map asserts);
+#   E_n <  1e-9: in [max(PHI_LO, E_n - ETA), E_n + ETA], ETA a generous FP64 noise level for these
+#   N <= 64, cond <= 25 cases, and PHI_LO below one unit in the last place of 1 (2^-53): a computed
+#   d = I - X with any diagonal entry X_ii != 1 has |d_ii| >= 2^-53 (checked on the result below).
+# Rule (Algorithm 2 with reading 2's guard): stop after update n when Err_n > Err_{n-1}^3 or
+# Err_n >= Err_{n-1}.  A step is predicted only when every value in the intervals gives the same
+# answer; the inputs are chosen so that every step is determinate.
+STOP_PHI_LO, STOP_ETA = 1e-17, 1e-13
+
+
+def _stop_interval(E):
+    if E >= 1e-9:
+        t = 1e-9 * E + 1e-12
+        return E - t, E + t
+    return max(STOP_PHI_LO, E - STOP_ETA), E + STOP_ETA
+
+
+def predict_stop(mu, m=2, nmax=12):
+    """(n, which test fired) from the spectrum mu of X0 alone; n = None if a step is ambiguous."""
+    E = oracle.scalar_map_hist(mu, m, nmax)
+    for n in range(1, nmax + 1):
+        alo, ahi = _stop_interval(E[n - 1])
+        blo, bhi = _stop_interval(E[n])
+        cube_yes, cube_no = blo > ahi ** 3, bhi <= alo ** 3
+        guard_yes, guard_no = blo >= ahi, bhi < alo
+        if cube_yes:
+            return n, "cube"
+        if guard_yes:
+            return n, "guard"
+        if not (cube_no and guard_no):
+            return None, n
+    return None, "nmax"
+
+
+def _start_with_spectrum(n, seed, mu):
+    """Z0 = Q diag(sqrt(mu/lam)) Q^T, so X0 = Z0^T S Z0 = Q diag(mu) Q^T (S = Q diag(lam) Q^T)."""
+    S, Q, lam = synth.householder_spd(n, seed=seed)
+    return S, (Q * np.sqrt(mu / lam)) @ Q.T
+
+
+def stop_cases():
+    n = 32
+    # (a) the cube test fires at the FP64 floor: E_1 ~ 1e-6, so E_1^3 ~ 1e-18 lies below any
+    #     non-zero computed Err_2 while E_1^2 ~ 1e-12 lies above it (a squared test would go on)
+    mu_a = np.concatenate([[1.0 - 0.0117], np.full(n - 1, 1.0 - 1e-3)])
+    # (b) Err_0 >= 1 and the iteration diverges (an eigenvalue of X0 at 3 maps to 6.75): Err grows
+    #     but by less than its cube, so only the monotone guard stops it
+    mu_b = np.linspace(0.3, 3.0, n)
+    cases = [("cube_at_floor", *_start_with_spectrum(n, 3, mu_a), 2, "cube"),
+             ("monotone_guard", *_start_with_spectrum(n, 3, mu_b), 1, "guard")]
+    # (c) cold starts (Gershgorin-scaled identity, workload 1's generator)
+    for nn, seed in ((32, 4), (40, 1), (64, 0)):
+        S, Q, lam = synth.householder_spd(nn, seed=seed)
+        cases.append(("cold_%d_%d" % (nn, seed), S, None, None, "cube"))
+    return cases
+
+
+def check_stop_rule(refine_fn):
+    for name, S, Z0, expect_n, expect_kind in stop_cases():
+        n = S.shape[0]
+        Zs = Z0 if Z0 is not None else np.eye(n) / math.sqrt(np.max(np.abs(S).sum(axis=1)))
+        X0 = Zs.T @ S @ Zs
+        mu = np.linalg.eigvalsh(0.5 * (X0 + X0.T))
+        pred, kind = predict_stop(mu)
+        assert pred is not None, (name, kind)          # the input must give a determinate prediction
+        assert kind == expect_kind, (name, kind)
+        if expect_n is not None:
+            assert pred == expect_n, (name, pred)
+        Z, hist, it = refine_fn(S, Z0, m=2, nmax=50)
+        assert it == pred, (name, it, pred, hist)
+        if kind == "cube":
+            # premise of PHI_LO: the returned iterate's computed d has a non-zero diagonal entry
+            d = np.eye(n) - Z.T @ S @ Z
+            assert np.max(np.abs(np.diag(d))) > 0.0, name
+
+
+def test_stop_rule_predicted_from_scalar_map():
+    check_stop_rule(oracle.refine)
+
+
 def test_algorithm1_tolerance_rule():
     S, Q, lam = synth.householder_spd(32, seed=5)
     Z, hist, it = oracle.refine(S, None, m=2, nmax=50, rule=1, tol=1e-6)
@@ -292,6 +376,29 @@ def test_features_against_spectrum():
     from scipy.stats import moment
     assert abs(f[13] - moment(1 - mu, 3)) < 1e-13
     assert abs(f[14] - moment(1 - mu, 4)) < 1e-13
+
+
+def check_features_by_hand(features_fn):
+    """All 16 features of a 3 x 3 S computed by hand.
+    S = [[4,-1,0],[-1,3,1],[0,1,2]]: diagonal (4,3,2), absolute row sums (5,5,3) (signed: 3,3,3),
+    off-diagonal sums (1,2,1), so g_hi = max(5,5,3) = 5 and g_lo = min(3,1,1) = 1.  d0 = I - S/5 =
+    B/5 with B = [[1,1,0],[1,2,-1],[0,-1,3]]; B^2 = [[2,3,-1],[3,6,-5],[-1,-5,10]], so tr B = 6,
+    tr B^2 = 18, tr B^3 = 5 + 20 + 35 = 60, tr B^4 = sum of (B^2)_ij^2 = 210, and
+    t_k = tr(B^k) / (3 5^k): t1 = 2/5, t2 = 6/25, t3 = 4/25, t4 = 14/125.  ||d0||_F = sqrt(18)/5."""
+    S = np.array([[4.0, -1.0, 0.0], [-1.0, 3.0, 1.0], [0.0, 1.0, 2.0]])
+    t1, t2, t3, t4 = 0.4, 0.24, 0.16, 0.112
+    want = [math.log(3), math.log(5), 1 / 5, 3 / 5, 2 / 5, 13 / 15, 3 / 5, t1, t2, t3, t4,
+            math.sqrt(6) / 5, 0.08, 0.0, 0.0096, math.log(math.sqrt(18) / 5)]
+    # the central moments by hand: t2 - t1^2 = 0.08; t3 - 3 t1 t2 + 2 t1^3 = 0.16 - 0.288 + 0.128;
+    # t4 - 4 t1 t3 + 6 t1^2 t2 - 3 t1^4 = 0.112 - 0.256 + 0.2304 - 0.0768
+    f = features_fn(S)
+    assert len(f) == 16
+    for k, (x, w) in enumerate(zip(f, want)):
+        assert abs(x - w) <= 1e-14 * max(1.0, abs(w)), (k, x, w)
+
+
+def test_features_by_hand():
+    check_features_by_hand(oracle.features)
 
 
 # ------------------------------------------------------------------ MLP
