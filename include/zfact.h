@@ -294,9 +294,10 @@ int zfact_selftest_timeout(zfact_ctx* ctx);
  * N must be in 1..1024; larger N returns ZFACT_ERR_ARG and launches nothing.  The product
  * S Z and the norm partials live in one static device array of 8 MiB + 8 KiB that every
  * GPU loading this library holds until the process exits; all calls on a device share
- * it, so calls that overlap on the GPU race.  The first call on each device looks up that
- * array's device address with the device current; make that first call before any stream
- * capture.  No context is needed. */
+ * it, so calls that overlap on the GPU race.  Every call looks up that array's device
+ * address in the current context (a host-side query, no allocation); the first lookup in a
+ * context may load the library's device code, so make the first call on each device before
+ * any stream capture.  No context is needed. */
 int zfact_residual_noalloc(const double* S, const double* Z, int64_t N, double* D, double* err,
                            void* cuda_stream);
 

@@ -16,7 +16,6 @@
 // zero (every entry a call reads it has written first), and two calls that
 // overlap on the GPU (different streams, or different host threads) race on it.
 #include <math.h>
-#include <mutex>
 
 #include "ctx.h"
 #include "kernels.h"
@@ -28,24 +27,17 @@ namespace {
 constexpr int kNoallocMaxN = 1024;
 constexpr size_t kProdDoubles = (size_t)kNoallocMaxN * kNoallocMaxN;  // S Z, N x N
 constexpr size_t kPartDoubles = 1024;                                  // >= blocks of the symmetric product
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) double g_noalloc_scratch[kProdDoubles + kPartDoubles];
 
-std::mutex g_setup_mu;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device (looked up once per device).
-cudaError_t scratch_address(int device, double** out) {
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[device] = static_cast<double*>(p);
-  }
-  *out = g_scratch_addr[device];
+// Device address of the scratch array in the current context.  It is looked up on every call (a
+// host-side query): a cached address would go stale when the module is loaded again, after
+// cudaDeviceReset or in another driver context of the same device.  The first lookup in a context
+// may load the module, which is why the first call on a device should come before any stream capture.
+cudaError_t scratch_address(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -70,13 +62,11 @@ extern "C" int zfact_residual_noalloc(const double* S, const double* Z, int64_t 
   if (N < 1 || N > kNoallocMaxN) return ZFACT_ERR_ARG;
   const int n = (int)N;
   if (f64_num_blocks(n, true) > (int)kPartDoubles) return ZFACT_ERR_ARG;
-  int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess) {
-    cudaGetLastError();
-    return ZFACT_ERR_CUDA;
-  }
+  // an error left by earlier, unrelated work on this thread is not this call's: clear it before
+  // queuing anything (a sticky error still makes the launches below fail, and is reported then)
+  cudaGetLastError();
   double* scratch = nullptr;
-  if (scratch_address(device, &scratch) != cudaSuccess) {
+  if (scratch_address(&scratch) != cudaSuccess) {
     cudaGetLastError();
     return ZFACT_ERR_CUDA;
   }

@@ -106,7 +106,7 @@ int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx,
   op->T = T;
   op->nmod = nmod;
   op->wide = wide;
-  if ((st = ctx_cuda(c, klaunch(c, "oz_residues", 0, 8.0 * n * n + 2.0 * nmod * n * n, 2, [&] {
+  if ((st = ctx_cuda(c, klaunch(c, wide ? "oz_residues.wide" : "oz_residues", 0, 8.0 * n * n + 2.0 * nmod * n * n, 2, [&] {
                        cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, cur_stream(c));
                        if (e != cudaSuccess) return e;
                        if (wide)
@@ -184,7 +184,7 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
       *fused_resid = true;
     }
     const double cbytes = 4.0 * k * nch * n * (double)n + 16.0 * n * n;
-    if ((st = ctx_cuda(c, klaunch(c, "oz_crt", 0, cbytes, 1, [&] {
+    if ((st = ctx_cuda(c, klaunch(c, A.wide ? "oz_crt.wide" : "oz_crt", 0, cbytes, 1, [&] {
                          if (A.wide)
                            return launch_ozmw_combine(G, (size_t)n * ld, ld, nch, wplan, A.e, B.e, A.T, B.T, n, out,
                                                       ld64, md, sym, partials, cur_stream(c));

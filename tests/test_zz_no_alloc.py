@@ -1,4 +1,4 @@
-"""zfact_residual_noalloc against the allocating zfact_residual.
+"""zfact_residual_noalloc against the allocating zfact_residual and the FP64 oracle.
 
 Some callers cannot allocate device memory where they need the residual: an
 application whose own pool owns the whole device, or a latency-critical step
@@ -11,6 +11,8 @@ import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 from paper_2404_19163_gb300 import synth
 
@@ -42,6 +44,12 @@ def test_noalloc_residual_matches_zfact_residual_two_calls():
             d_ref = D_ref.cpu().numpy()
             assert np.linalg.norm(D.cpu().numpy() - d_ref) <= RTOL * max(1.0, np.linalg.norm(d_ref))
             assert abs(err.item() - err_ref) <= RTOL * max(1.0, err_ref)
+            # and against the oracle's FP64 d = I - Z^T S Z, element by element: two FP64
+            # evaluations of the same products differ by rounding on the scale of |Z|^T |S| |Z|
+            d_or, err_or = oracle.residual(S, Z)
+            scale = float(np.max(np.abs(Z).T @ (np.abs(S) @ np.abs(Z))))
+            assert float(np.max(np.abs(D.cpu().numpy() - d_or))) <= 1e-13 * scale
+            assert abs(err.item() - err_or) <= 1e-13 * scale * n
 
 
 def test_noalloc_rejects_oversize():
