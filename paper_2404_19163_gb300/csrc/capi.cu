@@ -81,6 +81,10 @@ int kstat_id(zfact_ctx* c, const char* name) {
   return (int)c->kstats.size() - 1;
 }
 
+void kstat_note(zfact_ctx* c, const char* name, double flops) {
+  if (c->profiling) c->kstats[kstat_id(c, name)].flops += flops;
+}
+
 cudaEvent_t ev_get(zfact_ctx* c) {
   if (!c->ev_pool.empty()) {
     cudaEvent_t e = c->ev_pool.back();

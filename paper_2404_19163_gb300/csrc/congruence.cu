@@ -3,6 +3,7 @@
 // C = Z C_perp.  Both products reuse the factorization's kernels: FP64 CUDA-core products,
 // FP64-accurate products on the BF16 tensor cores (CRT residues or error-free slices), or BF16
 // (hi/lo) tensor-core products.
+#include <math.h>
 #include <string.h>
 
 #include "ctx.h"
@@ -118,6 +119,13 @@ extern "C" int zfact_congruence(zfact_ctx* c, const double* H, const double* Z, 
     out = (double*)ctx_buf(c, "cg.out", bytes, &st);
     if (!out) return st;
   }
+  // non-finite inputs are reported, not passed on: the FP64-accurate scheme's row scaling would turn
+  // a NaN into a finite fixed-point value
+  if ((st = ctx_cuda(c, launch_amax_f64(Hd, n, c->st_dev, 3, c->stream), "amax H"))) return st;
+  if ((st = ctx_cuda(c, launch_amax_f64(Zd, n, c->st_dev, 2, c->stream), "amax Z"))) return st;
+  if ((st = ctx_read_state(c))) return st;
+  if (!isfinite(c->st_host->amax[3]) || !isfinite(c->st_host->amax[2]))
+    return ctx_fail(c, ZFACT_ERR_NONFINITE, "H or Z holds a NaN or Inf");
   if (precision == ZFACT_P_FP64)
     st = refine_mode == ZFACT_R_OZAKI ? oz_congruence(c, Hd, Zd, out, n) : f64_congruence(c, Hd, Zd, out, n);
   else

@@ -106,9 +106,21 @@ ZF_HD inline float crt_residue_f(const float (&a)[5], int m) {
   return r;
 }
 
-// x mod m for an integer-valued float |x| <= 2^24, m >= 17 (|x / m| < 2^20): congruent, within
-// about 0.62 m of 0.
+// x mod m for an integer-valued float |x| <= 2^24 and m >= 13, inv = FP32(1 / m): congruent, and
+// within 0.66 m of 0.  The FP32 quotient x * inv carries a relative error of at most 2^-23 (inv and
+// the product each rounded once), so it is off by at most 2^24 / 13 * 2^-23 = 0.154 from x / m (well
+// inside crt_rint's range); rint is then at most one step from the nearest integer, |x - m rint| <=
+// m (1/2 + 0.154), and the fma is exact because that difference is an integer below 2^24.
 ZF_HD inline float crt_fmod_sym(float x, float m, float inv) { return fmaf(-m, crt_rint(x * inv), x); }
+
+// The CRT digit of an exact residue-product sum v (integer-valued float, |v| <= 2^24): y = (v mod m) w
+// mod m in [0, m), w = (M / m)^-1 mod m the plan's weight of this modulus.  |v mod m| <= 0.66 m <= 84
+// and w < 127, so the product stays an exact integer below 2^14, and its reduction errs by far less
+// than one step (|y| <= m / 2 before the shift into [0, m)).
+ZF_HD inline float crt_digit(float v, float m, float inv, float w) {
+  float y = crt_fmod_sym(crt_fmod_sym(v, m, inv) * w, m, inv);
+  return y < 0.0f ? y + m : y;
+}
 
 // Reconstruction constants of the first nmod moduli: M = prod m_i, P_i = M / m_i as four
 // 32-bit limbs, w_i = P_i^-1 mod m_i.
@@ -122,8 +134,8 @@ struct CrtPlan {
   unsigned M[4];
 };
 
-// Accumulates sum_i y_i P_i (y_i = (C mod m_i) w_i mod m_i) per 32-bit limb without carries
-// (each limb sum stays below 2^44) and sum_i y_i / m_i in FP32.  That sum equals q + C / M for
+// Accumulates sum_i y_i P_i (y_i congruent to (C mod m_i) w_i modulo m_i, y_i < 2^9) per 32-bit limb
+// without carries (each limb sum stays below 2^46) and sum_i y_i / m_i in FP32.  That sum equals q + C / M for
 // an integer q; with |C| < M / 4 and an FP32 error far below 1/4, q = round(sum) and
 // C = sum_i y_i P_i - q M, formed modulo 2^128 (exact, since |C| < 2^125).
 struct CrtAcc {
@@ -133,16 +145,12 @@ struct CrtAcc {
     L[0] = L[1] = L[2] = L[3] = 0ull;
     S = 0.0f;
   }
-  // Adds modulus t's digit from r = C mod m_t, given as an integer-valued float with |r| <= 2^9 (a
-  // sum of up to kCrtMaxChunks outputs of crt_fmod_sym): r w_t stays below 2^16, so the FP32
-  // reduction is exact.
-  ZF_HD void add_f(const CrtPlan& p, int t, float r) {
-    const float m = p.fm[t], inv = p.inv[t];
-    float y = crt_fmod_sym(r * p.fw[t], m, inv);
-    if (y < 0.0f) y += m;  // [0, m)
-    S = fmaf(y, inv, S);
-    const unsigned yi = crt_f_bits(y + 8388608.0f) & 0x7FFFFFu;  // the integer y < 2^23
-    for (int l = 0; l < 4; ++l) L[l] += (unsigned long long)yi * p.P[t][l];
+  // Adds a sum y of CRT digits of modulus t (one per K-chunk, each in [0, m_t), so y < 2^9).  The
+  // digits need no reduction: any y congruent to (C mod m_t) w_t gives sum_t y_t P_t = C (mod M), and
+  // sum_t y_t / m_t is still q + C / M for an integer q (below 2^10 here, far from FP32's limits).
+  ZF_HD void add_y(const CrtPlan& p, int t, unsigned y) {
+    S = fmaf((float)y, p.inv[t], S);
+    for (int l = 0; l < 4; ++l) L[l] += (unsigned long long)y * p.P[t][l];
   }
   // C 2^sc in FP64 (two roundings).
   ZF_HD double value(const CrtPlan& p, int sc) const {

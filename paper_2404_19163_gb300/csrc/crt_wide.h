@@ -4,8 +4,8 @@
 // so a plan of at most twenty moduli is the same plan.  Every modulus is at most 127, so the
 // residues, the K-chunk length (4224) and the FP32 reductions are those of crt.h.
 //
-// Not used by a kernel yet: checked on the host against exact big-integer products
-// (tests/test_crt_host.py).
+// Used by the residue kernels of k_ozmod_wide.cu (residues) and k_ozmod.cu (reconstruction); the
+// arithmetic is checked on the host against exact big-integer products (tests/test_crt_host.py).
 #pragma once
 #include "crt.h"
 
@@ -33,6 +33,19 @@ ZF_HD constexpr int modulus(int i) {
     case 30: return 13;
     default: return 1;
   }
+}
+
+// CRT digit weight of modulus t in the plan of the first k moduli: w_t = (M / m_t)^-1 mod m_t,
+// M = m_0 ... m_{k-1}, the value plan() stores in w[t] (checked against it on the host), formed
+// from small products only.
+ZF_HD inline int digit_weight(int t, int k) {
+  const int m = modulus(t);
+  int p = 1 % m;
+  for (int s = 0; s < k; ++s)
+    if (s != t) p = (p * (modulus(s) % m)) % m;
+  for (int x = 1; x < m; ++x)
+    if ((p * x) % m == 1) return x;
+  return 0;
 }
 
 // The six signed 14-bit parts of F (|F| <= 2^84), as floats: F = sum_k a_k 2^(14k).
@@ -85,13 +98,11 @@ struct Acc {
     for (int l = 0; l < kLimbs; ++l) L[l] = 0ull;
     S = 0.0f;
   }
-  ZF_HD void add_f(const Plan& p, int t, float r) {
-    const float m = p.fm[t], inv = p.inv[t];
-    float y = crt_fmod_sym(r * p.fw[t], m, inv);
-    if (y < 0.0f) y += m;
-    S = fmaf(y, inv, S);
-    const unsigned yi = crt_f_bits(y + 8388608.0f) & 0x7FFFFFu;
-    for (int l = 0; l < kLimbs; ++l) L[l] += (unsigned long long)yi * p.P[t][l];
+  // A sum y of CRT digits of modulus t (see CrtAcc::add_y): below 2^9, so every limb sum stays
+  // below 2^46 over 31 moduli.
+  ZF_HD void add_y(const Plan& p, int t, unsigned y) {
+    S = fmaf((float)y, p.inv[t], S);
+    for (int l = 0; l < kLimbs; ++l) L[l] += (unsigned long long)y * p.P[t][l];
   }
   // C 2^sc in FP64: the magnitude's three 64-bit words converted and added from the top.
   ZF_HD double value(const Plan& p, int sc) const {

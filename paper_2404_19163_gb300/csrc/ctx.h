@@ -66,6 +66,9 @@ struct zfact_ctx {
 };
 
 int kstat_id(zfact_ctx* c, const char* name);
+// Adds FLOPs to the statistics of `name` without a launch or a time: the FP64 product count of an
+// FP64-accurate product ("fp64_equiv": 2 N^2 K, half on symmetric tiles), whatever scheme formed it.
+void kstat_note(zfact_ctx* c, const char* name, double flops);
 cudaEvent_t ev_get(zfact_ctx* c);
 void kstats_flush(zfact_ctx* c);  // stream must be idle
 

@@ -19,7 +19,8 @@ __global__ void k_rowabs_max(const double* __restrict__ S, int n, IterState* st)
   for (int j = lane; j < n; j += 32) s += fabs(row[j]);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  // non-negative doubles order like their bit patterns
+  // non-negative doubles order like their bit patterns, and a NaN (or Inf) row sum orders above
+  // every finite one, so a non-finite entry of S leaves a non-finite maximum
   if (lane == 0) atomicMax(reinterpret_cast<unsigned long long*>(&st->amax[0]), __double_as_longlong(s));
 }
 
@@ -147,13 +148,17 @@ __global__ void k_f32_to_f64(const float* __restrict__ src, int n, int ld32, dou
   }
 }
 
+// max(m, x) that keeps a NaN (fmax drops it): a NaN anywhere makes the maximum NaN, whose bit
+// pattern then also wins the atomicMax below, so callers can test the result with isfinite.
+__device__ __forceinline__ double max_keep_nan(double m, double x) { return (x > m || x != x) ? x : m; }
+
 __global__ void k_amax_f64(const double* __restrict__ A, size_t total, IterState* st, int slot) {
   double m = 0.0;
 #pragma unroll 4
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
-    m = fmax(m, fabs(A[e]));
+    m = max_keep_nan(m, fabs(A[e]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = max_keep_nan(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0)
     atomicMax(reinterpret_cast<unsigned long long*>(&st->amax[slot]), (unsigned long long)__double_as_longlong(m));
 }

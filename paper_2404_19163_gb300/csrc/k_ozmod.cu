@@ -13,6 +13,7 @@
 // bits kept (about 6.4 bits per product), where slicing grows quadratically (s(s+1)/2 pairs).
 #include <math.h>
 
+#include "crt_wide.h"
 #include "kernels.h"
 
 namespace zf {
@@ -175,132 +176,116 @@ __global__ void k_ozm_tres(const double* __restrict__ X, int n, int ld, const in
   }
 }
 
-// The partials of all moduli of one element for K-chunk c (slot t * nch + c), issued together.
-__device__ __forceinline__ void load_moduli(const float* __restrict__ g, size_t slot, int nmod, bool ok,
-                                            float (&v)[kCrtMax]) {
-#pragma unroll
-  for (int t = 0; t < kCrtMax; ++t) v[t] = (ok && t < nmod) ? __ldcs(g + (size_t)t * slot) : 0.0f;
-}
-
-// C' from the residue products and the scales: per modulus the K-chunk partials (exact FP32
-// integers) are reduced (crt_fmod_sym) and summed, the CRT digits y_t = r_t w_t mod m_t weight the
-// limbs of M / m_t, and the FP32 sum of y_t / m_t gives the multiple of M to remove (CrtAcc).
-// Modes as the slicing combine: 0 out = C, 1 out += C, 2 (sym) d = I - C with the block's sum of
-// d^2 in partials[block].  32 x 32 tiles, blockDim 32 x 8, four rows per thread, two blocks per SM;
-// with one K-chunk the loads of the next row are in flight while a row is reduced.  With sym only
-// tiles on or above the diagonal run and the mirror goes through shared memory.
-__global__ void __launch_bounds__(256, 2) k_ozm_combine(const float* __restrict__ G, size_t gstride, int ld32, int nch,
-                                                        CrtPlan plan, const int* __restrict__ eA,
-                                                        const int* __restrict__ eB, int TA, int TB, int n,
-                                                        double* out, int ld64, int mode, int sym, double* partials) {
-  __shared__ double tile[32][33];
-  __shared__ double red[256];
-  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  const bool active = !(sym && bj < bi);
+// C' from the CRT digits of the residue products, scaled by 2^(eA_i + eB_j - TA - TB).  Plane
+// t * nch + c of G holds, for modulus t and K-chunk c, the byte y = (product mod m_t) w_t mod m_t
+// (the tensor-core epilogue kEpiCrt8); the digits of a modulus are summed over its chunks and
+// accumulated as sum_t y_t P_t in 32-bit limbs with sum_t y_t / m_t in FP32 (CrtAcc / crtw::Acc).
+// Modes: 0 out = C, 1 out += C, 2 (sym) d = I - C with the block's sum of d^2 in partials[block].
+// Tiles of 32 rows x 128 columns, blockDim 32 x 8: a thread forms 4 adjacent columns of 4 rows and
+// reads one 4-byte word per plane per row (a warp reads 128 consecutive bytes of a plane).  With sym
+// only entries j >= i are formed (their digits are the only ones written) and mirrored through
+// shared memory.
+template <class Plan, class Acc, int KMAX>
+__global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restrict__ G, size_t gstride, int ld8,
+                                                         int nch, const __grid_constant__ Plan plan,
+                                                         const int* __restrict__ eA, const int* __restrict__ eB, int TA,
+                                                         int TB, int n, double* __restrict__ out, int ld64, int mode,
+                                                         int sym, double* __restrict__ partials) {
+  __shared__ double tile[32][129];
+  __shared__ double red[8];
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 128;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool active = !sym || bj + 127 >= bi;
   const int nmod = plan.nmod;
   double ss = 0.0;
   if (active) {
-    const int j = bj + threadIdx.x;
-    const int eb = j < n ? eB[j] : -2000000000;
-    bool ok[4];
-    size_t off[4];
-    int ea[4];
+    const int j0 = bj + 4 * tx;
+    int eb[4];
 #pragma unroll
+    for (int k = 0; k < 4; ++k) eb[k] = j0 + k < n ? eB[j0 + k] : -2000000000;
+    const size_t tstride = (size_t)nch * gstride;
+#pragma unroll 1
     for (int q = 0; q < 4; ++q) {
-      const int i = bi + threadIdx.y + 8 * q;
-      ok[q] = i < n && j < n;
-      off[q] = ok[q] ? (size_t)i * ld32 + j : 0;
-      ea[q] = ok[q] ? eA[i] : -2000000000;
-    }
-    const size_t slot = (size_t)nch * gstride;
-    double val[4];
-    float cur[kCrtMax], nxt[kCrtMax];
-    if (nch == 1) load_moduli(G + off[0], slot, nmod, ok[0], cur);
+      const int r = ty + 8 * q, i = bi + r;
+      const bool rok = i < n && j0 < n;
+      const uint8_t* g = G + (rok ? (size_t)i * ld8 + j0 : 0);
+      // per modulus the chunk digits summed in two 16-bit lanes per word (even and odd bytes)
+      unsigned ev[KMAX], od[KMAX];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float r[kCrtMax];
-      if (nch == 1) {
-        if (q < 3) load_moduli(G + off[q + 1], slot, nmod, ok[q + 1], nxt);
+      for (int t = 0; t < KMAX; ++t) {
+        ev[t] = 0u;
+        od[t] = 0u;
+      }
+      for (int c = 0; c < nch; ++c) {
 #pragma unroll
-        for (int t = 0; t < kCrtMax; ++t) r[t] = crt_fmod_sym(cur[t], plan.fm[t], plan.inv[t]);
-      } else {
-#pragma unroll
-        for (int t = 0; t < kCrtMax; ++t) r[t] = 0.0f;
-        for (int c = 0; c < nch; ++c) {
-          float v[kCrtMax];
-          load_moduli(G + (size_t)c * gstride + off[q], slot, nmod, ok[q], v);
-#pragma unroll
-          for (int t = 0; t < kCrtMax; ++t) r[t] += crt_fmod_sym(v[t], plan.fm[t], plan.inv[t]);
+        for (int t = 0; t < KMAX; ++t) {
+          const unsigned w =
+              (rok && t < nmod) ? __ldcs(reinterpret_cast<const unsigned*>(g + (size_t)t * tstride + (size_t)c * gstride))
+                                : 0u;
+          ev[t] += w & 0x00FF00FFu;
+          od[t] += (w >> 8) & 0x00FF00FFu;
         }
       }
-      CrtAcc acc;
-      acc.clear();
+      Acc acc[4];
 #pragma unroll
-      for (int t = 0; t < kCrtMax; ++t)
-        if (t < nmod) acc.add_f(plan, t, r[t]);
-      const int i = bi + threadIdx.y + 8 * q;
-      double v = 0.0;
-      if (ok[q]) {
-        if (ea[q] > -1000 && eb > -1000) v = acc.value(plan, ea[q] + eb - TA - TB);
-        if (mode == 2) {
-          v = (i == j ? 1.0 : 0.0) - v;
-          if (j >= i) ss += (i == j ? 1.0 : 2.0) * v * v;
+      for (int k = 0; k < 4; ++k) acc[k].clear();
+#pragma unroll
+      for (int t = 0; t < KMAX; ++t) {
+        if (t < nmod) {
+          acc[0].add_y(plan, t, ev[t] & 0xFFFFu);
+          acc[1].add_y(plan, t, od[t] & 0xFFFFu);
+          acc[2].add_y(plan, t, ev[t] >> 16);
+          acc[3].add_y(plan, t, od[t] >> 16);
         }
       }
-      val[q] = v;
-      if (nch == 1 && q < 3) {
+      const int ea = i < n ? eA[i] : -2000000000;
 #pragma unroll
-        for (int t = 0; t < kCrtMax; ++t) cur[t] = nxt[t];
+      for (int k = 0; k < 4; ++k) {
+        const int j = j0 + k;
+        double v = 0.0;
+        if (i < n && j < n) {
+          if (ea > -1000 && eb[k] > -1000) v = acc[k].value(plan, ea + eb[k] - TA - TB);
+          if (mode == 2) {
+            v = (i == j ? 1.0 : 0.0) - v;
+            if (j >= i) ss += (i == j ? 1.0 : 2.0) * v * v;
+          }
+          if (!sym || j >= i) {
+            double* o = out + (size_t)i * ld64 + j;
+            if (mode == 1)
+              *o += v;
+            else
+              *o = v;
+          }
+        }
+        tile[r][4 * tx + k] = v;
       }
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = threadIdx.y + 8 * q;
-      const int i = bi + r;
-      if (ok[q] && (!sym || j >= i)) {
-        double* o = out + (size_t)i * ld64 + j;
-        if (mode == 1)
-          *o += val[q];
-        else
-          *o = val[q];
-      }
-      tile[r][threadIdx.x] = val[q];
-    }
-    if (sym && bj > bi) {
+    if (sym) {
+      // (i, j) with j > i also goes to (j, i): rows bj.. of the output, columns bi..
       __syncthreads();
-      for (int r = threadIdx.y; r < 32; r += 8) {
-        const int oi = bj + r, oj = bi + threadIdx.x;
-        if (oi < n && oj < n) {
+      for (int rr = ty; rr < 128; rr += 8) {
+        const int oi = bj + rr, oj = bi + tx;
+        if (oi < n && oj < n && oi > oj) {
           double* o = out + (size_t)oi * ld64 + oj;
           if (mode == 1)
-            *o += tile[threadIdx.x][r];
+            *o += tile[tx][rr];
           else
-            *o = tile[threadIdx.x][r];
-        }
-      }
-    } else if (sym) {
-      __syncthreads();
-      for (int r = threadIdx.y; r < 32; r += 8) {
-        const int i = bi + r, j2 = bj + threadIdx.x;
-        if (i < n && j2 < n && j2 < i) {
-          double* o = out + (size_t)i * ld64 + j2;
-          if (mode == 1)
-            *o += tile[threadIdx.x][r];
-          else
-            *o = tile[threadIdx.x][r];
+            *o = tile[tx][rr];
         }
       }
     }
   }
   if (mode == 2) {
-    red[tid] = ss;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if (tx == 0) red[ty] = ss;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (tid < w) red[tid] += red[tid + w];
-      __syncthreads();
+    if (ty == 0 && tx == 0) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += red[w];
+      partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
     }
-    if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
   }
 }
 
@@ -322,13 +307,27 @@ cudaError_t launch_ozm_residues(const double* X, int n, int ld, bool trans, int*
   return cudaGetLastError();
 }
 
-cudaError_t launch_ozm_combine(const float* G, size_t gstride, int ld32, int nch, const CrtPlan& plan, const int* eA,
-                               const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
-                               double* partials, cudaStream_t s) {
-  if (nch < 1 || nch > kCrtMaxChunks) return cudaErrorInvalidValue;
-  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-  k_ozm_combine<<<grid, block, 0, s>>>(G, gstride, ld32, nch, plan, eA, eB, TA, TB, n, out, ld64, mode, sym ? 1 : 0,
-                                       partials);
+int ozm_combine_blocks(int n) { return ((n + 127) / 128) * ((n + 31) / 32); }
+
+cudaError_t launch_ozm_combine8(const uint8_t* G, size_t gstride, int ld8, int nch, const CrtPlan& plan, const int* eA,
+                                const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
+                                double* partials, cudaStream_t s) {
+  if (nch < 1 || nch > kCrtMaxChunks || plan.nmod < 1 || plan.nmod > kCrtMax || (ld8 % 4) != 0)
+    return cudaErrorInvalidValue;
+  dim3 grid((n + 127) / 128, (n + 31) / 32), block(32, 8);
+  k_ozm_combine8<CrtPlan, CrtAcc, kCrtMax><<<grid, block, 0, s>>>(G, gstride, ld8, nch, plan, eA, eB, TA, TB, n, out,
+                                                                  ld64, mode, sym ? 1 : 0, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozmw_combine8(const uint8_t* G, size_t gstride, int ld8, int nch, const crtw::Plan& plan,
+                                 const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
+                                 bool sym, double* partials, cudaStream_t s) {
+  if (nch < 1 || nch > kCrtMaxChunks || plan.nmod < 1 || plan.nmod > crtw::kMax || (ld8 % 4) != 0)
+    return cudaErrorInvalidValue;
+  dim3 grid((n + 127) / 128, (n + 31) / 32), block(32, 8);
+  k_ozm_combine8<crtw::Plan, crtw::Acc, crtw::kMax><<<grid, block, 0, s>>>(G, gstride, ld8, nch, plan, eA, eB, TA, TB,
+                                                                         n, out, ld64, mode, sym ? 1 : 0, partials);
   return cudaGetLastError();
 }
 

@@ -1,7 +1,8 @@
 // Wider CRT residue products (crt_wide.h): rows of up to 83 bits kept as 128-bit fixed point, up to
 // 31 moduli, six-limb reconstruction.  Reached only with zfact_set_emulation(ZFACT_EMU_WIDE), for
 // products whose bound passes the twenty moduli of k_ozmod.cu (an ill-conditioned Z, whose
-// residual asks for 60 to 83 bits per row).  Same layouts and epilogue modes as k_ozmod.cu.
+// residual asks for 60 to 83 bits per row).  Same layouts as k_ozmod.cu, whose reconstruction kernel
+// takes the wider plan too.
 #include <math.h>
 
 #include "crt_wide.h"
@@ -137,100 +138,6 @@ __global__ void k_ozmw_tres(const double* __restrict__ X, int n, int ld, const i
   }
 }
 
-// C' from up to 31 residue products (crtw::Acc), modes as k_ozmod.cu's combine: 0 out = C, 1 out += C,
-// 2 (sym) d = I - C with the block's sum of d^2 in partials[block].  32 x 32 tiles, blockDim 32 x 8,
-// four rows per thread; with sym only tiles on or above the diagonal run, mirrored through shared memory.
-__global__ void __launch_bounds__(256) k_ozmw_combine(const float* __restrict__ G, size_t gstride, int ld32, int nch,
-                                                      crtw::Plan plan, const int* __restrict__ eA,
-                                                      const int* __restrict__ eB, int TA, int TB, int n, double* out,
-                                                      int ld64, int mode, int sym, double* partials) {
-  __shared__ double tile[32][33];
-  __shared__ double red[256];
-  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  const bool active = !(sym && bj < bi);
-  const int nmod = plan.nmod;
-  double ss = 0.0;
-  if (active) {
-    const int j = bj + threadIdx.x;
-    const int eb = j < n ? eB[j] : -2000000000;
-    const size_t slot = (size_t)nch * gstride;
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      const int i = bi + threadIdx.y + 8 * q;
-      const bool ok = i < n && j < n;
-      const size_t off = ok ? (size_t)i * ld32 + j : 0;
-      float r[crtw::kMax];
-#pragma unroll
-      for (int t = 0; t < crtw::kMax; ++t) r[t] = 0.0f;
-      for (int c = 0; c < nch; ++c) {
-        const float* g = G + (size_t)c * gstride + off;
-        float v[crtw::kMax];
-#pragma unroll
-        for (int t = 0; t < crtw::kMax; ++t) v[t] = (ok && t < nmod) ? __ldcs(g + (size_t)t * slot) : 0.0f;
-#pragma unroll
-        for (int t = 0; t < crtw::kMax; ++t) r[t] += crt_fmod_sym(v[t], plan.fm[t], plan.inv[t]);
-      }
-      crtw::Acc acc;
-      acc.clear();
-#pragma unroll
-      for (int t = 0; t < crtw::kMax; ++t)
-        if (t < nmod) acc.add_f(plan, t, r[t]);
-      double v = 0.0;
-      if (ok) {
-        const int ea = eA[i];
-        if (ea > -1000 && eb > -1000) v = acc.value(plan, ea + eb - TA - TB);
-        if (mode == 2) {
-          v = (i == j ? 1.0 : 0.0) - v;
-          if (j >= i) ss += (i == j ? 1.0 : 2.0) * v * v;
-        }
-      }
-      if (ok && (!sym || j >= i)) {
-        double* o = out + (size_t)i * ld64 + j;
-        if (mode == 1)
-          *o += v;
-        else
-          *o = v;
-      }
-      tile[threadIdx.y + 8 * q][threadIdx.x] = v;
-    }
-    if (sym && bj > bi) {
-      __syncthreads();
-      for (int r = threadIdx.y; r < 32; r += 8) {
-        const int oi = bj + r, oj = bi + threadIdx.x;
-        if (oi < n && oj < n) {
-          double* o = out + (size_t)oi * ld64 + oj;
-          if (mode == 1)
-            *o += tile[threadIdx.x][r];
-          else
-            *o = tile[threadIdx.x][r];
-        }
-      }
-    } else if (sym) {
-      __syncthreads();
-      for (int r = threadIdx.y; r < 32; r += 8) {
-        const int i = bi + r, j2 = bj + threadIdx.x;
-        if (i < n && j2 < n && j2 < i) {
-          double* o = out + (size_t)i * ld64 + j2;
-          if (mode == 1)
-            *o += tile[threadIdx.x][r];
-          else
-            *o = tile[threadIdx.x][r];
-        }
-      }
-    }
-  }
-  if (mode == 2) {
-    red[tid] = ss;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (tid < w) red[tid] += red[tid + w];
-      __syncthreads();
-    }
-    if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
-  }
-}
-
 }  // namespace
 
 cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
@@ -244,16 +151,6 @@ cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int
   } else {
     k_ozmw_rowres<<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ozmw_combine(const float* G, size_t gstride, int ld32, int nch, const crtw::Plan& plan,
-                                const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
-                                bool sym, double* partials, cudaStream_t s) {
-  if (nch < 1 || nch > kCrtMaxChunks || plan.nmod < 1 || plan.nmod > crtw::kMax) return cudaErrorInvalidValue;
-  dim3 grid((n + 31) / 32, (n + 31) / 32), block(32, 8);
-  k_ozmw_combine<<<grid, block, 0, s>>>(G, gstride, ld32, nch, plan, eA, eB, TA, TB, n, out, ld64, mode, sym ? 1 : 0,
-                                        partials);
   return cudaGetLastError();
 }
 

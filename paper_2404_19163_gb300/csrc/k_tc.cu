@@ -18,6 +18,7 @@
 // the device state and the CTA winds down (no trap).
 #include <stdio.h>
 
+#include "crt_wide.h"
 #include "tc_gemm.h"
 
 namespace zf {
@@ -203,6 +204,28 @@ __device__ __forceinline__ void put16_t(uint16_t* base, int ld, int i, int col0,
   }
 }
 
+// Store 32 bytes of row i starting at column col0 (entries j >= n, or j < i when `upper`, skipped).
+__device__ __forceinline__ void put8(uint8_t* base, int ld, int i, int col0, int n, bool upper, const uint32_t (&w)[8]) {
+  const bool full = (col0 + 32 <= n) && (!upper || col0 >= i);
+  uint8_t* row = base + (size_t)i * ld;
+  if (full) {
+    uint4* dst = reinterpret_cast<uint4*>(row + col0);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+      const int j = col0 + jj;
+      if (j < n && (!upper || j >= i)) row[j] = (uint8_t)(w[jj >> 2] >> (8 * (jj & 3)));
+    }
+  }
+}
+
+// Modulus of a residue product and its reconstruction weight (kEpiCrt8).
+struct CrtDigitConst {
+  float m, inv, w;
+};
+
 __device__ __forceinline__ void split32(const float (&x)[32], float sc, int bf16, bool want_lo, uint16_t (&h)[32],
                                         uint16_t (&l)[32]) {
 #pragma unroll
@@ -214,7 +237,7 @@ __device__ __forceinline__ void split32(const float (&x)[32], float sc, int bf16
 }
 
 __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, float (&v)[32], double& ss, float& amax,
-                                          float osc, float us, int group, int n, int row0) {
+                                          float osc, float us, int group, int n, int row0, const CrtDigitConst& cd) {
   // grouped problems are stacked along rows: shift every output/input base to the instance
   const size_t r16 = (size_t)row0 * a.ld16, r32 = (size_t)row0 * a.ld32, r64 = (size_t)row0 * a.ld64;
   uint16_t* o16h = a.o16h ? a.o16h + r16 : nullptr;
@@ -317,6 +340,23 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
     case kEpiG32: {
       float* g = f32 + (size_t)group * a.g_stride;
       put32(g, a.ld32, i, col0, n, a.sym != 0, false, v);
+      break;
+    }
+    case kEpiCrt8: {
+      // the accumulator is an exact integer below 2^24 (residues <= 63 over K-chunks of 4224); its
+      // CRT digit in [0, m) < 2^7 is all the reconstruction needs from this product
+      uint32_t w[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float y = crt_digit(v[4 * q + b], cd.m, cd.inv, cd.w);
+          word |= (__float_as_uint(y + 8388608.0f) & 0xFFu) << (8 * b);
+        }
+        w[q] = word;
+      }
+      put8(a.d8 + (size_t)group * a.g_stride, a.ld32, i, col0, n, a.sym != 0, w);
       break;
     }
     case kEpiZupd64: {
@@ -486,13 +526,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       decode_unit(pl.tile, a, pl.n, BN, bm, bn);
       const int i = bm * BM + q * 32 + lane;
       double ss = 0.0;
+      CrtDigitConst cd{1.0f, 1.0f, 0.0f};
+      if (a.epi == kEpiCrt8) {
+        cd.m = (float)crtw::modulus(pl.t);
+        cd.inv = 1.0f / cd.m;
+#pragma unroll
+        for (int t = 0; t < 32; ++t)
+          if (t == pl.t) cd.w = a.crt_w[t];
+      }
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         float v[32];
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
         const int col0 = bn * BN + c * 32;
         if (a.sym && col0 + 31 < bm * BM) continue;  // chunk entirely below the diagonal block
-        epi_chunk(a, i, col0, v, ss, amax, osc, us, pl.group, pl.n, pl.row0);
+        epi_chunk(a, i, col0, v, ss, amax, osc, us, pl.group, pl.n, pl.row0, cd);
       }
       tc_fence_before();
       __syncwarp();

@@ -88,19 +88,22 @@ cudaError_t launch_pow2_scales(IterState* st, int idx, float c1, float c2, cudaS
 // of operand row r at out[(t * Rp + r) * ld16 + k]; rows n..Rp-1 of every plane are zeroed.
 cudaError_t launch_ozm_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
                                 int ld16, int Rp, cudaStream_t s);
-// C' from the residue products G[t * nch + c] (FP32 exact integers) by the CRT, scaled by
-// 2^(eA_i + eB_j - TA - TB); modes, sym and partials as launch_oz_combine; nch <= kCrtMaxChunks.
-cudaError_t launch_ozm_combine(const float* G, size_t gstride, int ld32, int nch, const CrtPlan& plan, const int* eA,
-                               const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
-                               double* partials, cudaStream_t s);
+// C' from the CRT digits of the residue products (k_tc.cu epilogue kEpiCrt8: plane t * nch + c holds
+// the byte (product_t,c mod m_t) w_t mod m_t, row-major with leading dimension ld8), scaled by
+// 2^(eA_i + eB_j - TA - TB); modes as launch_oz_combine (mode 2 writes ozm_combine_blocks(n)
+// partials); sym forms i <= j and mirrors; nch <= kCrtMaxChunks.
+cudaError_t launch_ozm_combine8(const uint8_t* G, size_t gstride, int ld8, int nch, const CrtPlan& plan, const int* eA,
+                                const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
+                                double* partials, cudaStream_t s);
+int ozm_combine_blocks(int n);
 
-// The same with the wider moduli of crt_wide.h (k_ozmod_wide.cu): rows of up to 83 bits, up to
-// crtw::kMax planes and moduli.
+// Residues with the wider moduli of crt_wide.h (k_ozmod_wide.cu): rows of up to 83 bits, up to
+// crtw::kMax planes and moduli; and the reconstruction with the wider plan.
 cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
                                  int ld16, int Rp, cudaStream_t s);
-cudaError_t launch_ozmw_combine(const float* G, size_t gstride, int ld32, int nch, const crtw::Plan& plan,
-                                const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
-                                bool sym, double* partials, cudaStream_t s);
+cudaError_t launch_ozmw_combine8(const uint8_t* G, size_t gstride, int ld8, int nch, const crtw::Plan& plan,
+                                 const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
+                                 bool sym, double* partials, cudaStream_t s);
 
 // ---- error-free slicing (k_ozaki.cu)
 // e[r] = exponent bounding row r (cols = false) or column r (cols = true) of X.

@@ -19,7 +19,7 @@ constexpr int kOzBits = 6;             // bits per slice
 constexpr int kOzSlicesResid = 9;      // 54 bits: residual products of a well-scaled Z
 constexpr int kOzSlicesUpdateMin = 4;  // 24 bits: the least Z Q is formed with (see oz_update_slices)
 constexpr int kOzSlicesMax = 14;
-constexpr size_t kOzGBudget = (size_t)6 << 30;  // bytes of FP32 group partials per launch
+constexpr size_t kOzGBudget = (size_t)6 << 30;  // bytes of group partials (slices) or digits (CRT) per launch
 
 struct OzOperand {
   uint16_t* sl = nullptr;
@@ -119,9 +119,11 @@ int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx,
 }
 
 // out (mode 0: =, 1: +=, fused 2: I - .) A B^T to FP64 accuracy from the CRT residues of A and B:
-// one tensor-core product per modulus (group t = pair (t, t)), then the reconstruction.
+// one tensor-core product per modulus (group t = pair (t, t)) whose epilogue keeps only the CRT
+// digit of each entry (one byte), then the reconstruction from the digits.  A fused residual writes
+// *nparts Err partials.
 int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool sym, double* out, int ld64,
-                   int mode, double* partials = nullptr, bool* fused_resid = nullptr) {
+                   int mode, double* partials = nullptr, bool* fused_resid = nullptr, int* nparts = nullptr) {
   int st = ZFACT_OK;
   CrtPlan plan;
   crtw::Plan wplan;
@@ -132,12 +134,12 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
   const int ld = ld16_of(n);
   const int kblocks = (n + 63) / 64;
   const int nch_total = (kblocks + kCrtChunkKb - 1) / kCrtChunkKb;
-  const size_t slot_bytes = sizeof(float) * (size_t)n * ld;
+  const size_t slot_bytes = (size_t)n * ld;  // one digit plane
   int nch_b = (int)(kOzGBudget / (slot_bytes * k));
   if (nch_b < 1) nch_b = 1;
   if (nch_b > kCrtMaxChunks) nch_b = kCrtMaxChunks;
   if (nch_b > nch_total) nch_b = nch_total;
-  float* G = (float*)ctx_buf(c, lane_name(c, "oz.G").c_str(), slot_bytes * k * nch_b, &st);
+  uint8_t* G = (uint8_t*)ctx_buf(c, lane_name(c, "oz.G").c_str(), slot_bytes * k * nch_b, &st);
   if (!G) return st;
   TcMaps maps;
   memset(&maps, 0, sizeof(maps));
@@ -152,12 +154,13 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
     a.M = a.N = a.K = n;
     a.nseg = 1;
     a.sym = sym ? 1 : 0;
-    a.epi = kEpiG32;
+    a.epi = kEpiCrt8;
     a.bf16 = 1;
     a.unscale = 1.0f;
-    a.f32 = G;
+    a.d8 = G;
     a.ld32 = ld;
     a.g_stride = (size_t)n * ld;
+    for (int t = 0; t < k; ++t) a.crt_w[t] = A.wide ? wplan.fw[t] : plan.fw[t];
     a.oz_s = k;
     a.oz_diag = 1;
     a.oz_nch = nch;
@@ -172,7 +175,8 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
               kb_hi = (c0 + nch) * kCrtChunkKb < kblocks ? (c0 + nch) * kCrtChunkKb : kblocks;
     const double kk = (double)(kb_hi - kb_lo) * 64.0 < n ? (double)(kb_hi - kb_lo) * 64.0 : (double)n;
     const double flops = k * 2.0 * n * n * kk * (sym ? 0.5 : 1.0);
-    const double bytes = k * 2.0 * 2.0 * n * kk + 4.0 * k * nch * (double)n * n;
+    const double bytes = k * 2.0 * 2.0 * n * kk + 1.0 * k * nch * (double)n * n * (sym ? 0.5 : 1.0);
+    kstat_note(c, "fp64_equiv", flops / k);
     if ((st = ctx_cuda(c, klaunch(c, "tc_gemm.crt", flops, bytes, 1,
                                   [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, cur_stream(c)); }),
                        "tcgen05 residue products")))
@@ -182,14 +186,16 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
     if (fuse) {
       md = 2;
       *fused_resid = true;
+      if (nparts) *nparts = ozm_combine_blocks(n);
     }
-    const double cbytes = 4.0 * k * nch * n * (double)n + 16.0 * n * n;
+    // digits read (the upper triangle when sym), FP64 result written (read too when accumulating)
+    const double cbytes = (1.0 * k * nch * n * (double)n + (md == 1 ? 16.0 : 8.0) * n * n) * (sym ? 0.5 : 1.0);
     if ((st = ctx_cuda(c, klaunch(c, A.wide ? "oz_crt.wide" : "oz_crt", 0, cbytes, 1, [&] {
                          if (A.wide)
-                           return launch_ozmw_combine(G, (size_t)n * ld, ld, nch, wplan, A.e, B.e, A.T, B.T, n, out,
-                                                      ld64, md, sym, partials, cur_stream(c));
-                         return launch_ozm_combine(G, (size_t)n * ld, ld, nch, plan, A.e, B.e, A.T, B.T, n, out, ld64,
-                                                   md, sym, partials, cur_stream(c));
+                           return launch_ozmw_combine8(G, (size_t)n * ld, ld, nch, wplan, A.e, B.e, A.T, B.T, n, out,
+                                                       ld64, md, sym, partials, cur_stream(c));
+                         return launch_ozm_combine8(G, (size_t)n * ld, ld, nch, plan, A.e, B.e, A.T, B.T, n, out, ld64,
+                                                    md, sym, partials, cur_stream(c));
                        }),
                        "oz crt combine")))
       return st;
@@ -199,8 +205,10 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
 
 // out (mode 0: =, 1: +=) A B^T to FP64 accuracy, A and B given by their row slices.
 int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool sym, double* out, int ld64,
-               int mode, double* partials = nullptr, bool* fused_resid = nullptr) {
-  if (A.nmod > 0 || B.nmod > 0) return oz_product_mod(c, A, B, n, sym, out, ld64, mode, partials, fused_resid);
+               int mode, double* partials = nullptr, bool* fused_resid = nullptr, int* nparts = nullptr) {
+  if (A.nmod > 0 || B.nmod > 0)
+    return oz_product_mod(c, A, B, n, sym, out, ld64, mode, partials, fused_resid, nparts);
+  if (nparts) *nparts = oz_combine_blocks(n);
   int st = ZFACT_OK;
   const int s = A.s < B.s ? A.s : B.s;
   const int ld = ld16_of(n);
@@ -246,6 +254,7 @@ int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool
     const double pairs = s * (s + 1) / 2.0;
     const double flops = pairs * 2.0 * n * n * kk * (sym ? 0.5 : 1.0);
     const double bytes = pairs * 2.0 * 2.0 * n * kk + 4.0 * s * nch * (double)n * n;
+    kstat_note(c, "fp64_equiv", flops / pairs);
     if ((st = ctx_cuda(c, klaunch(c, "tc_gemm.ozaki", flops, bytes, 1,
                                   [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, cur_stream(c)); }),
                        "tcgen05 ozaki")))
@@ -319,10 +328,11 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   if (!A64) return st;
   double* X64 = (double*)ctx_buf(c, lane_name(c, "oz.X64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!X64) return st;
-  const int nb_fused = oz_combine_blocks(n), nb_sep = resid_from_x_blocks(n);
+  int nb_fused = oz_combine_blocks(n);
+  const int nb_sep = resid_from_x_blocks(n), nb_max = nb_fused > ozm_combine_blocks(n) ? nb_fused : ozm_combine_blocks(n);
   double* partials =
       (double*)ctx_buf(c, lane_name(c, "oz.partials").c_str(),
-                       sizeof(double) * (size_t)(nb_fused > nb_sep ? nb_fused : nb_sep), &st);
+                       sizeof(double) * (size_t)(nb_max > nb_sep ? nb_max : nb_sep), &st);
   if (!partials) return st;
   // rows of Z^T = columns of Z
   if ((st = oz_make_resid(c, "Zt", Z, n, true, &Zt))) return st;
@@ -332,7 +342,7 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   // X = Z^T A = Z^T (A^T)^T, symmetric tiles; d = I - X fused into the combine when possible
   bool fused = false;
   double* Xout = X64;
-  if ((st = oz_product(c, Zt, At, n, true, D, n, 0, partials, &fused))) return st;
+  if ((st = oz_product(c, Zt, At, n, true, D, n, 0, partials, &fused, &nb_fused))) return st;
   if (!fused) {
     // several K-chunk batches: the combine accumulated X into D; form d = I - X from it
     if ((st = ctx_cuda(c, cudaMemcpyAsync(Xout, D, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, cur_stream(c)),

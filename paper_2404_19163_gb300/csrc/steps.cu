@@ -117,6 +117,9 @@ extern "C" int zfact_residual(zfact_ctx* c, int mode, const double* S, const dou
     if ((st = ctx_cuda(c, launch_gershgorin(S, n, c->st_dev, c->stream), "gershgorin"))) return st;
     if ((st = ctx_cuda(c, launch_amax_f64(Z, n, c->st_dev, 2, c->stream), "amax Z"))) return st;
     if ((st = ctx_read_state(c))) return st;
+    // the fixed-point scaling takes row maxima, which would pass a NaN or Inf by as a finite value
+    if (!isfinite(c->st_host->amax[0]) || !isfinite(c->st_host->amax[2]))
+      return ctx_fail(c, ZFACT_ERR_NONFINITE, "S or Z holds a NaN or Inf");
     if ((st = oz_prepare_S(c, S, n, oz_slices_for(c->st_host->amax[2], c->st_host->amax[0])))) return st;
     if ((st = oz_residual(c, Z, Dw, n, 0, 0, 0.0, 0))) return st;
   } else if ((st = f64_residual(c, S, Z, A64, Dw, n, 0, 0, 0.0, 0))) {
@@ -124,5 +127,6 @@ extern "C" int zfact_residual(zfact_ctx* c, int mode, const double* S, const dou
   }
   if ((st = ctx_read_state(c))) return st;
   *err = c->st_host->hist[0];
+  if (!isfinite(*err)) return ctx_fail(c, ZFACT_ERR_NONFINITE, "the residual is not finite");
   return ZFACT_OK;
 }

@@ -20,6 +20,8 @@ enum TcEpi : int {
   kEpiF64 = 4,      // f64_out = v (double), row-major
   kEpiZupd64 = 5,   // f64_io += v (double); o16/t16 as kEpiZupd from the updated FP64 value
   kEpiG32 = 6,      // f32 + slot * g_stride = raw accumulator (Ozaki group partial), upper only when sym
+  kEpiCrt8 = 7,     // d8 + slot * g_stride = CRT digit (acc mod m_t) w_t mod m_t of residue product t
+                    // as one byte (row-major, leading dimension ld32), upper only when sym
 };
 
 struct TcArgs {
@@ -51,7 +53,9 @@ struct TcArgs {
   int oz_tiles;                 // output tiles of the product (units = oz_tiles * oz_s * oz_nch)
   int oz_diag;                  // residue mode: group t holds the one pair (t, t), i.e. oz_s
                                 // independent products A_t B_t^T (CRT residues)
-  size_t g_stride;              // kEpiG32: elements between group slots
+  size_t g_stride;              // kEpiG32 / kEpiCrt8: elements between group slots
+  uint8_t* d8;                  // kEpiCrt8: digit planes (slot t * oz_nch + c)
+  float crt_w[32];              // kEpiCrt8: digit weight w_t of modulus t in this product's plan
   // Grouped mode (ninst > 0): independent square problems stacked along the rows of every
   // operand and output buffer (common leading dimensions).  Scheduling slot j covers units
   // [g_prefix[j], g_prefix[j+1]) of instance g_inst[j]; instance i has size g_n[i], first row

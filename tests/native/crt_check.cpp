@@ -7,7 +7,7 @@
 #include <random>
 #include <vector>
 
-#include "../../paper_2404_19163_gb300/csrc/crt.h"
+#include "../../paper_2404_19163_gb300/csrc/crt_wide.h"
 
 using namespace zf;
 
@@ -75,14 +75,15 @@ int main() {
         __int128 exact = 0;
         for (int l = 0; l < K; ++l) exact += (__int128)a[l] * b[l];
         // two reconstructions: the integer reference (exact residues and reductions), and the FP32
-        // path of the kernels (crt_residue_f, per-chunk crt_fmod_sym, add_f)
+        // path of the kernels (crt_residue_f, the per-chunk digit crt_digit of the tensor-core
+        // epilogue, the digit sums over chunks, add_y)
         CrtAcc acc, accf;
         acc.clear();
         accf.clear();
         for (int t = 0; t < k; ++t) {
           const int m = p.m[t];
           long long R = 0;
-          float rsum = 0.0f;
+          unsigned ysum = 0;
           for (int c0 = 0; c0 < K; c0 += chunk) {
             long long part = 0, partf = 0;
             for (int l = c0; l < K && l < c0 + chunk; ++l) {
@@ -106,10 +107,16 @@ int main() {
               return 1;
             }
             R += part;
-            rsum += crt_fmod_sym((float)partf, (float)m, p.inv[t]);
+            const float y = crt_digit((float)partf, p.fm[t], p.inv[t], p.fw[t]);
+            if (y != floorf(y) || y < 0.0f || y >= (float)m ||
+                ((long long)y - (long long)ref_mod((long long)ref_mod(partf, m) * p.w[t], m)) % m != 0) {
+              printf("digit of %lld mod %d wrong: %g\n", partf, m, y);
+              return 1;
+            }
+            ysum += (unsigned)y;
           }
           ref_add(acc, p, t, R);
-          accf.add_f(p, t, rsum);
+          accf.add_y(p, t, ysum);
         }
         const double want = to_double(exact);
         for (const CrtAcc* A : {&acc, &accf}) {
@@ -137,16 +144,31 @@ int main() {
       return 1;
     }
   }
-  for (int i = 0; i < kCrtMax; ++i) {  // crt_fmod_sym over |x| <= 2^24
-    const int m = crt_modulus(i);
+  for (int i = 0; i < crtw::kMax; ++i) {  // crt_fmod_sym over |x| <= 2^24, every modulus down to 13
+    const int m = crtw::modulus(i);
     const float inv = 1.0f / (float)m;
     for (long long x = -(1ll << 24); x <= (1ll << 24); x += (x > -(1ll << 24) + 5000 && x < (1ll << 24) - 5000) ? 331 : 1) {
       const float r = crt_fmod_sym((float)x, (float)m, inv);
-      if (r != floorf(r) || ((long long)r - x) % m != 0 || fabsf(r) > 0.62f * m) {
+      if (r != floorf(r) || ((long long)r - x) % m != 0 || fabsf(r) > 0.66f * m) {
         printf("crt_fmod_sym(%lld, %d) = %g\n", x, m, r);
         return 1;
       }
     }
+  }
+  for (int k = 1; k <= kCrtMax; ++k) {  // the device's digit weights are the plan's
+    // bits = log2 of the first k - 1 moduli, summed as crt_plan sums them: the plan takes k moduli
+    double bits = 0.0;
+    for (int t = 0; t < k - 1; ++t) bits += log2((double)crt_modulus(t));
+    CrtPlan q;
+    if (crt_plan(bits, &q) != k) {
+      printf("plan of %d moduli not found\n", k);
+      return 1;
+    }
+    for (int t = 0; t < k; ++t)
+      if (crtw::digit_weight(t, k) != q.w[t]) {
+        printf("digit weight of modulus %d in a %d-moduli plan: %d vs %d\n", t, k, crtw::digit_weight(t, k), q.w[t]);
+        return 1;
+      }
   }
   CrtPlan p;
   if (crt_plan(122.0, &p) != 19 || crt_plan(124.0, &p) != 20 || crt_plan(127.0, &p) != 0) {

@@ -1,7 +1,8 @@
 // Host check of the wider CRT arithmetic (paper_2404_19163_gb300/csrc/crt_wide.h).  Reads cases
 // (T, K, then K pairs of fixed-point values as sign, high and low 64-bit words of the magnitude),
 // forms the residue products as the tensor cores would (exact chunk sums of K <= 4224 terms, each
-// below 2^24) and prints the reconstructed product; the Python side compares it with the exact
+// below 2^24, reduced to their CRT digits as the tensor-core epilogue does) and prints the
+// reconstructed product; the Python side compares it with the exact
 // big-integer product.  Also checks every residue against the magnitude modulo m.
 #include <math.h>
 #include <stdio.h>
@@ -44,11 +45,16 @@ int main(int argc, char** argv) {
       printf("noplan %d %d\n", T, K);
       continue;
     }
+    for (int t = 0; t < k; ++t)  // the device's digit weights are the plan's
+      if (crtw::digit_weight(t, k) != p.w[t]) {
+        printf("digitweight %d %d\n", t, k);
+        return 1;
+      }
     crtw::Acc acc;
     acc.clear();
     for (int t = 0; t < k; ++t) {
       const int m = p.m[t];
-      float rsum = 0.0f;
+      unsigned ysum = 0;
       for (int c0 = 0; c0 < K; c0 += chunk) {
         long long part = 0;
         for (int l = c0; l < K && l < c0 + chunk; ++l) {
@@ -72,9 +78,16 @@ int main(int argc, char** argv) {
           printf("chunk %lld\n", part);
           return 1;
         }
-        rsum += crt_fmod_sym((float)part, (float)m, p.inv[t]);
+        // the tensor-core epilogue's digit of this chunk sum, then the combine's digit sum
+        const float y = crt_digit((float)part, p.fm[t], p.inv[t], p.fw[t]);
+        const long long rm = ((part % m) + m) % m;
+        if (y != floorf(y) || y < 0.0f || y >= (float)m || ((long long)y - (rm * p.w[t]) % m) % m != 0) {
+          printf("digit %d %d %d\n", T, K, m);
+          return 1;
+        }
+        ysum += (unsigned)y;
       }
-      acc.add_f(p, t, rsum);
+      acc.add_y(p, t, ysum);
     }
     printf("%d %d %d %.17g\n", T, K, k, acc.value(p, 0));
   }

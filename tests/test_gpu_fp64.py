@@ -110,6 +110,35 @@ def test_errors(ctx):
     assert r.status == 100
 
 
+@pytest.mark.parametrize("mode", ["ozaki", "native"])
+def test_nonfinite_inputs_to_step_calls(ctx, mode):
+    """A NaN or Inf planted on the host in S, Z or H: the step-level residual and the congruence
+    report ZFACT_ERR_NONFINITE (the FP64-accurate scheme's row scaling must not turn them into finite
+    fixed-point values), and the context keeps working."""
+    from paper_2404_19163_gb300 import ZfactError
+    n = 70
+    S, Q, lam = synth.householder_spd(n, seed=12)
+    Z = (Q * lam ** -0.5) @ Q.T
+    for bad_s, bad_z, val in ((True, False, np.nan), (False, True, np.inf), (False, True, -np.nan)):
+        Sb, Zb = S.copy(), Z.copy()
+        if bad_s:
+            Sb[5, 9] = Sb[9, 5] = val
+        if bad_z:
+            Zb[n - 1, 3] = val
+        with pytest.raises(ZfactError) as e:
+            ctx.residual(dev(Sb), dev(Zb), mode)
+        assert e.value.code == 4, (bad_s, bad_z, val)
+        with pytest.raises(ZfactError) as e:
+            ctx.congruence(dev(Sb), dev(Zb), "fp64", mode)
+        assert e.value.code == 4
+    with pytest.raises(ZfactError) as e:
+        ctx.congruence(dev(S), dev(np.where(np.eye(n) > 0, np.nan, Z)), "bf16")
+    assert e.value.code == 4
+    # the context still works
+    d_or, e_or = oracle.residual(S, Z)
+    assert abs(ctx.residual(dev(S), dev(Z), mode) - e_or) <= 1e-12
+
+
 def test_workload2_full_size_against_oracle(ctx):
     """N = 4096 cubic Gaussian overlap, the launch configuration the benchmark times."""
     S = synth.cubic_overlap()
