@@ -396,7 +396,7 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
     if (st) return st;
     Zcur = c->mixed_result;
   } else {
-    st = mixed_refine(c, S, Zcur, Znext, n, order, precision, o, &iters, &ridx, &inf);
+    st = mixed_refine(c, S, Zcur, Znext, n, order, precision, o, &iters, &ridx, &inf, Z0_in == nullptr);
     if (st) return st;
     Zcur = c->mixed_result;
   }

@@ -125,5 +125,7 @@ int single_refine(zfact_ctx* c, const double* S, double* Za64, int n, int order,
                   int* ridx_out, zfact_info* inf);
 
 // Mixed-precision driver (mixed.cu): bulk tensor-core iterations, then Algorithm 3's refinement.
+// cold: Za holds the Gershgorin start Z0 = s I (s in the device state's gscale), whose first residual
+// and first update need no product.
 int mixed_refine(zfact_ctx* c, const double* S, double* Za, double* Zb, int n, int order, int precision,
-                 const zfact_opts& o, int* iters, int* ridx, zfact_info* inf);
+                 const zfact_opts& o, int* iters, int* ridx, zfact_info* inf, bool cold = false);

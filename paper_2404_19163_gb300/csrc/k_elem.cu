@@ -235,6 +235,116 @@ cudaError_t launch_split_flat(const double* A, int64_t n, double scale, uint16_t
   return cudaGetLastError();
 }
 
+// ---- cold start Z0 = s I (s = st->gscale, the Gershgorin scale of the start)
+// The first residual needs no product: A^T = Z0^T S = s S and X0 = Z0^T A = s^2 S, so
+// d0 = I - s^2 S, formed here from the upper triangle of S (X is defined by its upper triangle,
+// mirrored).  Writes d0 in FP32 (D32, leading dimension ld) and, when hi != nullptr, its 16-bit
+// hi (and lo, when lo != nullptr) copies; partials[block] = the block's sum of d0_ij^2 over the
+// entries it owns (off-diagonal entries twice), amax_bits = max |d0| as FP32 bits.  Blocks of
+// 32 x 8 threads walk the upper 32 x 32 tiles; the mirror goes through shared memory.
+__global__ void k_cold_resid(const double* __restrict__ S, int n, const IterState* __restrict__ st,
+                             float* __restrict__ D32, int ld, uint16_t* __restrict__ hi, uint16_t* __restrict__ lo,
+                             int bf16, double* __restrict__ partials, unsigned int* amax_bits) {
+  __shared__ float tile[32][33];
+  __shared__ double red[8];
+  const double s2 = st->gscale * st->gscale;
+  const int tb = (n + 31) / 32;
+  const int ntiles = tb * (tb + 1) / 2;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  double ss = 0.0;
+  float am = 0.0f;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // tile t -> (rb, cb), cb >= rb, row by row of the upper triangle
+    int rb = 0, rem = t;
+    while (rem >= tb - rb) {
+      rem -= tb - rb;
+      ++rb;
+    }
+    const int cb = rb + rem;
+    const int bi = rb * 32, bj = cb * 32;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q, i = bi + r, j = bj + tx;
+      float d = 0.0f;
+      if (i < n && j < n && j >= i) {
+        const double dd = (i == j ? 1.0 : 0.0) - s2 * S[(size_t)i * n + j];
+        d = (float)dd;
+        ss += (i == j ? 1.0 : 2.0) * dd * dd;
+        am = fmaxf(am, fabsf(d));
+        D32[(size_t)i * ld + j] = d;
+        if (hi) {
+          const uint16_t h = r16(d, bf16);
+          hi[(size_t)i * ld + j] = h;
+          if (lo) lo[(size_t)i * ld + j] = r16(d - f16v(h, bf16), bf16);
+        }
+      }
+      tile[r][tx] = d;
+    }
+    __syncthreads();
+    // mirror: (i, j) with j > i to (j, i): rows bj.., columns bi..
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 8 * q, oi = bj + r, oj = bi + tx;
+      if (oi < n && oj < n && oi > oj) {
+        const float d = tile[tx][r];
+        D32[(size_t)oi * ld + oj] = d;
+        if (hi) {
+          const uint16_t h = r16(d, bf16);
+          hi[(size_t)oi * ld + oj] = h;
+          if (lo) lo[(size_t)oi * ld + oj] = r16(d - f16v(h, bf16), bf16);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+  }
+  if (tx == 0) red[ty] = ss;
+  if (tx == 0) atomicMax(amax_bits, __float_as_uint(am));
+  __syncthreads();
+  if (tx == 0 && ty == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// The first update from a cold start: Z1 = Z0 + Z0 Q0 = s (I + Q0), elementwise from the FP32 Q0
+// (symmetric, both triangles written).  Writes the FP32 master Zm, the 16-bit copies of Z1
+// (scaled by *out_scale when given, as the update epilogue does) and the same values as the
+// transposed copy (Z1 is symmetric), and max |Z1| (FP32 bits) into amax_bits.
+__global__ void k_cold_update(const float* __restrict__ Q, int n, int ld, const IterState* __restrict__ st,
+                              float* __restrict__ Zm, uint16_t* zh, uint16_t* zl, uint16_t* th, uint16_t* tl,
+                              const float* out_scale, int bf16, unsigned int* amax_bits) {
+  const float s = (float)st->gscale;
+  const float osc = out_scale ? *out_scale : 1.0f;
+  float am = 0.0f;
+  const size_t total = (size_t)n * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const size_t o = (size_t)i * ld + j;
+    const float z = s * ((i == j ? 1.0f : 0.0f) + Q[o]);
+    Zm[o] = z;
+    am = fmaxf(am, fabsf(z));
+    const float y = z * osc;
+    const uint16_t h = r16(y, bf16);
+    zh[o] = h;
+    th[o] = h;
+    if (zl) {
+      const uint16_t l = r16(y - f16v(h, bf16), bf16);
+      zl[o] = l;
+      tl[o] = l;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax_bits, __float_as_uint(am));
+}
+
 static int grid_for(size_t total) { return (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192); }
 
 static dim3 rows_grid(int n) {
@@ -285,4 +395,26 @@ cudaError_t launch_finish_err(const double* partials, int nparts, IterState* st,
   return cudaGetLastError();
 }
 
+}  // namespace zf
+
+namespace zf {
+int cold_resid_blocks(int n) {
+  const int tb = (n + 31) / 32, t = tb * (tb + 1) / 2;
+  return t < 1024 ? t : 1024;
+}
+
+cudaError_t launch_cold_resid(const double* S, int n, const IterState* st, float* D32, int ld, uint16_t* hi,
+                              uint16_t* lo, bool bf16, double* partials, unsigned int* amax_bits, cudaStream_t s) {
+  k_cold_resid<<<cold_resid_blocks(n), dim3(32, 8), 0, s>>>(S, n, st, D32, ld, hi, lo, bf16 ? 1 : 0, partials,
+                                                           amax_bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cold_update(const float* Q, int n, int ld, const IterState* st, float* Zm, uint16_t* zh,
+                               uint16_t* zl, uint16_t* th, uint16_t* tl, const float* out_scale, bool bf16,
+                               unsigned int* amax_bits, cudaStream_t s) {
+  k_cold_update<<<grid_for((size_t)n * n), 256, 0, s>>>(Q, n, ld, st, Zm, zh, zl, th, tl, out_scale, bf16 ? 1 : 0,
+                                                       amax_bits);
+  return cudaGetLastError();
+}
 }  // namespace zf

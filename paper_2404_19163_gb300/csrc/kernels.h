@@ -82,6 +82,19 @@ cudaError_t launch_amax_f64(const double* A, int n, IterState* st, int slot, cud
 // bound_0 = amax[1] (d), bound_1 = c1*amax[1] + c2*hist[idx]^2 (Q), bound_2 = amax[2] (Z).
 cudaError_t launch_pow2_scales(IterState* st, int idx, float c1, float c2, cudaStream_t s);
 
+// Cold start Z0 = s I (s = st->gscale): d0 = I - s^2 S from S's upper triangle, in FP32 (D32) and,
+// when hi != nullptr, 16-bit hi (/lo) copies; cold_resid_blocks(n) Err partials; max |d0| (FP32
+// bits) into *amax_bits.
+int cold_resid_blocks(int n);
+cudaError_t launch_cold_resid(const double* S, int n, const IterState* st, float* D32, int ld, uint16_t* hi,
+                              uint16_t* lo, bool bf16, double* partials, unsigned int* amax_bits, cudaStream_t s);
+// The first update from that start, Z1 = s (I + Q0) from the FP32 Q0: FP32 master, 16-bit copies
+// (scaled by *out_scale when given) written to both the row-major and the transposed buffers (Z1 is
+// symmetric), max |Z1| (FP32 bits) into *amax_bits.
+cudaError_t launch_cold_update(const float* Q, int n, int ld, const IterState* st, float* Zm, uint16_t* zh,
+                               uint16_t* zl, uint16_t* th, uint16_t* tl, const float* out_scale, bool bf16,
+                               unsigned int* amax_bits, cudaStream_t s);
+
 // ---- modular residues (k_ozmod.cu)
 // Residue planes of X's rows (trans = false; e[r] written) or columns (trans = true; e from
 // launch_oz_exp): round(x 2^(T - e_r)) modulo crt_modulus(0..nmod-1), symmetric, as BF16; plane t

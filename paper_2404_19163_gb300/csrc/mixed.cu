@@ -303,7 +303,7 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
 }
 
 int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int n, int order, int precision,
-                 const zfact_opts& o, int* iters_out, int* ridx_out, zfact_info* inf) {
+                 const zfact_opts& o, int* iters_out, int* ridx_out, zfact_info* inf, bool cold) {
   const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
   const bool split = (precision == ZFACT_P_FP16_SPLIT || precision == ZFACT_P_BF16_SPLIT);
   // FP16 has a 5-bit exponent: every FP16 operand carries a power-of-two scale (exact, so it
@@ -342,8 +342,16 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     if (!Q32) return st;
   }
   const int max_units = tc_num_units(tc_args(n, bf16), 128) + 16;
-  double* partials = (double*)ctx_buf(c, "tc_partials", sizeof(double) * 4 * (size_t)max_units, &st);
+  const size_t npart = 4 * (size_t)max_units > (size_t)cold_resid_blocks(n) ? 4 * (size_t)max_units
+                                                                          : (size_t)cold_resid_blocks(n);
+  double* partials = (double*)ctx_buf(c, "tc_partials", sizeof(double) * npart, &st);
   if (!partials) return st;
+  // cold start: the first polynomial also keeps Q0 in FP32 for the elementwise first update
+  float* Q0 = nullptr;
+  if (cold) {
+    Q0 = (float*)ctx_buf(c, "Q0f32", sizeof(float) * (size_t)n * ld, &st);
+    if (!Q0) return st;
+  }
 
   auto elem = [&](const char* what, int count, auto&& f) -> int {
     return ctx_cuda(c, klaunch(c, "elementwise", 0, 0, count, f), what);
@@ -431,8 +439,38 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     return ZFACT_OK;
   };
 
-  // Q = sum_k c_k d^k (products of commuting symmetric matrices: symmetric tiles)
-  auto polynomial = [&]() -> int {
+  // Cold start Z0 = s I: the first residual is d0 = I - s^2 S (no product; the symmetric X is read
+  // from S's upper triangle), with the residual epilogue's outputs: FP32 d, its 16-bit copy, the Err
+  // partials and max |d|.
+  auto cold_residual = [&]() -> int {
+    int s2;
+    cudaMemsetAsync(&sd->amaxf[1], 0, sizeof(unsigned int), c->stream);
+    if ((s2 = elem("cold residual", 1, [&] {
+           return launch_cold_resid(S, n, sd, D32, ld, scaled ? nullptr : D16.h, scaled ? nullptr : D16.l, bf16,
+                                    partials, &sd->amaxf[1], c->stream);
+         })))
+      return s2;
+    if ((s2 = ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
+                         return launch_finish_err(partials, cold_resid_blocks(n), sd, 0, o.stop_rule, o.tol, n, 0,
+                                                  c->stream);
+                       }),
+                       "finish err")))
+      return s2;
+    if (scaled) {
+      if ((s2 = elem("d16", 2, [&] {
+             cudaError_t e = launch_fp16_scales(sd, 0, 0, (float)coef[1], (float)coef[2], 0, c->stream);
+             if (e == cudaSuccess)
+               e = launch_cvt16_f32(D32, n, ld, D16.h, D16.l, ld, false, false, sp(kSlotD), c->stream);
+             return e;
+           })))
+        return s2;
+    }
+    return ZFACT_OK;
+  };
+
+  // Q = sum_k c_k d^k (products of commuting symmetric matrices: symmetric tiles); q32 != nullptr
+  // also keeps the final Q in FP32
+  auto polynomial = [&](float* q32) -> int {
     int s2;
     Mat16* Pin = &D16;
     Mat16* Pout = &Pa;
@@ -452,6 +490,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
         kp.o16h = Q16.h;
         kp.o16l = Q16.l;
         kp.out_scale = sp(kSlotQ);
+        kp.f32 = q32;
       } else {
         kp.f32 = Q32;
         kp.t16h = Pout->h;
@@ -466,7 +505,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   };
 
   // ---- bulk phase (Algorithm 2)
-  if ((st = residual(0, 0))) return st;
+  if ((st = cold ? cold_residual() : residual(0, 0))) return st;
   if ((st = ctx_read_state(c))) return st;
   const double err0 = c->st_host->hist[0];
   if (!(err0 < 1.0)) inf->warn = ZFACT_WARN_NONCONTRACTIVE;
@@ -474,12 +513,21 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.nmax;
   int iters = 0;
   while (!done && iters < limit && iters + 1 + o.refine_steps + 1 < kHistMax) {
-    if ((st = polynomial())) return st;
+    const bool cold_update = cold && iters == 0;
+    if ((st = polynomial(cold_update ? Q0 : nullptr))) return st;
     if (scaled && (st = elem("scale Z", 1, [&] {
                      return launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zn_slot, c->stream);
                    })))
       return st;
     cudaMemsetAsync(&sd->amaxf[2], 0, sizeof(unsigned int), c->stream);
+    if (cold_update) {
+      // Z1 = Z0 + Z0 Q0 = s (I + Q0): no product
+      if ((st = elem("cold update", 1, [&] {
+             return launch_cold_update(Q0, n, ld, sd, Zm, Zn->h, Zn->l, Ztn->h, Ztn->l, sp(zn_slot), bf16,
+                                       &sd->amaxf[2], c->stream);
+           })))
+        return st;
+    }
     TcArgs k4 = tc_args(n, bf16);
     k4.epi = kEpiZupd;
     k4.split_out = split;
@@ -494,7 +542,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     k4.sb_ptr = sp(kSlotQ);
     k4.out_scale = sp(zn_slot);
     k4.amax_bits = &sd->amaxf[2];
-    if ((st = tc_product(c, k4, *Zc, Q16, ld, bn))) return st;
+    if (!cold_update && (st = tc_product(c, k4, *Zc, Q16, ld, bn))) return st;
     if (scaled && (st = elem("amax Z", 1, [&] { return launch_fp16_scales(sd, 3, 0, 0.f, 0.f, 0, c->stream); })))
       return st;
     std::swap(Zc, Zn);

@@ -6,7 +6,7 @@ each rank factorizing its own share.  Only host metadata (iteration counts, resi
 gathered, for reporting."""
 from __future__ import annotations
 
-from typing import List, Sequence
+from typing import Any, Dict, List, Sequence
 
 
 def assign(sizes: Sequence[int], world_size: int) -> List[List[int]]:
@@ -32,3 +32,23 @@ def imbalance(sizes: Sequence[int], world_size: int) -> float:
     parts = assign(sizes, world_size)
     loads = [sum(int(sizes[i]) ** 3 for i in p) for p in parts]
     return max(loads) / (sum(loads) / world_size)
+
+
+def gather(local: Dict[int, Any], count: int) -> List[Any]:
+    """Every rank's per-instance results ({instance index: result}) gathered on all ranks and
+    returned in instance order (host metadata only, through torch.distributed's object
+    all-gather).  Raises if an instance is missing or reported twice."""
+    import torch.distributed as dist
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, dict(local))
+    out: List[Any] = [None] * count
+    seen = set()
+    for part in parts:
+        for i, v in part.items():
+            if i in seen or not 0 <= i < count:
+                raise ValueError("instance %d reported twice or out of range" % i)
+            seen.add(i)
+            out[i] = v
+    if len(seen) != count:
+        raise ValueError("missing instances: %s" % sorted(set(range(count)) - seen)[:8])
+    return out
