@@ -613,6 +613,30 @@ def batched_leg(args, rank=0, ws=1, local=0, frames_timed=None, fp64_comparator=
     return out if rank == 0 else None
 
 
+def run_case_factor(args):
+    """Profiling case: the headline factorization alone (workload 2, the benchmark's precision and
+    refinement), W warm-up and K timed calls and nothing else, so that a launch list of it holds only
+    factorizations; prints its own JSON line with the launches per factorization."""
+    import torch
+    from paper_2404_19163_gb300 import Context, build as zbuild
+    zbuild.build()
+    S = torch.from_numpy(workload()).cuda()
+    n = S.shape[0]
+    Z = torch.empty_like(S)
+    with Context(0) as ctx:
+        kw = dict(order=2, precision=args.precision, tol=TOL, Z=Z)
+        for _ in range(args.warmup):
+            r = ctx.refine(S, None, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r = ctx.refine(S, None, **kw)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    print(json.dumps({"case": "factor", "N": n, "ms": round(ms, 3), "launches_per_factorization": r.info["launches"],
+                      "resid": r.info["resid_f"] / math.sqrt(n)}), flush=True)
+
+
 def run_batched(args, rank=0, ws=1, local=0):
     out = batched_leg(args, rank, ws, local, fp64_comparator=args.fp64_comparator)
     if out is not None:
@@ -768,7 +792,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the workload 3 and 4 legs that the default line carries as extra keys")
-    ap.add_argument("--case", default=None, choices=[None, "residual"])
+    ap.add_argument("--case", default=None, choices=[None, "residual", "factor"])
     ap.add_argument("--workload", default="single", choices=["single", "batched", "ill", "paper"])
     ap.add_argument("--paper-sizes", default="1024,4096,16384")
     ap.add_argument("--tol-ill", type=float, default=1e-12)
@@ -777,6 +801,9 @@ def main():
     args = ap.parse_args()
     if args.case == "residual":
         run_case_residual(args)
+        return
+    if args.case == "factor":
+        run_case_factor(args)
         return
     if args.workload == "batched":
         rank, ws, local = dist_setup()

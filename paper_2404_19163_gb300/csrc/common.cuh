@@ -41,6 +41,21 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 __device__ __forceinline__ void raise_error(int* flag, int bits) { atomicOr(flag, bits); }
 
+// Magnitudes of doubles on the integer pipes (GB300's FP64 pipe is a small fraction of them): the
+// bit pattern with the sign cleared orders like |x| (Inf above every finite value, NaN above Inf),
+// and frexp's exponent follows from it.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+__device__ __forceinline__ unsigned long long max_bits(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+// e with |x| in [2^(e-1), 2^e) for the non-zero, finite magnitude pattern b (frexp's exponent).
+__device__ __forceinline__ int exp_of_bits(unsigned long long b) {
+  const int eb = (int)(b >> 52);
+  return eb ? eb - 1022 : (63 - __clzll((long long)b)) - 1073;
+}
+
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));

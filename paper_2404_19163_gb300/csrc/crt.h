@@ -72,6 +72,62 @@ ZF_HD inline float crt_rint(float x) {
   return (x + C) - C;
 }
 
+ZF_HD inline double crt_bits_d(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double d;
+  memcpy(&d, &u, 8);
+  return d;
+#endif
+}
+ZF_HD inline int crt_clz64(unsigned long long x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+// The integer nearest (ties to even) to |x| < 2^22 with FP32 and integer operations only.
+ZF_HD inline int crt_rint_i(float x) { return (int)(crt_f_bits(x + 12582912.0f) - 0x4B400000u); }
+// An integer 0 <= y < 2^23 as a float, exactly (the bits of 2^23 + y, minus 2^23).
+ZF_HD inline float crt_u2f(unsigned y) { return crt_bits_f(0x4B000000u | y) - 8388608.0f; }
+
+// (neg ? -x : x) 2^sc for the 128-bit magnitude x = hi 2^64 + lo, rounded once to the nearest double
+// (ties to even), with integer operations only: GB300's FP64 pipe runs at a small fraction of its
+// integer rate, and a reconstruction converts every entry.  Results outside the normal range go
+// through ldexp of the exactly representable rounded significand.
+ZF_HD inline double crt_to_double(unsigned long long hi, unsigned long long lo, bool neg, int sc) {
+  if ((hi | lo) == 0ull) return 0.0;
+  const int lz = hi ? crt_clz64(hi) : 64 + crt_clz64(lo);
+  unsigned long long t, r;  // the magnitude shifted so that its leading one is bit 63 of t; r the rest
+  if (lz >= 64) {
+    t = lo << (lz - 64);
+    r = 0ull;
+  } else if (lz == 0) {
+    t = hi;
+    r = lo;
+  } else {
+    t = (hi << lz) | (lo >> (64 - lz));
+    r = lo << lz;
+  }
+  unsigned long long m = t >> 11;  // 53 significant bits
+  const bool round_bit = ((t >> 10) & 1ull) != 0ull, sticky = ((t & 0x3FFull) | r) != 0ull;
+  if (round_bit && (sticky || (m & 1ull))) ++m;
+  int e = 127 - lz + sc;  // value = m 2^(e - 52)
+  if (m >> 53) {
+    m >>= 1;
+    ++e;
+  }
+  const int be = e + 1023;
+  if (be <= 0 || be >= 2047) {
+    const double v = ldexp((double)m, e - 52);
+    return neg ? -v : v;
+  }
+  return crt_bits_d(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1ull)));
+}
+
 // 2^e mod m in symmetric form (|c| <= m/2).
 ZF_HD constexpr int crt_pow2_sym(int m, int e) {
   int r = 1 % m;
@@ -149,12 +205,12 @@ struct CrtAcc {
   // digits need no reduction: any y congruent to (C mod m_t) w_t gives sum_t y_t P_t = C (mod M), and
   // sum_t y_t / m_t is still q + C / M for an integer q (below 2^10 here, far from FP32's limits).
   ZF_HD void add_y(const CrtPlan& p, int t, unsigned y) {
-    S = fmaf((float)y, p.inv[t], S);
+    S = fmaf(crt_u2f(y), p.inv[t], S);
     for (int l = 0; l < 4; ++l) L[l] += (unsigned long long)y * p.P[t][l];
   }
-  // C 2^sc in FP64 (two roundings).
+  // C 2^sc in FP64, rounded once (crt_to_double).
   ZF_HD double value(const CrtPlan& p, int sc) const {
-    const long long q = (long long)rintf(S);
+    const long long q = crt_rint_i(S);
     long long t0 = (long long)L[0] - q * (long long)p.M[0];
     long long t1 = (long long)L[1] - q * (long long)p.M[1] + (t0 >> 32);
     long long t2 = (long long)L[2] - q * (long long)p.M[2] + (t1 >> 32);
@@ -166,8 +222,7 @@ struct CrtAcc {
       lo = ~lo + 1ull;
       hi = ~hi + (lo == 0ull ? 1ull : 0ull);
     }
-    const double v = ldexp((double)hi, 64 + sc) + ldexp((double)lo, sc);
-    return neg ? -v : v;
+    return crt_to_double(hi, lo, neg, sc);
   }
 };
 

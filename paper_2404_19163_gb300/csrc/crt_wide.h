@@ -101,12 +101,14 @@ struct Acc {
   // A sum y of CRT digits of modulus t (see CrtAcc::add_y): below 2^9, so every limb sum stays
   // below 2^46 over 31 moduli.
   ZF_HD void add_y(const Plan& p, int t, unsigned y) {
-    S = fmaf((float)y, p.inv[t], S);
+    S = fmaf(crt_u2f(y), p.inv[t], S);
     for (int l = 0; l < kLimbs; ++l) L[l] += (unsigned long long)y * p.P[t][l];
   }
-  // C 2^sc in FP64: the magnitude's three 64-bit words converted and added from the top.
+  // C 2^sc in FP64, rounded once.  With a non-zero top word the magnitude is at least 2^128, so its
+  // 53 leading bits lie in the top two words and the lowest word only decides the sticky bit (folded
+  // into the lowest bit of the middle word, far below the rounding position).
   ZF_HD double value(const Plan& p, int sc) const {
-    const long long q = (long long)rintf(S);
+    const long long q = crt_rint_i(S);
     unsigned l[kLimbs];
     long long carry = 0;
     for (int k = 0; k < kLimbs; ++k) {
@@ -124,8 +126,8 @@ struct Acc {
       const unsigned long long c2 = (c1 && w1 == 0ull) ? 1ull : 0ull;
       w2 = ~w2 + c2;
     }
-    const double v = ldexp((double)w2, 128 + sc) + (ldexp((double)w1, 64 + sc) + ldexp((double)w0, sc));
-    return neg ? -v : v;
+    if (w2 != 0ull) return crt_to_double(w2, w1 | (w0 != 0ull ? 1ull : 0ull), neg, 64 + sc);
+    return crt_to_double(w1, w0, neg, sc);
   }
 };
 

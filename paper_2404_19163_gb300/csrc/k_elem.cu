@@ -148,19 +148,16 @@ __global__ void k_f32_to_f64(const float* __restrict__ src, int n, int ld32, dou
   }
 }
 
-// max(m, x) that keeps a NaN (fmax drops it): a NaN anywhere makes the maximum NaN, whose bit
-// pattern then also wins the atomicMax below, so callers can test the result with isfinite.
-__device__ __forceinline__ double max_keep_nan(double m, double x) { return (x > m || x != x) ? x : m; }
-
+// max |A_ij| on the integer pipes (abs_bits): a NaN orders above every number, so a NaN anywhere
+// makes the maximum NaN and callers can test the result with isfinite.
 __global__ void k_amax_f64(const double* __restrict__ A, size_t total, IterState* st, int slot) {
-  double m = 0.0;
+  unsigned long long m = 0ull;
 #pragma unroll 4
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
-    m = max_keep_nan(m, fabs(A[e]));
+    m = max_bits(m, abs_bits(A[e]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max_keep_nan(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0)
-    atomicMax(reinterpret_cast<unsigned long long*>(&st->amax[slot]), (unsigned long long)__double_as_longlong(m));
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(&st->amax[slot]), m);
 }
 
 __device__ float pow2_for(double bound) {

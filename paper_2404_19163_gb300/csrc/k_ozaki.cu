@@ -20,13 +20,6 @@
 namespace zf {
 namespace {
 
-__device__ __forceinline__ int exp_bound(double v) {
-  // smallest-ish e with |v| <= 2^e (frexp: v = f 2^e, f in [0.5, 1))
-  int e;
-  frexp(v, &e);
-  return e;
-}
-
 // The same for T > 62 bits (more than ten 6-bit slices): a 128-bit fixed point.
 __device__ __forceinline__ __int128 fixed_point128(double x, int e, int T) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
@@ -92,16 +85,16 @@ __device__ __forceinline__ void slice_digits_offset(long long F, long long D, in
 // Column exponents of X (operand rows = columns of X): each block owns a stripe of 32 columns
 // and walks every row (coalesced), so no atomics are needed.
 __global__ void k_oz_colexp(const double* __restrict__ X, int n, int ld, int* __restrict__ e) {
-  __shared__ double red[8][33];
+  __shared__ unsigned long long red[8][33];
   const int j = blockIdx.x * 32 + threadIdx.x;
-  double m = 0.0;
+  unsigned long long m = 0ull;  // magnitude bit patterns: integer pipes only
   if (j < n)
-    for (int i = threadIdx.y; i < n; i += 8) m = fmax(m, fabs(X[(size_t)i * ld + j]));
+    for (int i = threadIdx.y; i < n; i += 8) m = max_bits(m, abs_bits(X[(size_t)i * ld + j]));
   red[threadIdx.y][threadIdx.x] = m;
   __syncthreads();
   if (threadIdx.y == 0 && j < n) {
-    for (int y = 1; y < 8; ++y) m = fmax(m, red[y][threadIdx.x]);
-    e[j] = m > 0.0 ? exp_bound(m) : -2000000000;
+    for (int y = 1; y < 8; ++y) m = max_bits(m, red[y][threadIdx.x]);
+    e[j] = m ? exp_of_bits(m) : -2000000000;
   }
 }
 
@@ -234,15 +227,15 @@ __global__ void k_oz_rowslice(const double* __restrict__ X, int n, int ld, int* 
   const double* xr = X + (size_t)row * ld;
   // vec: the row starts on 16 bytes (X aligned, ld even), so lanes take element pairs
   const int npair = vec ? n / 2 : 0;
-  double m = 0.0;
+  unsigned long long m = 0ull;  // magnitude bit patterns: integer pipes only
   for (int c = lane; c < npair; c += 32) {
     const double2 v = reinterpret_cast<const double2*>(xr)[c];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    m = max_bits(m, max_bits(abs_bits(v.x), abs_bits(v.y)));
   }
-  for (int c = 2 * npair + lane; c < n; c += 32) m = fmax(m, fabs(xr[c]));
+  for (int c = 2 * npair + lane; c < n; c += 32) m = max_bits(m, abs_bits(xr[c]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  const int er = m > 0.0 ? exp_bound(m) : -2000000000;
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int er = m ? exp_of_bits(m) : -2000000000;
   if (lane == 0) e[row] = er;
   const int T = s * b;
   const size_t stride = (size_t)Rp * ld16;
@@ -285,29 +278,29 @@ template <int NT, int PAIRS>
 __global__ void __launch_bounds__(NT) k_oz_rowslice_reg(const double* __restrict__ X, int n, int ld,
                                                        int* __restrict__ e, int s, int b, uint16_t* __restrict__ out,
                                                        int ld16, int Rp) {
-  __shared__ double red[NT / 32];
+  __shared__ unsigned long long red[NT / 32];
   const int row = blockIdx.x;
   const int tid = threadIdx.x;
   const double* xr = X + (size_t)row * ld;
   const int npair = n / 2;
   double2 v[PAIRS];
-  double m = 0.0;
+  unsigned long long m = 0ull;  // magnitude bit patterns: integer pipes only
 #pragma unroll
   for (int k = 0; k < PAIRS; ++k) {
     const int c = tid + NT * k;
     v[k] = c < npair ? reinterpret_cast<const double2*>(xr)[c] : make_double2(0.0, 0.0);
-    m = fmax(m, fmax(fabs(v[k].x), fabs(v[k].y)));
+    m = max_bits(m, max_bits(abs_bits(v[k].x), abs_bits(v[k].y)));
   }
   const double last = ((n & 1) && tid == 0) ? xr[n - 1] : 0.0;
-  m = fmax(m, fabs(last));
+  m = max_bits(m, abs_bits(last));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((tid & 31) == 0) red[tid >> 5] = m;
   __syncthreads();
   m = red[0];
 #pragma unroll
-  for (int w = 1; w < NT / 32; ++w) m = fmax(m, red[w]);
-  const int er = m > 0.0 ? exp_bound(m) : -2000000000;
+  for (int w = 1; w < NT / 32; ++w) m = max_bits(m, red[w]);
+  const int er = m ? exp_of_bits(m) : -2000000000;
   if (tid == 0) e[row] = er;
   const int T = s * b;
   const size_t stride = (size_t)Rp * ld16;

@@ -20,12 +20,6 @@ namespace zf {
 
 namespace {
 
-__device__ __forceinline__ int exp_bound_m(double v) {
-  int e;
-  frexp(v, &e);
-  return e;
-}
-
 // round(x 2^(T - e)) for |x| < 2^e and T <= 62, from the bits of x (integer operations only).
 __device__ __forceinline__ long long fixed_point_m(double x, int e, int T) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
@@ -86,34 +80,34 @@ __device__ __forceinline__ void parts_of(double x, int er, int T, float (&p)[5])
 template <int NT, int PAIRS>
 __global__ void __launch_bounds__(NT) k_ozm_rowres(const double* __restrict__ X, int n, int ld, int* __restrict__ e,
                                                   int T, int nmod, uint16_t* __restrict__ out, int ld16, int Rp) {
-  __shared__ double red[NT / 32];
+  __shared__ unsigned long long red[NT / 32];
   const int row = blockIdx.x;
   const int tid = threadIdx.x;
   const double* xr = X + (size_t)row * ld;
   const int npair = n / 2;
   constexpr int NREG = PAIRS > 0 ? PAIRS : 1;
   double v0[NREG], v1[NREG];
-  double m = 0.0;
+  unsigned long long m = 0ull;  // the row's largest magnitude, as a bit pattern (integer pipes)
   if (PAIRS > 0) {
 #pragma unroll
     for (int k = 0; k < NREG; ++k) {
       const int c = tid + NT * k;
       v0[k] = c < npair ? xr[2 * c] : 0.0;
       v1[k] = c < npair ? xr[2 * c + 1] : 0.0;
-      m = fmax(m, fmax(fabs(v0[k]), fabs(v1[k])));
+      m = max_bits(m, max_bits(abs_bits(v0[k]), abs_bits(v1[k])));
     }
   } else {
-    for (int c = tid; c < n; c += NT) m = fmax(m, fabs(xr[c]));
+    for (int c = tid; c < n; c += NT) m = max_bits(m, abs_bits(xr[c]));
   }
-  if (PAIRS > 0 && (n & 1) && tid == 0) m = fmax(m, fabs(xr[n - 1]));
+  if (PAIRS > 0 && (n & 1) && tid == 0) m = max_bits(m, abs_bits(xr[n - 1]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((tid & 31) == 0) red[tid >> 5] = m;
   __syncthreads();
   m = red[0];
 #pragma unroll
-  for (int w = 1; w < NT / 32; ++w) m = fmax(m, red[w]);
-  const int er = m > 0.0 ? exp_bound_m(m) : -2000000000;
+  for (int w = 1; w < NT / 32; ++w) m = max_bits(m, red[w]);
+  const int er = m ? exp_of_bits(m) : -2000000000;
   if (tid == 0) e[row] = er;
   const size_t stride = (size_t)Rp * ld16;
   uint16_t* orow = out + (size_t)row * ld16;
@@ -197,7 +191,7 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool active = !sym || bj + 127 >= bi;
   const int nmod = plan.nmod;
-  double ss = 0.0;
+  double ss_off = 0.0, ss_diag = 0.0;  // sums of d_ij^2 over j > i and j = i
   if (active) {
     const int j0 = bj + 4 * tx;
     int eb[4];
@@ -246,8 +240,14 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
         if (i < n && j < n) {
           if (ea > -1000 && eb[k] > -1000) v = acc[k].value(plan, ea + eb[k] - TA - TB);
           if (mode == 2) {
-            v = (i == j ? 1.0 : 0.0) - v;
-            if (j >= i) ss += (i == j ? 1.0 : 2.0) * v * v;
+            // d = I - C: a sign flip off the diagonal (no FP64 arithmetic), one subtraction on it
+            if (i == j) {
+              v = 1.0 - v;
+              ss_diag = fma(v, v, ss_diag);
+            } else {
+              v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+              if (j > i) ss_off = fma(v, v, ss_off);
+            }
           }
           if (!sym || j >= i) {
             double* o = out + (size_t)i * ld64 + j;
@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
     }
   }
   if (mode == 2) {
+    double ss = fma(2.0, ss_off, ss_diag);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if (tx == 0) red[ty] = ss;

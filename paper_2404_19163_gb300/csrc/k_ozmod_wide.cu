@@ -11,12 +11,6 @@
 namespace zf {
 namespace {
 
-__device__ __forceinline__ int exp_bound_w(double v) {
-  int e;
-  frexp(v, &e);
-  return e;
-}
-
 // round(x 2^(T - e)) for |x| < 2^e and T <= 83, as sign and 128-bit magnitude (hi, lo), from the
 // bits of x.  For a normal x the shift T - e + E is at most T - 53, so the magnitude stays below 2^84.
 __device__ __forceinline__ void parts_w(double x, int er, int T, float (&a)[crtw::kParts]) {
@@ -74,20 +68,20 @@ __device__ __forceinline__ void wres_one(const float (&p0)[crtw::kParts], int nm
 // Residues of the rows of X: one block of 256 threads per row, exponent pass then residue pass.
 __global__ void __launch_bounds__(256) k_ozmw_rowres(const double* __restrict__ X, int n, int ld, int* __restrict__ e,
                                                      int T, int nmod, uint16_t* __restrict__ out, int ld16, int Rp) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   const int row = blockIdx.x;
   const int tid = threadIdx.x;
   const double* xr = X + (size_t)row * ld;
-  double m = 0.0;
-  for (int c = tid; c < n; c += 256) m = fmax(m, fabs(xr[c]));
+  unsigned long long m = 0ull;  // the row's largest magnitude, as a bit pattern (integer pipes)
+  for (int c = tid; c < n; c += 256) m = max_bits(m, abs_bits(xr[c]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((tid & 31) == 0) red[tid >> 5] = m;
   __syncthreads();
   m = red[0];
 #pragma unroll
-  for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
-  const int er = m > 0.0 ? exp_bound_w(m) : -2000000000;
+  for (int w = 1; w < 8; ++w) m = max_bits(m, red[w]);
+  const int er = m ? exp_of_bits(m) : -2000000000;
   if (tid == 0) e[row] = er;
   const size_t stride = (size_t)Rp * ld16;
   uint16_t* orow = out + (size_t)row * ld16;

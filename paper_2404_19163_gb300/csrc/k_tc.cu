@@ -204,6 +204,25 @@ __device__ __forceinline__ void put16_t(uint16_t* base, int ld, int i, int col0,
   }
 }
 
+// Load 32 floats of a row starting at column col0 (16-byte vector loads when the whole chunk is
+// inside the row's n columns; entries j >= n read as 0).
+__device__ __forceinline__ void load32(const float* row, int col0, int n, float (&x)[32]) {
+  if (col0 + 32 <= n) {
+    const float4* src = reinterpret_cast<const float4*>(row + col0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 t = src[q];
+      x[4 * q] = t.x;
+      x[4 * q + 1] = t.y;
+      x[4 * q + 2] = t.z;
+      x[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) x[jj] = (col0 + jj < n) ? row[col0 + jj] : 0.0f;
+  }
+}
+
 // Store 32 bytes of row i starting at column col0 (entries j >= n, or j < i when `upper`, skipped).
 __device__ __forceinline__ void put8(uint8_t* base, int ld, int i, int col0, int n, bool upper, const uint32_t (&w)[8]) {
   const bool full = (col0 + 32 <= n) && (!upper || col0 >= i);
@@ -281,14 +300,12 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
       // r = c1 * f32_in + c2 * v: the running sum of c_k d^k.  Outputs: the running sum in
       // FP32 (f32), its 16-bit copy (o16, the final Q), and the raw power v (t16, P_k for
       // the next product of the chain), all at (i, j) and (j, i).
-      const float* drow = f32_in + (size_t)i * a.ld32;
       float r[32];
+      load32(f32_in + (size_t)i * a.ld32, col0, n, r);
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
-        const int j = col0 + jj;
-        const float d = (j < n) ? drow[j] : 0.0f;
         v[jj] *= us;
-        r[jj] = a.c1 * d + a.c2 * v[jj];
+        r[jj] = a.c1 * r[jj] + a.c2 * v[jj];
       }
       if (f32) put32(f32, a.ld32, i, col0, n, true, true, r);
       if (o16h) {
@@ -305,18 +322,15 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
     }
     case kEpiZupd: {
       float* zrow = f32 + (size_t)i * a.ld32;
+      float zo[32];
+      load32(zrow, col0, n, zo);
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
-        const int j = col0 + jj;
-        if (j < n) {
-          const float z = zrow[j] + v[jj] * us;
-          zrow[j] = z;
-          v[jj] = z;
-          amax = fmaxf(amax, fabsf(z));
-        } else {
-          v[jj] = 0.0f;
-        }
+        const float z = (col0 + jj < n) ? zo[jj] + v[jj] * us : 0.0f;
+        v[jj] = z;
+        amax = fmaxf(amax, fabsf(z));
       }
+      put32(zrow - (size_t)i * a.ld32, a.ld32, i, col0, n, false, false, v);
       split32(v, osc, a.bf16, lo, h, l);
       put16(o16h, a.ld16, i, col0, n, false, false, h);
       if (lo) put16(o16l, a.ld16, i, col0, n, false, false, l);

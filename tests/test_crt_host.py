@@ -1,6 +1,7 @@
 """Host arithmetic of the CRT residue products against exact integer products, compiled with the host
-C++ compiler (no GPU needed): the library's crt.h against 128-bit integers, and the wider crt_wide.h
-(up to 31 moduli, 84-bit rows) against Python's big integers."""
+C++ compiler (no GPU needed): the library's crt.h against 128-bit integers, the wider crt_wide.h
+(up to 31 moduli, 84-bit rows) against Python's big integers, and the integer-only conversion of a
+128-bit product to FP64 against Python's correctly rounded conversion of the exact rational."""
 import os
 import shutil
 import subprocess
@@ -80,3 +81,44 @@ def test_crt_wide_arithmetic_exact():
         assert abs(float(got) - want) <= 4 * 2.0 ** -53 * abs(want), (T, K, nmod, got, want)
     # the widest case needs all 31 moduli, the 20-modulus cases agree with crt.h's counts
     assert any(line.split()[2] == "31" for line in lines)
+
+
+def test_crt_to_double_correctly_rounded():
+    import random
+    import struct
+    from fractions import Fraction
+
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    rng = random.Random(7)
+    cases = []
+    for _ in range(20000):
+        bits = rng.randrange(1, 129)
+        x = rng.randrange(1 << (bits - 1), 1 << bits)
+        cases.append((rng.choice((-1, 1)), x, rng.randrange(-300, 300)))
+    # ties and near-ties around the rounding position, carries into a new binade, tiny and huge values
+    for k in (53, 54, 60, 64, 65, 100, 127):
+        base = (1 << k) - 1
+        cases += [(1, base, 0), (-1, base, -7), (1, (1 << k) + (1 << (k - 53)), 3),
+                  (1, (1 << k) + (1 << (k - 53)) + 1, 3), (1, (1 << k) + 3 * (1 << (k - 53)), -40)]
+    cases += [(1, 1, 0), (-1, 1, -1000), (1, 3, 1000), (1, (1 << 127) + 1, -200)]
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "crt_convert_check")
+        subprocess.run([cxx, "-O2", "-std=c++17", os.path.join(HERE, "native", "crt_convert_check.cpp"), "-o", exe],
+                       check=True)
+        inp = os.path.join(d, "cases.txt")
+        with open(inp, "w") as f:
+            for sg, x, sc in cases:
+                f.write("%d %d %d %d\n" % (sg, x >> 64, x & ((1 << 64) - 1), sc))
+        r = subprocess.run([exe, inp], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    got = [struct.unpack("<d", struct.pack("<Q", int(v)))[0] for v in r.stdout.split()]
+    assert len(got) == len(cases)
+    for (sg, x, sc), g in zip(cases, got):
+        want = float(sg * Fraction(x) * Fraction(2) ** sc)
+        lo = 2.0 ** -1022
+        if abs(want) >= lo or want == 0.0:
+            assert g == want, (sg, x, sc, g, want)
+        else:   # subnormal results: within one unit of the last place
+            assert abs(g - want) <= 2.0 ** -1074, (sg, x, sc, g, want)
