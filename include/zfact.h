@@ -260,13 +260,12 @@ int zfact_set_workspace_limit(zfact_ctx* ctx, int64_t bytes);
  *   ZFACT_EMU_AUTO (default): modular residues (Ozaki, Uchino, Imamura, "Ozaki Scheme II: A
  *     GEMM-oriented emulation of floating-point matrix multiplication using an integer modular
  *     technique", 2025): one BF16 tensor-core product per modulus (<= 127, pairwise coprime)
- *     and a Chinese-remainder reconstruction, wherever the bound N 2^(T_A + T_B) on the integer
- *     product fits the twenty moduli (product just below 2^127); error-free slices otherwise;
+ *     and a Chinese-remainder reconstruction.  Twenty moduli (product just below 2^127) where the
+ *     bound N 2^(T_A + T_B) on the integer product fits them, up to 31 (product just below 2^183,
+ *     rows of up to 83 bits: an ill-conditioned Z) where it does not; error-free slices beyond;
  *   ZFACT_EMU_SLICES: error-free slices always (the Ozaki et al. 2012 scheme above);
- *   ZFACT_EMU_WIDE: as ZFACT_EMU_AUTO, and where the twenty moduli do not fit, residues modulo up
- *     to 31 moduli (product just below 2^183, rows of up to 83 bits: an ill-conditioned Z) before
- *     falling back to slices.  Its arithmetic is checked on the host; it is not yet measured on a
- *     GPU, so it is not part of ZFACT_EMU_AUTO.
+ *   ZFACT_EMU_WIDE: the same as ZFACT_EMU_AUTO (kept for callers that asked for the wider moduli
+ *     before they were part of the default).
  * Other values return ZFACT_ERR_ARG.  No counterpart in the paper, which refines in FP64. */
 typedef enum zfact_emulation {
     ZFACT_EMU_AUTO = 0,

@@ -75,15 +75,14 @@ int oz_mod_count(const zfact_ctx* c, int TA, int TB, int n) {
   return crt_plan(TA + TB + log2((double)n) + 2.0, &p);
 }
 
-// The same with the wider moduli (only when the context asks for them), for rows of up to 83 bits.
+// The same with the wider moduli (unless the context asks for slices), for rows of up to 83 bits.
 int oz_mod_count_wide(const zfact_ctx* c, int TA, int TB, int n) {
-  if (c->oz_scheme != ZFACT_EMU_WIDE || TA < 1 || TB < 1 || TA > 83 || TB > 83) return 0;
+  if (c->oz_scheme == ZFACT_EMU_SLICES || TA < 1 || TB < 1 || TA > 83 || TB > 83) return 0;
   crtw::Plan p;
   return crtw::plan(TA + TB + log2((double)n) + 2.0, &p);
 }
 
-// Residues modulo the twenty moduli where they fit, else the wider ones where asked for (*wide = 1),
-// else 0 (slices).
+// Residues modulo the twenty moduli where they fit, else the wider ones (*wide = 1), else 0 (slices).
 int oz_mod_choice(const zfact_ctx* c, int TA, int TB, int n, int* wide) {
   *wide = 0;
   int k = oz_mod_count(c, TA, TB, n);

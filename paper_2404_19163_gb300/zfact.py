@@ -268,8 +268,8 @@ class Context:
         self._raise(self.lib.zfact_set_workspace_limit(self.h, int(nbytes)))
 
     def set_emulation(self, scheme: str = "auto"):
-        """zfact_set_emulation: "auto" (CRT residues where they fit, else slices), "slices", or "wide"
-        (as "auto", with up to 31 moduli before slices; not yet measured on a GPU)."""
+        """zfact_set_emulation: "auto" (CRT residues, twenty moduli or up to 31 where the rows need more
+        bits, else slices), "slices", or "wide" (the same as "auto")."""
         self._raise(self.lib.zfact_set_emulation(self.h, EMULATION[scheme] if isinstance(scheme, str) else int(scheme)))
 
     def selftest_timeout(self) -> int:
