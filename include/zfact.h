@@ -100,6 +100,10 @@ typedef struct zfact_opts {
     int fixed_iters;     /* > 0: exactly this many bulk updates, no stop test (parity mode) */
     int final_residual;  /* 1 (default): form ||I - Z^T S Z||_F of the returned Z in FP64 accuracy */
     int tile_cfg;        /* 0 = automatic; otherwise an index into the tuned tile table */
+    double start_scale;  /* Z0 = NULL only: > 0 starts from Z0 = start_scale I (a learned proposal,
+                            zfact_propose); 0 (default) from the Gershgorin scale I / sqrt(g_hi).  Either
+                            way the cold start's first residual d0 = I - s^2 S and first update
+                            s (I + Q0) need no products */
 } zfact_opts;
 
 typedef struct zfact_info {

@@ -88,7 +88,7 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
     rows += rup(n[i], 256);
   }
   for (int i = 0; i < count; ++i) {
-    nparts[i] = 4 * tiles_sq(n[i], true, 128);  // the larger of the two tile widths' counts
+    nparts[i] = kTcPartsPerTile * tiles_sq(n[i], true, 128);  // the larger of the two tile widths' counts
     part0[i] = parts;
     parts += nparts[i];
   }
@@ -143,7 +143,7 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
       const int i = order_idx[j];
       h_pre_ns[j + 1] = h_pre_ns[j] + tiles_sq(n[i], false, bnv);
       h_pre_s[j + 1] = h_pre_s[j] + tiles_sq(n[i], true, bnv);
-      h_nparts[i] = 4 * tiles_sq(n[i], true, bnv);  // partials the residual epilogue writes
+      h_nparts[i] = kTcPartsPerTile * tiles_sq(n[i], true, bnv);  // partials the residual epilogue writes
     }
   };
   auto it_tuned = tuned.find(sig);
@@ -434,22 +434,33 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
       if (!c->lane_stream[l] && cudaStreamCreateWithFlags(&c->lane_stream[l], cudaStreamNonBlocking) != cudaSuccess)
         return ctx_fail(c, ZFACT_ERR_CUDA, "lane stream");
     // every instance's slice count from its dynamic range, as in the single-instance refinement
-    unsigned long long* rng = (unsigned long long*)ctx_buf(c, "b.ranges", 16 * (size_t)count, &st);
+    // and the scaled row norms of S_i's rows and Z_i's columns, which set the moduli of its residue
+    // products (one read-back for all instances)
+    unsigned long long* rng = (unsigned long long*)ctx_buf(c, "b.ranges", 16 * (size_t)count + 8 * (size_t)count, &st);
     if (!rng) return st;
-    std::vector<unsigned long long> hr(2 * (size_t)count);
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
-                         return launch_b_ranges(t, count, max_n, rng, rng + count, c->stream);
+    unsigned int* rho2 = reinterpret_cast<unsigned int*>(rng + 2 * (size_t)count);
+    void* rscratch = ctx_buf(c, "b.rho_scratch", b_rho_scratch_bytes(rows), &st);
+    if (!rscratch) return st;
+    std::vector<unsigned long long> hr(3 * (size_t)count);
+    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 6, [&] {
+                         cudaError_t e = launch_b_ranges(t, count, max_n, rng, rng + count, c->stream);
+                         if (e == cudaSuccess) e = launch_b_rho(t, count, max_n, rows, rho2, rscratch, c->stream);
+                         return e;
                        }),
                        "batch ranges")))
       return st;
-    cudaMemcpyAsync(hr.data(), rng, 16 * (size_t)count, cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(hr.data(), rng, 24 * (size_t)count, cudaMemcpyDeviceToHost, c->stream);
     if ((st = ctx_cuda(c, cudaStreamSynchronize(c->stream), "ranges read-back"))) return st;
     std::vector<int> slices(count);
+    std::vector<double> rho_s(count), rho_z(count);
+    const unsigned int* hrho = reinterpret_cast<const unsigned int*>(hr.data() + 2 * (size_t)count);
     for (int i = 0; i < count; ++i) {
       double g, z;
       memcpy(&g, &hr[i], 8);
       memcpy(&z, &hr[count + i], 8);
       slices[i] = oz_slices_for(z, g);
+      rho_s[i] = oz_rho_from(hrho[i], n[i]);
+      rho_z[i] = oz_rho_from(hrho[count + i], n[i]);
     }
     cudaEvent_t fork = ev_get(c);
     cudaEvent_t join[zfact_ctx::kLanes];
@@ -467,8 +478,8 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
           c->lane = -1;
           return st;
         }
-        st = oz_prepare_S(c, S[i], n[i], slices[i]);
-        if (!st) st = oz_residual(c, Z[i], D64, n[i], l, 0, 0.0, 0);
+        st = oz_prepare_S(c, S[i], n[i], slices[i], rho_s[i]);
+        if (!st) st = oz_residual(c, Z[i], D64, n[i], l, 0, 0.0, 0, rho_z[i]);
         cudaEventRecord(join[l], c->lane_stream[l]);
         c->lane = -1;
         if (st) return st;

@@ -30,6 +30,12 @@ cudaError_t launch_b_gersh(const BatchTables& t, int count, int max_n, unsigned 
 // g_i (largest absolute row sum of S_i) and z_i (largest |Z_i|) as FP64 bits, for every instance.
 cudaError_t launch_b_ranges(const BatchTables& t, int count, int max_n, unsigned long long* gmax_bits,
                             unsigned long long* zmax_bits, cudaStream_t s);
+// Scaled row norms for the moduli of every instance's residue products (as launch_ozm_rho): rho2[i] over the
+// rows of S_i, rho2[count + i] over the columns of Z_i (FP32 bits of the largest squared norm).  rows: the
+// packed row count (instance i's columns at scratch offset row0[i]); scratch: b_rho_scratch_bytes(rows).
+cudaError_t launch_b_rho(const BatchTables& t, int count, int max_n, int rows, unsigned int* rho2, void* scratch,
+                         cudaStream_t s);
+size_t b_rho_scratch_bytes(int rows);
 cudaError_t launch_b_pack(const BatchTables& t, int count, int max_n, int mode, const unsigned long long* gmax_bits,
                           int ld, bool bf16, uint16_t* h16, uint16_t* l16, uint16_t* th16, uint16_t* tl16, float* m32,
                           cudaStream_t s);

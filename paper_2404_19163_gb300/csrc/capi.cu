@@ -152,6 +152,7 @@ extern "C" void zfact_default_opts(zfact_opts* o) {
   o->fixed_iters = 0;
   o->final_residual = 1;
   o->tile_cfg = 0;
+  o->start_scale = 0.0;
 }
 
 extern "C" int zfact_create(zfact_ctx** out, int device, void* stream) {
@@ -339,6 +340,11 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
     if ((st = ctx_cuda(c, klaunch(c, "gershgorin", 2.0 * n * n, 8.0 * n * n, 2,
                                   [&] { return launch_gershgorin(S, n, c->st_dev, c->stream); }),
                        "gershgorin")))
+      return st;
+    if (o.start_scale > 0.0 &&
+        (st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
+                                  [&] { return launch_set_gscale(c->st_dev, o.start_scale, c->stream); }),
+                       "start scale")))
       return st;
     if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 8.0 * n * n, 1,
                                   [&] { return launch_scaled_identity_f64(Za, n, c->st_dev, c->stream); }),

@@ -31,6 +31,7 @@ struct IterState {
   int error;              // kErr* bits raised by kernels (bounded waits, shape checks)
   int hist_len;           // entries of hist written
   int timeout_where;      // which wait gave up (diagnostics)
+  unsigned int rho2[4];   // largest squared scaled row norm of CRT operands (FP32 bits, launch_ozm_rho)
   int pad[3];
 };
 
@@ -54,6 +55,13 @@ __device__ __forceinline__ unsigned long long max_bits(unsigned long long a, uns
 __device__ __forceinline__ int exp_of_bits(unsigned long long b) {
   const int eb = (int)(b >> 52);
   return eb ? eb - 1022 : (63 - __clzll((long long)b)) - 1073;
+}
+// |x| 2^-e rounded toward zero to FP32, for the magnitude pattern b of x with |x| < 2^e (integer
+// operations on the bits); values below FP32's normal range read as zero.
+__device__ __forceinline__ float scaled_mag_f32(unsigned long long b, int e) {
+  const int eb = (int)(b >> 52), fe = eb - 1023 - e + 127;
+  if (eb == 0 || fe <= 0) return 0.0f;
+  return __uint_as_float(((unsigned)fe << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
 }
 
 // ---------------------------------------------------------------- mbarrier

@@ -53,6 +53,7 @@ struct zfact_ctx {
   int oz_T = 54;     // fixed-point bits per operand of the current residual products
   int oz_nmod = 0;   // > 0: those products use this many CRT residues instead of slices
   int oz_wide = 0;   // 1: those residues use the wider moduli of crt_wide.h
+  double oz_rho_s = -1.0;  // largest scaled row norm of S's rows (-1: unknown), see oz_prod_bits
   int oz_scheme = 0;  // zfact_emulation: 0 residues where they fit, 1 slices always, 2 also wide residues
   cudaStream_t lane_stream[kLanes] = {};
   int lane = -1;
@@ -108,9 +109,13 @@ int f64_update(zfact_ctx* c, const double* Z, const double* Q, double* Zn, int n
 
 // FP64-accurate products by error-free slicing (ozaki.cu)
 int oz_slices_for(double zmax, double g_hi);
-int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s = 0);
-int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop);
-int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax);
+// rho_s, rho_zt, rho_zr: scaled row norms of S's rows and Z's columns and rows (oz_rho_from; -1 when
+// unknown), which set the moduli of the CRT products (fewer where the rows are far from the worst case)
+int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s = 0, double rho_s = -1.0);
+int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop,
+                double rho_zt = -1.0);
+int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax, double rho_zr = -1.0);
+double oz_rho_from(unsigned int rho2_bits, int n);
 int oz_update_slices(int n, double q);
 int oz_update_bits(int n, double q);
 int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, int n);

@@ -57,6 +57,100 @@ __global__ void k_b_ranges(const BatchTables t, unsigned long long* gmax_bits, u
   }
 }
 
+// Scaled row norms of every instance for the moduli of its residue products (as launch_ozm_rho):
+// rho2[i] = max_r sum_c (S_i[r][c] 2^-e_r)^2, e_r the row's exponent bound, FP32 bits, atomic maximum;
+// +Inf for a row holding a NaN or Inf or whose largest entry is subnormal.  One warp per row (two passes
+// over the row: its maximum, then the scaled sum), grid.y = instance.
+__global__ void k_b_rowrho(const BatchTables t, unsigned int* rho2) {
+  const int i = blockIdx.y;
+  const int n = t.n[i];
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* S = t.S[i] + (size_t)row * n;
+  unsigned long long m = 0ull;
+  for (int c = lane; c < n; c += 32) m = max_bits(m, abs_bits(S[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (m == 0ull) return;
+  if (m >= 0x7FF0000000000000ull || m < (1ull << 52)) {
+    if (lane == 0) atomicMax(&rho2[i], 0x7F800000u);
+    return;
+  }
+  const int e = exp_of_bits(m);
+  float acc = 0.0f;
+  for (int c = lane; c < n; c += 32) {
+    const float f = scaled_mag_f32(abs_bits(S[c]), e);
+    acc = fmaf(f, f, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) atomicMax(&rho2[i], __float_as_uint(acc));
+}
+
+// The same for the columns of every Z_i (the rows of the residual's first operand Z_i^T): blocks of 32
+// columns x 256 rows (grid.z = instance), the column maxima and then the scaled sums accumulated with
+// atomics into cmax / csum at the instance's packed row offset, then the largest sum per instance.
+__global__ void k_b_colmax(const BatchTables t, unsigned long long* cmax) {
+  __shared__ unsigned long long red[8][33];
+  const int i = blockIdx.z, n = t.n[i];
+  const int j = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 256;
+  if (blockIdx.x * 32 >= n || r0 >= n) return;
+  const int r1 = r0 + 256 < n ? r0 + 256 : n;
+  const double* Z = t.Z[i];
+  unsigned long long m = 0ull;
+  if (j < n)
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) m = max_bits(m, abs_bits(Z[(size_t)r * n + j]));
+  red[threadIdx.y][threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < n) {
+    for (int y = 1; y < 8; ++y) m = max_bits(m, red[y][threadIdx.x]);
+    if (m) atomicMax(&cmax[t.row0[i] + j], m);
+  }
+}
+
+__device__ __forceinline__ bool b_no_bound(unsigned long long m) {
+  return m >= 0x7FF0000000000000ull || (m != 0ull && m < (1ull << 52));
+}
+
+__global__ void k_b_colsum(const BatchTables t, const unsigned long long* cmax, float* csum) {
+  __shared__ float red[8][33];
+  const int i = blockIdx.z, n = t.n[i];
+  const int j = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 256;
+  if (blockIdx.x * 32 >= n || r0 >= n) return;
+  const int r1 = r0 + 256 < n ? r0 + 256 : n;
+  const double* Z = t.Z[i];
+  const unsigned long long m = j < n ? cmax[t.row0[i] + j] : 0ull;
+  float acc = 0.0f;
+  if (m != 0ull && !b_no_bound(m)) {
+    const int e = exp_of_bits(m);
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) {
+      const float f = scaled_mag_f32(abs_bits(Z[(size_t)r * n + j]), e);
+      acc = fmaf(f, f, acc);
+    }
+  }
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && m != 0ull && !b_no_bound(m)) {
+    for (int y = 1; y < 8; ++y) acc += red[y][threadIdx.x];
+    atomicAdd(&csum[t.row0[i] + j], acc);
+  }
+}
+
+__global__ void k_b_colfin(const BatchTables t, const unsigned long long* cmax, const float* csum,
+                           unsigned int* rho2) {
+  const int i = blockIdx.y, n = t.n[i];
+  const int j = blockIdx.x * 256 + threadIdx.x;
+  unsigned u = 0u;
+  if (j < n) {
+    const unsigned long long m = cmax[t.row0[i] + j];
+    u = b_no_bound(m) ? 0x7F800000u : __float_as_uint(csum[t.row0[i] + j]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) u = max(u, __shfl_xor_sync(0xffffffffu, u, o));
+  if ((threadIdx.x & 31) == 0 && u) atomicMax(&rho2[i], u);
+}
+
 // Pack instance i (grid.z) into the stacked buffers, 32 x 32 tiles through shared memory:
 //   mode 0: S16 (hi[, lo]) from S_i
 //   mode 1: Z master (FP32) + Z16 and Zt16 (hi[, lo]) from Z0_i, or from s_i I when Z0_i is null
@@ -171,6 +265,24 @@ cudaError_t launch_b_ranges(const BatchTables& t, int count, int max_n, unsigned
   k_b_ranges<<<grid, 256, 0, s>>>(t, gmax_bits, zmax_bits);
   return cudaGetLastError();
 }
+
+cudaError_t launch_b_rho(const BatchTables& t, int count, int max_n, int rows, unsigned int* rho2,
+                        void* scratch, cudaStream_t s) {
+  // rho2[0..count): rows of S_i; rho2[count..2 count): columns of Z_i
+  unsigned long long* cmax = static_cast<unsigned long long*>(scratch);
+  float* csum = reinterpret_cast<float*>(cmax + rows);
+  cudaError_t e = cudaMemsetAsync(rho2, 0, sizeof(unsigned int) * 2 * (size_t)count, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, b_rho_scratch_bytes(rows), s);
+  if (e != cudaSuccess) return e;
+  k_b_rowrho<<<dim3((max_n + 7) / 8, count), 256, 0, s>>>(t, rho2);
+  const dim3 grid((max_n + 31) / 32, (max_n + 255) / 256, count), block(32, 8);
+  k_b_colmax<<<grid, block, 0, s>>>(t, cmax);
+  k_b_colsum<<<grid, block, 0, s>>>(t, cmax, csum);
+  k_b_colfin<<<dim3((max_n + 255) / 256, count), 256, 0, s>>>(t, cmax, csum, rho2 + count);
+  return cudaGetLastError();
+}
+
+size_t b_rho_scratch_bytes(int rows) { return (size_t)rows * (sizeof(unsigned long long) + sizeof(float)); }
 
 cudaError_t launch_b_pack(const BatchTables& t, int count, int max_n, int mode, const unsigned long long* gmax_bits,
                           int ld, bool bf16, uint16_t* h16, uint16_t* l16, uint16_t* th16, uint16_t* tl16, float* m32,

@@ -25,6 +25,7 @@ __global__ void k_rowabs_max(const double* __restrict__ S, int n, IterState* st)
 }
 
 __global__ void k_gscale(IterState* st) { st->gscale = 1.0 / sqrt(st->amax[0]); }
+__global__ void k_set_gscale(IterState* st, double s) { st->gscale = s; }
 
 __global__ void k_scaled_identity_f64(double* Z, int n, const IterState* st) {
   const size_t total = (size_t)n * n;
@@ -376,6 +377,11 @@ cudaError_t launch_gershgorin(const double* S, int n, IterState* st, cudaStream_
   const int warps_per_block = 8;
   k_rowabs_max<<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(S, n, st);
   k_gscale<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_gscale(IterState* st, double scale, cudaStream_t s) {
+  k_set_gscale<<<1, 1, 0, s>>>(st, scale);
   return cudaGetLastError();
 }
 

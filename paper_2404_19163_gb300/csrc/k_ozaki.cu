@@ -82,19 +82,65 @@ __device__ __forceinline__ void slice_digits_offset(long long F, long long D, in
   }
 }
 
-// Column exponents of X (operand rows = columns of X): each block owns a stripe of 32 columns
-// and walks every row (coalesced), so no atomics are needed.
-__global__ void k_oz_colexp(const double* __restrict__ X, int n, int ld, int* __restrict__ e) {
+// Column statistics of X (operand rows = columns of X) in three light passes over a 2-D grid (32 columns
+// x 256 rows per block, so that every SM has work): the columns' largest magnitudes (bit patterns,
+// integer pipes, atomic maximum per column), optionally the sums of (x 2^-e_j)^2 in FP32 (atomic add per
+// column), then e_j and the largest sum.  cmax and csum start at zero.
+__global__ void k_oz_colmax(const double* __restrict__ X, int n, int ld, unsigned long long* __restrict__ cmax) {
   __shared__ unsigned long long red[8][33];
-  const int j = blockIdx.x * 32 + threadIdx.x;
-  unsigned long long m = 0ull;  // magnitude bit patterns: integer pipes only
+  const int j = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 256;
+  const int r1 = r0 + 256 < n ? r0 + 256 : n;
+  unsigned long long m = 0ull;
   if (j < n)
-    for (int i = threadIdx.y; i < n; i += 8) m = max_bits(m, abs_bits(X[(size_t)i * ld + j]));
+    for (int i = r0 + threadIdx.y; i < r1; i += 8) m = max_bits(m, abs_bits(X[(size_t)i * ld + j]));
   red[threadIdx.y][threadIdx.x] = m;
   __syncthreads();
   if (threadIdx.y == 0 && j < n) {
     for (int y = 1; y < 8; ++y) m = max_bits(m, red[y][threadIdx.x]);
+    if (m) atomicMax(&cmax[j], m);
+  }
+}
+
+__device__ __forceinline__ bool oz_no_bound(unsigned long long m) {
+  // NaN or Inf, or a largest entry that is subnormal (its scaled values would read as zero)
+  return m >= 0x7FF0000000000000ull || (m != 0ull && m < (1ull << 52));
+}
+
+__global__ void k_oz_colsum(const double* __restrict__ X, int n, int ld, const unsigned long long* __restrict__ cmax,
+                            float* __restrict__ csum) {
+  __shared__ float red[8][33];
+  const int j = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 256;
+  const int r1 = r0 + 256 < n ? r0 + 256 : n;
+  float acc = 0.0f;
+  const unsigned long long m = j < n ? cmax[j] : 0ull;
+  if (m != 0ull && !oz_no_bound(m)) {
+    const int e = exp_of_bits(m);
+    for (int i = r0 + threadIdx.y; i < r1; i += 8) {
+      const float f = scaled_mag_f32(abs_bits(X[(size_t)i * ld + j]), e);
+      acc = fmaf(f, f, acc);
+    }
+  }
+  red[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && m != 0ull && !oz_no_bound(m)) {
+    for (int y = 1; y < 8; ++y) acc += red[y][threadIdx.x];
+    atomicAdd(&csum[j], acc);
+  }
+}
+
+__global__ void k_oz_colfin(const unsigned long long* __restrict__ cmax, const float* __restrict__ csum, int n,
+                            int* __restrict__ e, unsigned int* __restrict__ rho2) {
+  const int j = blockIdx.x * 256 + threadIdx.x;
+  unsigned u = 0u;
+  if (j < n) {
+    const unsigned long long m = cmax[j];
     e[j] = m ? exp_of_bits(m) : -2000000000;
+    if (rho2) u = oz_no_bound(m) ? 0x7F800000u : __float_as_uint(csum[j]);
+  }
+  if (rho2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) u = max(u, __shfl_xor_sync(0xffffffffu, u, o));
+    if ((threadIdx.x & 31) == 0 && u) atomicMax(rho2, u);
   }
 }
 
@@ -530,17 +576,34 @@ cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_oz_exp(const double* X, int n, int ld, bool cols, int* e, cudaStream_t s) {
-  // column exponents only: row exponents are found by the row slicing kernel itself
-  if (!cols) return cudaSuccess;
-  k_oz_colexp<<<(n + 31) / 32, dim3(32, 8), 0, s>>>(X, n, ld, e);
+cudaError_t launch_oz_colstats(const double* X, int n, int ld, int* e, unsigned int* rho2, void* scratch,
+                               cudaStream_t s) {
+  if (n < 1 || !scratch) return cudaErrorInvalidValue;
+  unsigned long long* cmax = static_cast<unsigned long long*>(scratch);
+  float* csum = reinterpret_cast<float*>(cmax + n);
+  cudaError_t err = cudaMemsetAsync(scratch, 0, oz_colstats_scratch_bytes(n), s);
+  if (err != cudaSuccess) return err;
+  const dim3 grid((n + 31) / 32, (n + 255) / 256), block(32, 8);
+  k_oz_colmax<<<grid, block, 0, s>>>(X, n, ld, cmax);
+  if (rho2) k_oz_colsum<<<grid, block, 0, s>>>(X, n, ld, cmax, csum);
+  k_oz_colfin<<<(n + 255) / 256, 256, 0, s>>>(cmax, csum, n, e, rho2);
   return cudaGetLastError();
+}
+
+size_t oz_colstats_scratch_bytes(int n) { return (size_t)n * (sizeof(unsigned long long) + sizeof(float)); }
+
+cudaError_t launch_oz_exp(const double* X, int n, int ld, bool cols, int* e, void* scratch, cudaStream_t s) {
+  // column exponents only: row exponents are found by the row kernels themselves
+  if (!cols) return cudaSuccess;
+  return launch_oz_colstats(X, n, ld, e, nullptr, scratch, s);
 }
 
 cudaError_t launch_oz_slice(const double* X, int n, int ld, bool trans, const int* e, int sl, int b, uint16_t* out,
                             int ld16, int Rp, cudaStream_t s) {
-  for (int p = 0; p < sl; ++p)  // padding rows n..Rp-1 of every slice must read as zero
-    if (Rp > n) cudaMemsetAsync(out + ((size_t)p * Rp + n) * ld16, 0, sizeof(uint16_t) * (size_t)(Rp - n) * ld16, s);
+  // padding rows n..Rp-1 of every slice read as zero: one strided memset over all of them
+  if (Rp > n)
+    cudaMemset2DAsync(out + (size_t)n * ld16, sizeof(uint16_t) * (size_t)Rp * ld16, 0,
+                      sizeof(uint16_t) * (size_t)(Rp - n) * ld16, sl, s);
   if (trans) {
     if (sl * b <= 62 && (ld16 & 1) == 0) {
       dim3 grid((n + 31) / 32, (n + 63) / 64), block(32, 8);

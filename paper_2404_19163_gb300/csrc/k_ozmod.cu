@@ -290,13 +290,59 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
   }
 }
 
+// rho_r^2 = sum_k (x_rk 2^-e_r)^2 of every row r of X (e_r the row's exponent bound, as in the
+// residue kernels), and the largest of them as an FP32 bit pattern into *rho2 (atomic maximum:
+// non-negative floats order like their bit patterns).  A row holding a NaN or Inf, or whose
+// largest entry is subnormal, writes +Inf (no bound).
+// One block of 256 threads per row; the sum runs in FP32 (its error is bounded by the caller).
+__global__ void __launch_bounds__(256) k_ozm_rowrho(const double* __restrict__ X, int n, int ld,
+                                                    unsigned int* __restrict__ rho2) {
+  __shared__ unsigned long long redm[8];
+  __shared__ float reds[8];
+  const double* xr = X + (size_t)blockIdx.x * ld;
+  const int tid = threadIdx.x;
+  unsigned long long m = 0ull;
+  for (int c = tid; c < n; c += 256) m = max_bits(m, abs_bits(xr[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) redm[tid >> 5] = m;
+  __syncthreads();
+  m = redm[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = max_bits(m, redm[w]);
+  if (m == 0ull) return;
+  if (m >= 0x7FF0000000000000ull || m < (1ull << 52)) {
+    // NaN or Inf, or a row of subnormals (their scaled values would all read as zero): no bound
+    if (tid == 0) atomicMax(rho2, 0x7F800000u);
+    return;
+  }
+  const int e = exp_of_bits(m);
+  float acc = 0.0f;
+  for (int c = tid; c < n; c += 256) {
+    const float f = scaled_mag_f32(abs_bits(xr[c]), e);
+    acc = fmaf(f, f, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) reds[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += reds[w];
+    atomicMax(rho2, __float_as_uint(t));
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_ozm_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
                                 int ld16, int Rp, cudaStream_t s) {
   if (nmod < 1 || nmod > kCrtMax || T < 1 || T > 62) return cudaErrorInvalidValue;
-  for (int p = 0; p < nmod; ++p)  // padding rows n..Rp-1 of every plane read as zero
-    if (Rp > n) cudaMemsetAsync(out + ((size_t)p * Rp + n) * ld16, 0, sizeof(uint16_t) * (size_t)(Rp - n) * ld16, s);
+  // padding rows n..Rp-1 of every plane read as zero: one strided memset over all of them
+  if (Rp > n)
+    cudaMemset2DAsync(out + (size_t)n * ld16, sizeof(uint16_t) * (size_t)Rp * ld16, 0,
+                      sizeof(uint16_t) * (size_t)(Rp - n) * ld16, nmod, s);
   if (trans) {
     dim3 grid((n + 31) / 32, (n + 63) / 64), block(32, 8);
     k_ozm_tres<<<grid, block, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
@@ -305,6 +351,18 @@ cudaError_t launch_ozm_residues(const double* X, int n, int ld, bool trans, int*
   } else {
     k_ozm_rowres<256, 0><<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ozm_rho(const double* X, int n, int ld, bool cols, unsigned int* rho2, void* scratch,
+                           cudaStream_t s) {
+  if (n < 1) return cudaErrorInvalidValue;
+  if (cols) {
+    // column exponents land in the scratch too (after the statistics the passes need)
+    char* p = static_cast<char*>(scratch);
+    return launch_oz_colstats(X, n, ld, reinterpret_cast<int*>(p + oz_colstats_scratch_bytes(n)), rho2, p, s);
+  }
+  k_ozm_rowrho<<<n, 256, 0, s>>>(X, n, ld, rho2);
   return cudaGetLastError();
 }
 

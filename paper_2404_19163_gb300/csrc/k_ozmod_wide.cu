@@ -137,8 +137,10 @@ __global__ void k_ozmw_tres(const double* __restrict__ X, int n, int ld, const i
 cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
                                  int ld16, int Rp, cudaStream_t s) {
   if (nmod < 1 || nmod > crtw::kMax || T < 1 || T > 83) return cudaErrorInvalidValue;
-  for (int p = 0; p < nmod; ++p)  // padding rows n..Rp-1 of every plane read as zero
-    if (Rp > n) cudaMemsetAsync(out + ((size_t)p * Rp + n) * ld16, 0, sizeof(uint16_t) * (size_t)(Rp - n) * ld16, s);
+  // padding rows n..Rp-1 of every plane read as zero: one strided memset over all of them
+  if (Rp > n)
+    cudaMemset2DAsync(out + (size_t)n * ld16, sizeof(uint16_t) * (size_t)Rp * ld16, 0,
+                      sizeof(uint16_t) * (size_t)(Rp - n) * ld16, nmod, s);
   if (trans) {
     dim3 grid((n + 31) / 32, (n + 63) / 64), block(32, 8);
     k_ozmw_tres<<<grid, block, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);

@@ -4,9 +4,13 @@
 // streams K-blocks of the operands into a ring of shared-memory stages with
 // TMA (128-byte swizzle); one thread of warp 1 issues tcgen05.mma (kind::f16,
 // FP32 accumulation in tensor memory) and releases each stage with
-// tcgen05.commit; warps 2-5 read the accumulator back with tcgen05.ld and run
+// tcgen05.commit; warps 2-9 read the accumulator back with tcgen05.ld and run
 // the fused epilogue while the next tile accumulates in the other half of the
-// tensor memory (two accumulator buffers).
+// tensor memory (two accumulator buffers).  Two epilogue warps share each
+// 32-lane quadrant of the accumulator (a warp may only read its own quadrant),
+// one for each half of the tile's columns: the epilogue stores and conversions
+// of a tile then take no longer than its products.  Each epilogue is its own
+// instantiation of the kernel, so no epilogue pays for another's registers.
 //
 // A product may consist of up to four K-concatenated segments accumulated
 // into one accumulator: the split scheme (h)(h)+(h)(l)+(l)(h) of Sec. 3.2
@@ -24,7 +28,7 @@
 namespace zf {
 namespace {
 
-constexpr int BM = 128, BK = 64, UK = 16, NTHREADS = 192;
+constexpr int BM = 128, BK = 64, UK = 16, NEPI_WARPS = 8, NTHREADS = 64 + 32 * NEPI_WARPS;
 
 template <int BN>
 struct Cfg {
@@ -255,6 +259,7 @@ __device__ __forceinline__ void split32(const float (&x)[32], float sc, int bf16
   }
 }
 
+template <int EPI>
 __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, float (&v)[32], double& ss, float& amax,
                                           float osc, float us, int group, int n, int row0, const CrtDigitConst& cd) {
   // grouped problems are stacked along rows: shift every output/input base to the instance
@@ -269,7 +274,7 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
   if (i >= (a.ninst > 0 ? n : a.M)) return;
   const bool lo = a.split_out != 0;
   uint16_t h[32], l[32];
-  switch (a.epi) {
+  switch (EPI) {
     case kEpiStore16: {
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) v[jj] *= us;
@@ -279,17 +284,20 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
       break;
     }
     case kEpiResid: {
+      // the chunk's sum of squares in FP32 (32 terms: relative error below 2^-19), then one FP64 add:
+      // GB300's FP64 pipe would otherwise set the pace of this epilogue
+      float cs = 0.0f;
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int j = col0 + jj;
         const float d = (i == j ? 1.0f : 0.0f) - v[jj] * us;
         v[jj] = d;
         if (j < n && j >= i) {
-          const double dd = (double)d;
-          ss += (i == j ? 1.0 : 2.0) * dd * dd;
+          cs = fmaf(i == j ? d : 2.0f * d, d, cs);
           amax = fmaxf(amax, fabsf(d));
         }
       }
+      ss += (double)cs;
       put32(f32, a.ld32, i, col0, n, true, true, v);
       split32(v, osc, a.bf16, lo, h, l);
       put16(o16h, a.ld16, i, col0, n, true, true, h);
@@ -405,7 +413,7 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~(uintptr_t)1023);
 }
 
-template <int BN>
+template <int BN, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__ TcMaps maps, const TcArgs a) {
   using C = Cfg<BN>;
   extern __shared__ uint8_t smem_raw[];
@@ -428,7 +436,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
+      mbar_init(&tempty[b], NEPI_WARPS);
     }
     mbar_init(done_bar, 1);
     mbar_fence_init();
@@ -521,7 +529,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       mbar_wait(done_bar, 0, a.err_flag, 4);
     }
   } else {
-    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int q = warp & 3;                  // TMEM lane quadrant this warp may access
+    const int half = (warp - 2) / 4;         // which half of the tile's columns it handles
+    constexpr int CH = BN / 64;              // 32-column chunks per half
     int ui = 0;
     const float osc = a.out_scale ? *a.out_scale : 1.0f;
     float us = a.unscale;
@@ -541,30 +551,41 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       const int i = bm * BM + q * 32 + lane;
       double ss = 0.0;
       CrtDigitConst cd{1.0f, 1.0f, 0.0f};
-      if (a.epi == kEpiCrt8) {
+      if constexpr (EPI == kEpiCrt8) {
         cd.m = (float)crtw::modulus(pl.t);
         cd.inv = 1.0f / cd.m;
 #pragma unroll
         for (int t = 0; t < 32; ++t)
           if (t == pl.t) cd.w = a.crt_w[t];
       }
+      if constexpr (EPI == kEpiPoly || EPI == kEpiZupd) {
+        // the FP32 input row segments of this half (one 128-byte line per chunk) into L1 ahead of use
+        const float* src = (EPI == kEpiPoly) ? a.f32_in : a.f32;
+        if (src && i < (a.ninst > 0 ? pl.n : a.M)) {
+          const float* r = src + ((size_t)pl.row0 + i) * a.ld32 + (size_t)bn * BN + half * CH * 32;
+#pragma unroll
+          for (int c = 0; c < CH; ++c)
+            if (bn * BN + (half * CH + c) * 32 < pl.n) asm volatile("prefetch.global.L1 [%0];" ::"l"(r + c * 32));
+        }
+      }
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = half * CH; c < (half + 1) * CH; ++c) {
         float v[32];
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
         const int col0 = bn * BN + c * 32;
         if (a.sym && col0 + 31 < bm * BM) continue;  // chunk entirely below the diagonal block
-        epi_chunk(a, i, col0, v, ss, amax, osc, us, pl.group, pl.n, pl.row0, cd);
+        epi_chunk<EPI>(a, i, col0, v, ss, amax, osc, us, pl.group, pl.n, pl.row0, cd);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
-      if (a.epi == kEpiResid) {
-        // fixed-order warp reduction; one partial per (tile, quadrant), summed in order later
+      if constexpr (EPI == kEpiResid) {
+        // fixed-order warp reduction; one partial per (tile, quadrant, half), summed in order later
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        const size_t pidx = a.ninst > 0 ? (size_t)a.g_part0[pl.inst] + (size_t)pl.tile * 4 : (size_t)u * 4;
-        if (lane == 0) a.partials[pidx + q] = ss;
+        const size_t pidx = a.ninst > 0 ? (size_t)a.g_part0[pl.inst] + (size_t)pl.tile * kTcPartsPerTile
+                                        : (size_t)u * kTcPartsPerTile;
+        if (lane == 0) a.partials[pidx + half * 4 + q] = ss;
       }
     }
     if (a.amax_bits) {
@@ -617,26 +638,45 @@ int tc_make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, in
 
 int tc_num_units(const TcArgs& a, int bn) { return units_of(a, bn); }
 
-template <int BN>
+template <int BN, int EPI>
 static cudaError_t launch_bn(const TcArgs& a, const TcMaps& maps, int num_sms, cudaStream_t s) {
   static bool attr_set = false;
   using C = Cfg<BN>;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int units = units_of(a, BN);
   const int grid = units < num_sms ? units : num_sms;
   if (grid <= 0) return cudaSuccess;
-  k_tc_gemm<BN><<<grid, NTHREADS, C::SMEM, s>>>(maps, a);
+  k_tc_gemm<BN, EPI><<<grid, NTHREADS, C::SMEM, s>>>(maps, a);
   return cudaGetLastError();
+}
+
+template <int BN>
+static cudaError_t launch_epi(const TcArgs& a, const TcMaps& maps, int num_sms, cudaStream_t s) {
+  switch (a.epi) {
+    case kEpiStore16: return launch_bn<BN, kEpiStore16>(a, maps, num_sms, s);
+    case kEpiResid: return launch_bn<BN, kEpiResid>(a, maps, num_sms, s);
+    case kEpiPoly: return launch_bn<BN, kEpiPoly>(a, maps, num_sms, s);
+    case kEpiZupd: return launch_bn<BN, kEpiZupd>(a, maps, num_sms, s);
+    case kEpiF64: return launch_bn<BN, kEpiF64>(a, maps, num_sms, s);
+    case kEpiZupd64: return launch_bn<BN, kEpiZupd64>(a, maps, num_sms, s);
+    default: break;
+  }
+  // the emulation epilogues run on 256-wide tiles only
+  if constexpr (BN == 256) {
+    if (a.epi == kEpiG32) return launch_bn<BN, kEpiG32>(a, maps, num_sms, s);
+    if (a.epi == kEpiCrt8) return launch_bn<BN, kEpiCrt8>(a, maps, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tc_gemm(const TcArgs& a, const TcMaps& maps, int bn, int num_sms, cudaStream_t s) {
   if (a.oz_s <= 0 && (a.nseg < 1 || a.nseg > kTcMaxSeg)) return cudaErrorInvalidValue;
-  if (bn == 256) return launch_bn<256>(a, maps, num_sms, s);
-  if (bn == 128) return launch_bn<128>(a, maps, num_sms, s);
+  if (bn == 256) return launch_epi<256>(a, maps, num_sms, s);
+  if (bn == 128) return launch_epi<128>(a, maps, num_sms, s);
   return cudaErrorInvalidValue;
 }
 

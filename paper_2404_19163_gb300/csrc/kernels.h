@@ -49,6 +49,8 @@ cudaError_t launch_f32_gemm(const F32Gemm& g, cudaStream_t s);
 // ----------------------------------------------------------------- elementwise / reductions (k_elem.cu)
 // st->gscale = 1/sqrt(max_i sum_j |S_ij|) (st->amax[0] is used as scratch).
 cudaError_t launch_gershgorin(const double* S, int n, IterState* st, cudaStream_t s);
+// st->gscale = scale: the scale s of a cold start Z0 = s I chosen by the caller (zfact_opts.start_scale).
+cudaError_t launch_set_gscale(IterState* st, double scale, cudaStream_t s);
 // Z = st->gscale * I (FP64, N x N).
 cudaError_t launch_scaled_identity_f64(double* Z, int n, const IterState* st, cudaStream_t s);
 // Err = sqrt(sum of partials in a fixed order) -> st->hist[idx]; if check_stop, evaluate the stop
@@ -109,6 +111,13 @@ cudaError_t launch_ozm_combine8(const uint8_t* G, size_t gstride, int ld8, int n
                                 const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
                                 double* partials, cudaStream_t s);
 int ozm_combine_blocks(int n);
+// max_r rho_r^2 over the rows (cols = false) or columns (cols = true) of X, rho_r^2 = sum_k (x_rk 2^-e_r)^2
+// with e_r the exponent bound of the residue kernels, as an FP32 bit pattern: atomic maximum into
+// *rho2 (the caller zeroes it).  Summed in FP32: the result is below the exact value by at most
+// (n/8 + 40) 2^-23 of it.  +Inf when X holds a NaN or Inf, or a row whose largest entry is subnormal.
+// Columns need scratch of oz_colstats_scratch_bytes(n) + 4 n bytes (8-byte aligned).
+cudaError_t launch_ozm_rho(const double* X, int n, int ld, bool cols, unsigned int* rho2, void* scratch,
+                           cudaStream_t s);
 
 // Residues with the wider moduli of crt_wide.h (k_ozmod_wide.cu): rows of up to 83 bits, up to
 // crtw::kMax planes and moduli; and the reconstruction with the wider plan.
@@ -119,8 +128,13 @@ cudaError_t launch_ozmw_combine8(const uint8_t* G, size_t gstride, int ld8, int 
                                  bool sym, double* partials, cudaStream_t s);
 
 // ---- error-free slicing (k_ozaki.cu)
-// e[r] = exponent bounding row r (cols = false) or column r (cols = true) of X.
-cudaError_t launch_oz_exp(const double* X, int n, int ld, bool cols, int* e, cudaStream_t s);
+// e[r] = exponent bounding column r of X (cols = true; rows: nothing, the row kernels find their own).
+// scratch: oz_colstats_scratch_bytes(n) bytes of device memory, 8-byte aligned.
+cudaError_t launch_oz_exp(const double* X, int n, int ld, bool cols, int* e, void* scratch, cudaStream_t s);
+// The same column exponents, and with rho2 the largest rho_j^2 of the columns as launch_ozm_rho.
+cudaError_t launch_oz_colstats(const double* X, int n, int ld, int* e, unsigned int* rho2, void* scratch,
+                               cudaStream_t s);
+size_t oz_colstats_scratch_bytes(int n);
 // Integer slices (b bits each) of X's rows (trans = false) or columns (trans = true); slice p of
 // operand row r at out[(p * Rp + r) * ld16 + k]; rows n..Rp-1 of every slice are zeroed.
 cudaError_t launch_oz_slice(const double* X, int n, int ld, bool trans, const int* e, int sl, int b, uint16_t* out,

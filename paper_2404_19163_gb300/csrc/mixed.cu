@@ -213,21 +213,46 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
   Mat16 Dr, Pr;
   if ((st = alloc16(c, "D16r", n, ld, true, &Dr))) return st;
   if (order > 2 && (st = alloc16(c, "P16r", n, ld, true, &Pr))) return st;
-  // slice count from the dynamic range of Z and S (see oz_slices_for)
-  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 3, [&] {
+  // slice count from the dynamic range of Z and S (see oz_slices_for); the scaled row norms of S's rows
+  // and of Z's columns and rows, which set the moduli of the residue products
+  void* cs = ctx_buf(c, "oz.colstats", oz_colstats_scratch_bytes(n) + sizeof(int) * (size_t)n, &st);
+  if (!cs) return st;
+  auto z_norms = [&]() -> cudaError_t {
+    cudaError_t e = launch_ozm_rho(Z64, n, n, true, &c->st_dev->rho2[1], cs, c->stream);
+    if (e == cudaSuccess) e = launch_ozm_rho(Z64, n, n, false, &c->st_dev->rho2[2], nullptr, c->stream);
+    return e;
+  };
+  cudaMemsetAsync(c->st_dev->rho2, 0, sizeof(c->st_dev->rho2), c->stream);
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 5, [&] {
                        cudaError_t e = launch_gershgorin(S, n, c->st_dev, c->stream);
                        if (e == cudaSuccess) e = launch_amax_f64(Z64, n, c->st_dev, 2, c->stream);
+                       if (e == cudaSuccess) e = launch_ozm_rho(S, n, n, false, &c->st_dev->rho2[0], nullptr, c->stream);
+                       if (e == cudaSuccess) e = z_norms();
                        return e;
                      }),
                      "dynamic range")))
     return st;
   if ((st = ctx_read_state(c))) return st;
   const int s_res = oz_slices_for(c->st_host->amax[2], c->st_host->amax[0]);
-  if ((st = oz_prepare_S(c, S, n, s_res))) return st;
+  double rho_zt = oz_rho_from(c->st_host->rho2[1], n), rho_zr = oz_rho_from(c->st_host->rho2[2], n);
+  if ((st = oz_prepare_S(c, S, n, s_res, oz_rho_from(c->st_host->rho2[0], n)))) return st;
   int ridx = 0, idx = iters;
   for (int r = 0; r <= o.refine_steps; ++r) {
     ++idx;
-    if ((st = oz_residual(c, Z64, D64, n, idx, o.stop_rule, o.tol, 0))) return st;
+    if (r > 0) {
+      // Z changed in the update: the column norms again for this residual (a further update, rare,
+      // takes the bound for any rows)
+      cudaMemsetAsync(&c->st_dev->rho2[1], 0, sizeof(unsigned int), c->stream);
+      if ((st = ctx_cuda(c, klaunch(c, "oz_rho", 0, 16.0 * n * n, 3, [&] {
+                           return launch_ozm_rho(Z64, n, n, true, &c->st_dev->rho2[1], cs, c->stream);
+                         }),
+                         "Z norms")))
+        return st;
+      if ((st = ctx_read_state(c))) return st;
+      rho_zt = oz_rho_from(c->st_host->rho2[1], n);
+      rho_zr = -1.0;
+    }
+    if ((st = oz_residual(c, Z64, D64, n, idx, o.stop_rule, o.tol, 0, rho_zt))) return st;
     // max|d| comes back with Err: it scales d's 16-bit copy and bounds Q for the update's slices
     if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
                                   [&] { return launch_amax_f64(D64, n, c->st_dev, 1, c->stream); }),
@@ -295,7 +320,7 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
         Pprev = keep;
       }
     }
-    if ((st = oz_update(c, Z64, Q64, n, qmax))) return st;
+    if ((st = oz_update(c, Z64, Q64, n, qmax, rho_zr))) return st;
     ++ridx;
   }
   *ridx_out = ridx;
@@ -342,8 +367,9 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     if (!Q32) return st;
   }
   const int max_units = tc_num_units(tc_args(n, bf16), 128) + 16;
-  const size_t npart = 4 * (size_t)max_units > (size_t)cold_resid_blocks(n) ? 4 * (size_t)max_units
-                                                                          : (size_t)cold_resid_blocks(n);
+  const size_t npart = kTcPartsPerTile * (size_t)max_units > (size_t)cold_resid_blocks(n)
+                           ? kTcPartsPerTile * (size_t)max_units
+                           : (size_t)cold_resid_blocks(n);
   double* partials = (double*)ctx_buf(c, "tc_partials", sizeof(double) * npart, &st);
   if (!partials) return st;
   // cold start: the first polynomial also keeps Q0 in FP32 for the elementwise first update
@@ -361,8 +387,10 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
 
   // ---- set-up: 16-bit S (once), FP32 master Z and its 16-bit copies
   if (scaled) {
-    if ((st = elem("scales S", 5, [&] {
+    if ((st = elem("scales S", 5 + (cold && o.start_scale > 0.0 ? 1 : 0), [&] {
            cudaError_t e = launch_gershgorin(S, n, sd, c->stream);  // amax[0] = max row sum of |S|
+           // (which also resets the start scale: a caller's start_scale applies again)
+           if (e == cudaSuccess && cold && o.start_scale > 0.0) e = launch_set_gscale(sd, o.start_scale, c->stream);
            if (e == cudaSuccess) e = launch_amax_f64(S, n, sd, kSlotS, c->stream);
            if (e == cudaSuccess) e = launch_pow2_slot(sd, kSlotS, kSlotS, c->stream);
            if (e == cudaSuccess) e = launch_amax_f64(Za64, n, sd, 6, c->stream);
@@ -375,13 +403,19 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
          return launch_cvt16(S, n, n, S16.h, S16.l, ld, 1.0, sp(kSlotS), false, bf16, c->stream);
        })))
     return st;
-  if ((st = elem("Z master", 1, [&] { return launch_f64_to_f32(Za64, n, n, Zm, ld, c->stream); }))) return st;
-  if ((st = elem("Z16", 2, [&] {
-         cudaError_t e = launch_cvt16(Za64, n, n, Za.h, Za.l, ld, 1.0, sp(zc_slot), false, bf16, c->stream);
-         if (e == cudaSuccess) e = launch_cvt16(Za64, n, n, Zta.h, Zta.l, ld, 1.0, sp(zc_slot), true, bf16, c->stream);
-         return e;
-       })))
-    return st;
+  // FP32 master Z and its 16-bit copies from Z0.  A cold start reads neither: its first residual and
+  // first update are formed from S and s alone, and the update writes them (they are made from Z0 only
+  // if the bulk stops before its first update).
+  auto z0_copies = [&]() -> int {
+    int s2;
+    if ((s2 = elem("Z master", 1, [&] { return launch_f64_to_f32(Za64, n, n, Zm, ld, c->stream); }))) return s2;
+    return elem("Z16", 2, [&] {
+      cudaError_t e = launch_cvt16(Za64, n, n, Za.h, Za.l, ld, 1.0, sp(zc_slot), false, bf16, c->stream);
+      if (e == cudaSuccess) e = launch_cvt16(Za64, n, n, Zta.h, Zta.l, ld, 1.0, sp(zc_slot), true, bf16, c->stream);
+      return e;
+    });
+  };
+  if (!cold && (st = z0_copies())) return st;
 
   Mat16* Zc = &Za;
   Mat16* Ztc = &Zta;
@@ -420,7 +454,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     k2.sa_ptr = sp(zc_slot);
     k2.sb_ptr = sp(kSlotAt);
     if ((s2 = tc_product(c, k2, *Ztc, At, ld, bn))) return s2;
-    const int np = 4 * tc_num_units(k2, bn);
+    const int np = kTcPartsPerTile * tc_num_units(k2, bn);
     if ((s2 = ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
                          return launch_finish_err(partials, np, sd, idx, o.stop_rule, o.tol, n, check_stop, c->stream);
                        }),
@@ -511,6 +545,8 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   if (!(err0 < 1.0)) inf->warn = ZFACT_WARN_NONCONTRACTIVE;
   bool done = c->st_host->nonfinite || (o.fixed_iters <= 0 && o.stop_rule == 1 && err0 / sqrt((double)n) <= o.tol);
   const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.nmax;
+  // (the loop below runs no update exactly when this holds)
+  if (cold && !(!done && 0 < limit && 0 + 1 + o.refine_steps + 1 < kHistMax) && (st = z0_copies())) return st;
   int iters = 0;
   while (!done && iters < limit && iters + 1 + o.refine_steps + 1 < kHistMax) {
     const bool cold_update = cold && iters == 0;

@@ -19,7 +19,12 @@ constexpr int kOzBits = 6;             // bits per slice
 constexpr int kOzSlicesResid = 9;      // 54 bits: residual products of a well-scaled Z
 constexpr int kOzSlicesUpdateMin = 4;  // 24 bits: the least Z Q is formed with (see oz_update_slices)
 constexpr int kOzSlicesMax = 14;
-constexpr size_t kOzGBudget = (size_t)6 << 30;  // bytes of group partials (slices) or digits (CRT) per launch
+// Target bytes of group partials (slices) or digits (CRT) per launch: K-chunks are batched up to it.  One
+// K-chunk of every group or modulus is the least a launch holds, so a product may exceed it: the CRT digits
+// of one chunk take k N^2 bytes (up to 8.3 GB for 31 moduli at N = 16384), the FP32 partials of one slicing
+// chunk 4 s N^2 bytes (up to 15 GB for 14 slices at N = 16384); both fit GB300's HBM many times over, and a
+// workspace cap (zfact_set_workspace_limit) turns them into ZFACT_ERR_NOMEM before anything is allocated.
+constexpr size_t kOzGBudget = (size_t)6 << 30;
 
 struct OzOperand {
   uint16_t* sl = nullptr;
@@ -52,12 +57,14 @@ int oz_make(zfact_ctx* c, const char* name, const double* X, int n, int ldx, boo
               ne = lane_name(c, (std::string("oz.") + name + ".e").c_str());
   op->sl = (uint16_t*)ctx_buf(c, ns.c_str(), sizeof(uint16_t) * (size_t)s * Rp * ld16, &st);
   if (!op->sl) return st;
-  op->e = (int*)ctx_buf(c, ne.c_str(), sizeof(int) * (size_t)n, &st);
+  // the exponents, then the scratch of the column-statistics passes
+  const size_t e_bytes = (sizeof(int) * (size_t)n + 15) / 16 * 16;
+  op->e = (int*)ctx_buf(c, ne.c_str(), e_bytes + oz_colstats_scratch_bytes(n), &st);
   if (!op->e) return st;
   op->Rp = Rp;
   op->s = s;
   if ((st = ctx_cuda(c, klaunch(c, "oz_slice", 0, 8.0 * n * n * 2 + 2.0 * s * n * n, 2, [&] {
-                       cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, cur_stream(c));
+                       cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, (char*)op->e + e_bytes, cur_stream(c));
                        if (e != cudaSuccess) return e;
                        return launch_oz_slice(X, n, ldx, trans, op->e, s, kOzBits, op->sl, ld16, Rp, cur_stream(c));
                      }),
@@ -66,29 +73,48 @@ int oz_make(zfact_ctx* c, const char* name, const double* X, int n, int ldx, boo
   return ZFACT_OK;
 }
 
-// Residue count for the product of T_A- and T_B-bit operands over K = n terms: the integer
-// product is below n 2^(T_A + T_B), and M must exceed four times that.  0 = use slices (the
-// context asks for them, or the bound needs more than the twenty moduli give).
-int oz_mod_count(const zfact_ctx* c, int TA, int TB, int n) {
-  if (c->oz_scheme == ZFACT_EMU_SLICES || TA < 1 || TB < 1 || TA > 62 || TB > 62) return 0;
-  CrtPlan p;
-  return crt_plan(TA + TB + log2((double)n) + 2.0, &p);
+// Bits the moduli product must exceed for C' = F_A F_B^T of T_A- and T_B-bit operand rows with scaled row
+// norms at most rhoA, rhoB (rho_r = ||x_r||_2 2^-e_r < sqrt(K)): by Cauchy-Schwarz |C'_ij| <= ||f_i|| ||g_j||,
+// and rounding the rows to integers adds at most sqrt(K)/2 to each norm, so |C'| <= 2^(T_A + T_B) rA rB with
+// r = rho + sqrt(K) 2^(-T-1); M must exceed four times that.  Never more than the bound K 2^(T_A + T_B)
+// that holds for any rows (rho = sqrt(K)).
+double oz_prod_bits(int TA, int TB, double rhoA, double rhoB, int n) {
+  const double sq = sqrt((double)n);
+  const double worst = TA + TB + log2((double)n) + 2.0;
+  // an unknown (negative) or implausible norm takes the bound for any rows
+  if (!(rhoA >= 0.0 && rhoA <= sq)) rhoA = sq;
+  if (!(rhoB >= 0.0 && rhoB <= sq)) rhoB = sq;
+  const double ra = rhoA + sq * ldexp(1.0, -TA - 1), rb = rhoB + sq * ldexp(1.0, -TB - 1);
+  const double b = TA + TB + log2(ra * rb) + 2.0;
+  return b < worst ? b : worst;
 }
 
-// The same with the wider moduli (unless the context asks for slices), for rows of up to 83 bits.
-int oz_mod_count_wide(const zfact_ctx* c, int TA, int TB, int n) {
-  if (c->oz_scheme == ZFACT_EMU_SLICES || TA < 1 || TB < 1 || TA > 83 || TB > 83) return 0;
-  crtw::Plan p;
-  return crtw::plan(TA + TB + log2((double)n) + 2.0, &p);
-}
-
-// Residues modulo the twenty moduli where they fit, else the wider ones (*wide = 1), else 0 (slices).
-int oz_mod_choice(const zfact_ctx* c, int TA, int TB, int n, int* wide) {
+// Moduli for a product of `bits`: the twenty of crt.h where they suffice, else the wider ones
+// (*wide = 1), else 0 (the product needs slices).
+int oz_moduli_for(const zfact_ctx* c, int TA, int TB, double bits, int* wide) {
   *wide = 0;
-  int k = oz_mod_count(c, TA, TB, n);
-  if (k == 0 && (k = oz_mod_count_wide(c, TA, TB, n)) > 0) *wide = 1;
+  if (c->oz_scheme == ZFACT_EMU_SLICES || TA < 1 || TB < 1 || TA > 83 || TB > 83) return 0;
+  CrtPlan p;
+  int k = crt_plan(bits, &p);
+  if (k > 0) return k;
+  crtw::Plan wp;
+  k = crtw::plan(bits, &wp);
+  if (k > 0) *wide = 1;
   return k;
 }
+
+}  // namespace
+
+// rho from the FP32 pattern of max_r rho_r^2 that launch_ozm_rho wrote (an FP32 sum whose result lies at
+// most (n/8 + 40) 2^-23 below the exact one, enlarged here by twice that); -1 when there is no bound.
+double oz_rho_from(unsigned int rho2_bits, int n) {
+  float t;
+  memcpy(&t, &rho2_bits, sizeof(t));
+  if (!(t >= 0.0f) || isinf(t)) return -1.0;
+  return sqrt((double)t * (1.0 + (n / 8.0 + 40.0) * ldexp(1.0, -22)));
+}
+
+namespace {
 
 int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx, bool trans, int T, int nmod,
                 int wide, OzOperand* op) {
@@ -98,15 +124,20 @@ int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx,
               ne = lane_name(c, (std::string("oz.") + name + ".e").c_str());
   op->sl = (uint16_t*)ctx_buf(c, ns.c_str(), sizeof(uint16_t) * (size_t)nmod * Rp * ld16, &st);
   if (!op->sl) return st;
-  op->e = (int*)ctx_buf(c, ne.c_str(), sizeof(int) * (size_t)n, &st);
+  // the exponents, then the scratch of the column-statistics passes
+  const size_t e_bytes = (sizeof(int) * (size_t)n + 15) / 16 * 16;
+  op->e = (int*)ctx_buf(c, ne.c_str(), e_bytes + oz_colstats_scratch_bytes(n), &st);
   if (!op->e) return st;
   op->Rp = Rp;
   op->s = nmod;
   op->T = T;
   op->nmod = nmod;
+  // the twenty-moduli kernel holds rows of up to 62 bits; wider rows or more planes take the wide one
+  // (both write the same residues of the same fixed-point rows)
+  wide = (wide || T > 62 || nmod > kCrtMax) ? 1 : 0;
   op->wide = wide;
   if ((st = ctx_cuda(c, klaunch(c, wide ? "oz_residues.wide" : "oz_residues", 0, 8.0 * n * n + 2.0 * nmod * n * n, 2, [&] {
-                       cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, cur_stream(c));
+                       cudaError_t e = launch_oz_exp(X, n, ldx, trans, op->e, (char*)op->e + e_bytes, cur_stream(c));
                        if (e != cudaSuccess) return e;
                        if (wide)
                          return launch_ozmw_residues(X, n, ldx, trans, op->e, T, nmod, op->sl, ld16, Rp, cur_stream(c));
@@ -122,13 +153,20 @@ int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx,
 // digit of each entry (one byte), then the reconstruction from the digits.  A fused residual writes
 // *nparts Err partials.
 int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool sym, double* out, int ld64,
-                   int mode, double* partials = nullptr, bool* fused_resid = nullptr, int* nparts = nullptr) {
+                   int mode, double bits, double* partials = nullptr, bool* fused_resid = nullptr,
+                   int* nparts = nullptr) {
   int st = ZFACT_OK;
   CrtPlan plan;
   crtw::Plan wplan;
-  const double bits = A.T + B.T + log2((double)n) + 2.0;
-  const int k = A.wide ? crtw::plan(bits, &wplan) : crt_plan(bits, &plan);
-  if (k < 1 || k != A.nmod || k != B.nmod || A.wide != B.wide)
+  // the first k moduli whose product exceeds 2^bits: crt.h's twenty where they suffice, else the wider
+  // moduli (the same twenty first); the operands hold at least k residue planes
+  bool wide = false;
+  int k = crt_plan(bits, &plan);
+  if (k < 1) {
+    k = crtw::plan(bits, &wplan);
+    wide = true;
+  }
+  if (k < 1 || k > A.nmod || k > B.nmod)
     return ctx_fail(c, ZFACT_ERR_ARG, "residue operands do not match (%d, %d, %d moduli)", k, A.nmod, B.nmod);
   const int ld = ld16_of(n);
   const int kblocks = (n + 63) / 64;
@@ -159,7 +197,7 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
     a.d8 = G;
     a.ld32 = ld;
     a.g_stride = (size_t)n * ld;
-    for (int t = 0; t < k; ++t) a.crt_w[t] = A.wide ? wplan.fw[t] : plan.fw[t];
+    for (int t = 0; t < k; ++t) a.crt_w[t] = wide ? wplan.fw[t] : plan.fw[t];
     a.oz_s = k;
     a.oz_diag = 1;
     a.oz_nch = nch;
@@ -189,8 +227,8 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
     }
     // digits read (the upper triangle when sym), FP64 result written (read too when accumulating)
     const double cbytes = (1.0 * k * nch * n * (double)n + (md == 1 ? 16.0 : 8.0) * n * n) * (sym ? 0.5 : 1.0);
-    if ((st = ctx_cuda(c, klaunch(c, A.wide ? "oz_crt.wide" : "oz_crt", 0, cbytes, 1, [&] {
-                         if (A.wide)
+    if ((st = ctx_cuda(c, klaunch(c, wide ? "oz_crt.wide" : "oz_crt", 0, cbytes, 1, [&] {
+                         if (wide)
                            return launch_ozmw_combine8(G, (size_t)n * ld, ld, nch, wplan, A.e, B.e, A.T, B.T, n, out,
                                                        ld64, md, sym, partials, cur_stream(c));
                          return launch_ozm_combine8(G, (size_t)n * ld, ld, nch, plan, A.e, B.e, A.T, B.T, n, out, ld64,
@@ -203,10 +241,15 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
 }
 
 // out (mode 0: =, 1: +=) A B^T to FP64 accuracy, A and B given by their row slices.
+// bits: what the moduli product must exceed (residue operands; oz_prod_bits), <= 0 for the bound that holds
+// for any rows.
 int oz_product(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, bool sym, double* out, int ld64,
-               int mode, double* partials = nullptr, bool* fused_resid = nullptr, int* nparts = nullptr) {
-  if (A.nmod > 0 || B.nmod > 0)
-    return oz_product_mod(c, A, B, n, sym, out, ld64, mode, partials, fused_resid, nparts);
+               int mode, double* partials = nullptr, bool* fused_resid = nullptr, int* nparts = nullptr,
+               double bits = 0.0) {
+  if (A.nmod > 0 || B.nmod > 0) {
+    if (bits <= 0.0) bits = A.T + B.T + log2((double)n) + 2.0;
+    return oz_product_mod(c, A, B, n, sym, out, ld64, mode, bits, partials, fused_resid, nparts);
+  }
   if (nparts) *nparts = oz_combine_blocks(n);
   int st = ZFACT_OK;
   const int s = A.s < B.s ? A.s : B.s;
@@ -293,25 +336,32 @@ int oz_slices_for(double zmax, double g_hi) {
 
 // The residual's operands keep T = b s bits either way: as s slices, or as CRT residues of the
 // T-bit rows where the product bound fits the moduli (then c->oz_nmod > 0).
-int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s) {
+int oz_prepare_S(zfact_ctx* c, const double* S, int n, int s, double rho_s) {
   OzOperand op;
   c->oz_s = s > 0 ? s : kOzSlicesResid;
   c->oz_T = kOzBits * c->oz_s;
-  c->oz_nmod = oz_mod_choice(c, c->oz_T, c->oz_T, n, &c->oz_wide);
+  c->oz_rho_s = rho_s;
+  // S's residue planes serve Z^T S for any Z (rho_Z <= sqrt(N)) of this factorization
+  const double bits = oz_prod_bits(c->oz_T, c->oz_T, -1.0, rho_s, n);
+  c->oz_nmod = oz_moduli_for(c, c->oz_T, c->oz_T, bits, &c->oz_wide);
   if (c->oz_nmod > 0) return oz_make_mod(c, "S", S, n, n, false, c->oz_T, c->oz_nmod, c->oz_wide, &op);
   return oz_make(c, "S", S, n, n, false, c->oz_s, &op);
 }
 
 namespace {
 // An operand of the current residual products (slices or residues, as oz_prepare_S chose).
-int oz_make_resid(zfact_ctx* c, const char* name, const double* X, int n, bool trans, OzOperand* op) {
-  if (c->oz_nmod > 0) return oz_make_mod(c, name, X, n, n, trans, c->oz_T, c->oz_nmod, c->oz_wide, op);
+int oz_make_resid(zfact_ctx* c, const char* name, const double* X, int n, bool trans, OzOperand* op, int planes = 0,
+                  int wide = 0) {
+  if (c->oz_nmod > 0)
+    return oz_make_mod(c, name, X, n, n, trans, c->oz_T, planes > 0 ? planes : c->oz_nmod, planes > 0 ? wide : c->oz_wide,
+                       op);
   return oz_make(c, name, X, n, n, trans, c->oz_s, op);
 }
 }  // namespace
 
 // d = I - Z^T S Z to FP64 accuracy; Err -> hist[idx].  oz_prepare_S must have run for this S.
-int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop) {
+int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int rule, double tol, int check_stop,
+                double rho_zt) {
   int st = ZFACT_OK;
   OzOperand Sop, Zt, At;
   Sop.sl = (uint16_t*)ctx_buf(c, lane_name(c, "oz.S.sl").c_str(), 0, &st);
@@ -333,15 +383,40 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
       (double*)ctx_buf(c, lane_name(c, "oz.partials").c_str(),
                        sizeof(double) * (size_t)(nb_max > nb_sep ? nb_max : nb_sep), &st);
   if (!partials) return st;
+  // Moduli per product from the scaled row norms of its operands (oz_prod_bits): S's from oz_prepare_S,
+  // Z's columns from the caller, A's rows measured below (one read-back) when the context runs on its
+  // own stream; an unknown norm takes the bound for any rows.
+  const int T = c->oz_T;
+  double bits1 = 0.0, bits2 = 0.0;
+  int planes_zt = 0, wide_zt = 0;
+  if (c->oz_nmod > 0) {
+    bits1 = oz_prod_bits(T, T, rho_zt, c->oz_rho_s, n);
+    bits2 = oz_prod_bits(T, T, rho_zt, -1.0, n);
+    planes_zt = oz_moduli_for(c, T, T, bits1 > bits2 ? bits1 : bits2, &wide_zt);
+    if (planes_zt < 1) return ctx_fail(c, ZFACT_ERR_ARG, "no moduli for the residual products");
+  }
   // rows of Z^T = columns of Z
-  if ((st = oz_make_resid(c, "Zt", Z, n, true, &Zt))) return st;
+  if ((st = oz_make_resid(c, "Zt", Z, n, true, &Zt, planes_zt, wide_zt))) return st;
   // A^T = Z^T S  (S symmetric: B operand rows are rows of S)
-  if ((st = oz_product(c, Zt, Sop, n, false, A64, n, 0))) return st;
-  if ((st = oz_make_resid(c, "At", A64, n, false, &At))) return st;
+  if ((st = oz_product(c, Zt, Sop, n, false, A64, n, 0, nullptr, nullptr, nullptr, bits1))) return st;
+  int planes_at = 0, wide_at = 0;
+  if (c->oz_nmod > 0) {
+    if (c->lane < 0 && rho_zt >= 0.0) {
+      cudaMemsetAsync(&c->st_dev->rho2[3], 0, sizeof(unsigned int), c->stream);
+      if ((st = ctx_cuda(c, klaunch(c, "oz_rho", 0, 8.0 * n * n, 1,
+                                    [&] { return launch_ozm_rho(A64, n, n, false, &c->st_dev->rho2[3], nullptr, c->stream); }),
+                         "rho A")))
+        return st;
+      if ((st = ctx_read_state(c))) return st;
+      bits2 = oz_prod_bits(T, T, rho_zt, oz_rho_from(c->st_host->rho2[3], n), n);
+    }
+    planes_at = oz_moduli_for(c, T, T, bits2, &wide_at);
+  }
+  if ((st = oz_make_resid(c, "At", A64, n, false, &At, planes_at, wide_at))) return st;
   // X = Z^T A = Z^T (A^T)^T, symmetric tiles; d = I - X fused into the combine when possible
   bool fused = false;
   double* Xout = X64;
-  if ((st = oz_product(c, Zt, At, n, true, D, n, 0, partials, &fused, &nb_fused))) return st;
+  if ((st = oz_product(c, Zt, At, n, true, D, n, 0, partials, &fused, &nb_fused, bits2))) return st;
   if (!fused) {
     // several K-chunk batches: the combine accumulated X into D; form d = I - X from it
     if ((st = ctx_cuda(c, cudaMemcpyAsync(Xout, D, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, cur_stream(c)),
@@ -390,7 +465,7 @@ int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, i
   int st = ZFACT_OK;
   const int s = kOzSlicesResid, T = kOzBits * s;
   int wide = 0;
-  const int nm = oz_mod_choice(c, T, T, n, &wide);
+  const int nm = oz_moduli_for(c, T, T, oz_prod_bits(T, T, -1.0, -1.0, n), &wide);
   OzOperand Hop, Zt, At;
   double* A64 = (double*)ctx_buf(c, lane_name(c, "oz.At64").c_str(), sizeof(double) * (size_t)n * n, &st);
   if (!A64) return st;
@@ -406,18 +481,21 @@ int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, i
 }
 
 // Z <- Z + Z Q to FP64 accuracy (Q symmetric: B operand rows are rows of Q); qmax bounds |Q_ij|.
-int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax) {
+int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax, double rho_zr) {
   int st = ZFACT_OK;
   OzOperand Zr, Qr;
   if (qmax == 0.0) return ZFACT_OK;  // Q = 0: Z is unchanged
   if (qmax > 0.0 && isfinite(qmax)) {
-    // T = 53 + log2(4 sqrt(N) q) bits as below, kept exactly by CRT residues where they fit
+    // T = 53 + log2(4 sqrt(N) q) bits as below, kept exactly by CRT residues where they fit; the moduli
+    // from the scaled row norms of Z (the caller's, or unknown) and of any Q
     int wide = 0;
-    const int Tu = oz_update_bits(n, qmax), nm = oz_mod_choice(c, Tu, Tu, n, &wide);
+    const int Tu = oz_update_bits(n, qmax);
+    const double bits = oz_prod_bits(Tu, Tu, rho_zr, -1.0, n);
+    const int nm = oz_moduli_for(c, Tu, Tu, bits, &wide);
     if (nm > 0) {
       if ((st = oz_make_mod(c, "Zr", Z, n, n, false, Tu, nm, wide, &Zr))) return st;
       if ((st = oz_make_mod(c, "Qr", Q, n, n, false, Tu, nm, wide, &Qr))) return st;
-      return oz_product(c, Zr, Qr, n, false, Z, n, 1);
+      return oz_product(c, Zr, Qr, n, false, Z, n, 1, nullptr, nullptr, nullptr, bits);
     }
   }
   const int su = (qmax > 0.0 && isfinite(qmax)) ? oz_update_slices(n, qmax) : kOzSlicesMax;

@@ -116,12 +116,19 @@ extern "C" int zfact_residual(zfact_ctx* c, int mode, const double* S, const dou
     // slice count from the dynamic range of Z and S, as in the refinement
     if ((st = ctx_cuda(c, launch_gershgorin(S, n, c->st_dev, c->stream), "gershgorin"))) return st;
     if ((st = ctx_cuda(c, launch_amax_f64(Z, n, c->st_dev, 2, c->stream), "amax Z"))) return st;
+    // scaled row norms of S's rows and Z's columns: the moduli of the residue products
+    void* cs = ctx_buf(c, "oz.colstats", oz_colstats_scratch_bytes(n) + sizeof(int) * (size_t)n, &st);
+    if (!cs) return st;
+    if ((st = ctx_cuda(c, launch_ozm_rho(S, n, n, false, &c->st_dev->rho2[0], nullptr, c->stream), "rho S"))) return st;
+    if ((st = ctx_cuda(c, launch_ozm_rho(Z, n, n, true, &c->st_dev->rho2[1], cs, c->stream), "rho Z"))) return st;
     if ((st = ctx_read_state(c))) return st;
     // the fixed-point scaling takes row maxima, which would pass a NaN or Inf by as a finite value
     if (!isfinite(c->st_host->amax[0]) || !isfinite(c->st_host->amax[2]))
       return ctx_fail(c, ZFACT_ERR_NONFINITE, "S or Z holds a NaN or Inf");
-    if ((st = oz_prepare_S(c, S, n, oz_slices_for(c->st_host->amax[2], c->st_host->amax[0])))) return st;
-    if ((st = oz_residual(c, Z, Dw, n, 0, 0, 0.0, 0))) return st;
+    if ((st = oz_prepare_S(c, S, n, oz_slices_for(c->st_host->amax[2], c->st_host->amax[0]),
+                           oz_rho_from(c->st_host->rho2[0], n))))
+      return st;
+    if ((st = oz_residual(c, Z, Dw, n, 0, 0, 0.0, 0, oz_rho_from(c->st_host->rho2[1], n)))) return st;
   } else if ((st = f64_residual(c, S, Z, A64, Dw, n, 0, 0, 0.0, 0))) {
     return st;
   }

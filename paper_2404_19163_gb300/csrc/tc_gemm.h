@@ -9,6 +9,8 @@
 namespace zf {
 
 constexpr int kTcMaxSeg = 4;
+// Err partials the residual epilogue writes per output tile (one per TMEM lane quadrant and column half).
+constexpr int kTcPartsPerTile = 8;
 
 // Epilogue of a tensor-core product (acc = sum over segments of A_s B_s^T, FP32).
 // v = acc * unscale is the product in true units.
@@ -43,7 +45,7 @@ struct TcArgs {
   uint16_t* o16h; uint16_t* o16l; int ld16;
   uint16_t* t16h; uint16_t* t16l;  // kEpiZupd: transposed copy
   float c1, c2;
-  double* partials;             // kEpiResid: 4 per tile (one per TMEM lane quadrant)
+  double* partials;             // kEpiResid: kTcPartsPerTile per tile, in a fixed order
   unsigned int* amax_bits;      // kEpiResid: max |d| as FP32 bits; kEpiZupd: max |Z|
   int* err_flag;
   // Ozaki mode (oz_s > 0): operands are integer slices stacked along rows (slice p of A at

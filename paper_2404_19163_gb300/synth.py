@@ -207,22 +207,20 @@ def trajectory(count: int = 128, n_lo: int = 256, n_hi: int = 3072, frames: int 
 
 
 # ------------------------------------------------------------------ workload 5: proposal data
-def proposal_instance(k: int, n_lo: int = 128, n_hi: int = 4096, split: str = "train"):
-    """One training/held-out overlap matrix for the start-proposal network.
-    N is log-uniform in [n_lo, n_hi]; the conditioning is varied through the
-    lattice spacing and the exponent range (Gaussian-overlap models, cond
-    roughly 10 ... 1e6).  Returns S."""
+def proposal_sites(k: int, n_lo: int = 128, n_hi: int = 4096, split: str = "train"):
+    """Geometry of one training/held-out overlap matrix for the start-proposal network:
+    (centres (n, 3), exponents (n,) or None for unit exponents).  N is log-uniform in
+    [n_lo, n_hi]; the conditioning is varied through the lattice spacing and the exponent
+    range (Gaussian-overlap models, cond roughly 10 ... 1e6)."""
     g = rng(5, (0 if split == "train" else 1_000_000) + k)
     n_target = int(round(math.exp(g.uniform(math.log(n_lo), math.log(n_hi)))))
     kind = g.integers(0, 3)
     if kind == 0:      # single exponent, random cluster, spacing sets the conditioning
         dens = 1.0 / g.uniform(1.6, 3.0) ** 3
-        pos = cluster_sites(n_target, int(g.integers(1 << 30)), min_dist=1.0, density=dens, workload=5)
-        return gaussian_overlap(pos)
+        return cluster_sites(n_target, int(g.integers(1 << 30)), min_dist=1.0, density=dens, workload=5), None
     if kind == 1:      # jittered cubic block
         side = max(2, int(round(n_target ** (1.0 / 3.0))))
-        pos = cubic_sites(side, g.uniform(1.6, 3.0), 0.1, int(g.integers(1 << 30)), workload=5)
-        return gaussian_overlap(pos)
+        return cubic_sites(side, g.uniform(1.6, 3.0), 0.1, int(g.integers(1 << 30)), workload=5), None
     # multi-exponent fcc block (ill-conditioned end)
     nexp = int(g.integers(2, 5))
     lo, hi = 0.3, g.uniform(0.6, 1.5)
@@ -231,8 +229,19 @@ def proposal_instance(k: int, n_lo: int = 128, n_hi: int = 4096, split: str = "t
     cz = max(1, int(round(cells_total ** (1.0 / 3.0))))
     cells = (cz, cz, max(1, cells_total // (cz * cz)))
     pos = fcc_sites(cells, g.uniform(3.4, 6.0), 0.05, int(g.integers(1 << 30)), workload=5)
-    c, a = fcc_basis(pos, exps)
-    return gaussian_overlap(c, a)
+    return fcc_basis(pos, exps)
+
+
+def proposal_instance(k: int, n_lo: int = 128, n_hi: int = 4096, split: str = "train"):
+    """S of ``proposal_sites`` built on the host (NumPy)."""
+    pos, exps = proposal_sites(k, n_lo, n_hi, split)
+    return gaussian_overlap(pos, exps)
+
+
+def proposal_instance_torch(k: int, n_lo: int = 128, n_hi: int = 4096, split: str = "train", device="cuda"):
+    """S of ``proposal_sites`` built on a torch device (the same matrix up to rounding)."""
+    pos, exps = proposal_sites(k, n_lo, n_hi, split)
+    return gaussian_overlap_torch(pos, exps, device=device)
 
 
 # ------------------------------------------------------------------ the paper's own test matrix

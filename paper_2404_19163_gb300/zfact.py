@@ -45,7 +45,7 @@ class ZfactError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("nmax", ctypes.c_int), ("refine_steps", ctypes.c_int), ("refine_mode", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("tol", ctypes.c_double), ("fixed_iters", ctypes.c_int),
-                ("final_residual", ctypes.c_int), ("tile_cfg", ctypes.c_int)]
+                ("final_residual", ctypes.c_int), ("tile_cfg", ctypes.c_int), ("start_scale", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

@@ -201,3 +201,28 @@ def test_bounded_wait_times_out_and_context_survives(ctx):
     S, Q, lam = synth.householder_spd(128, seed=8)
     r = ctx.refine(dev(S), None, order=2, precision="bf16_split", tol=1e-12)
     assert r.status in (0, 100) and r.info["resid_f"] / math.sqrt(128) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "bf16_split", "fp16_split"])
+def test_start_scale_is_the_cold_start_with_that_scale(ctx, precision):
+    """zfact_opts.start_scale (a proposal's scale) starts from Z0 = s I on the cold-start path: FP64
+    against the oracle from the same explicit Z0; the mixed precisions start from Err_0 = ||I - s^2 S||_F
+    and converge to tol."""
+    S, Q, lam = synth.householder_spd(300, seed=11)
+    s0 = oracle.gershgorin_scale(S)
+    s = 1.3 * s0
+    if precision == "fp64":
+        Zo, ho, it = oracle.refine(S, np.eye(300) * s, m=2, nmax=50, fixed_iters=5)
+        r = ctx.refine(dev(S), None, order=2, precision="fp64", fixed_iters=5, start_scale=s)
+        assert rel(r.Z.cpu().numpy(), Zo) <= 1e-12
+        assert np.allclose(r.hist[:6], ho[:6], rtol=1e-9, atol=1e-14)
+        # start_scale = 0 is the Gershgorin default
+        r0 = ctx.refine(dev(S), None, order=2, precision="fp64", fixed_iters=3, start_scale=0.0)
+        r1 = ctx.refine(dev(S), None, order=2, precision="fp64", fixed_iters=3)
+        assert np.array_equal(r0.Z.cpu().numpy(), r1.Z.cpu().numpy())
+    else:
+        r = ctx.refine(dev(S), None, order=3, precision=precision, tol=1e-12, start_scale=s)
+        _, err = oracle.residual(S, r.Z.cpu().numpy())
+        assert err / math.sqrt(300) <= 1e-12
+        e0 = np.linalg.norm(np.eye(300) - s * s * S)
+        assert abs(r.hist[0] - e0) <= 1e-5 * e0

@@ -100,6 +100,38 @@ def test_residual_exact_on_scaled_integer_inputs(ctx, n):
     assert np.array_equal(D[:, cols].cpu().numpy(), np.eye(n)[:, cols] - X)
 
 
+@pytest.mark.parametrize("n", [700, 2100])
+def test_residual_exact_with_norm_bound_moduli(ctx, n):
+    """Rows far from the worst case: Z = 2^-10 (I + sparse integers), S an integer matrix with
+    64 on the diagonal and sparse small entries off it.  Every row's scaled 2-norm is about 1/2
+    (one dominant entry), so by Cauchy-Schwarz the integer products need about log2(N) bits fewer
+    than the bound N 2^(2T) that holds for any rows: 17 moduli instead of 19.  d must still equal
+    I - Z^T S Z bit for bit, and the tensor-core flops show how many moduli ran (k 2 N^3 for Z^T S,
+    k N^3 for the symmetric Z^T A)."""
+    import torch
+    g = np.random.default_rng(100 + n)
+    Zi = np.eye(n) * 1024.0
+    m = g.random((n, n)) < 0.02
+    Zi[m] += g.integers(-3, 4, m.sum())
+    A = np.where(g.random((n, n)) < 0.02, g.integers(-2, 3, (n, n)), 0).astype(np.float64)
+    S = A + A.T
+    np.fill_diagonal(S, 64.0)
+    X = Zi.T @ (S @ Zi)
+    assert np.abs(X).max() < 2.0 ** 40
+    d_exact = np.eye(n) - X * 2.0 ** -40
+    D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    ctx.set_profiling(True)
+    ctx.kernel_stats(reset=True)
+    ctx.residual(dev(S), dev(Zi * 2.0 ** -20), "ozaki", D=D)
+    stats = {k["name"]: k for k in ctx.kernel_stats()}
+    ctx.set_profiling(False)
+    assert np.array_equal(D.cpu().numpy(), d_exact)
+    if ctx.emu == "auto":
+        k = stats["tc_gemm.crt"]["flops"] / (3.0 * n ** 3)
+        assert stats["tc_gemm.crt"]["launches"] == 2 and abs(k - round(k)) < 1e-9, stats["tc_gemm.crt"]
+        assert round(k) == 17, k
+
+
 def test_ozaki_residual_unaligned_operand_bit_identical(ctx):
     """S at an 8-byte offset (no 16-byte loads): the same digits, so the same bits as aligned S."""
     import torch
