@@ -11,7 +11,8 @@ Workload (default): N = 4096 Gaussian overlap, s-type sites exp(-r^2/2) on a
 jittered 16^3 cubic lattice (spacing 2.5, jitter 0.1), cold start Z0 = I/sqrt(g_hi),
 m = 2, BF16 tensor-core bulk with FP32 accumulation in the paper's split scheme
 (h)(h)+(h)(l)+(l)(h) with BF16 hi/lo operands, then Algorithm 3's refinement with
-d and Z + Z Q formed to FP64 accuracy by error-free slicing on the tensor cores.
+d and Z + Z Q formed to FP64 accuracy on the tensor cores by modular (CRT) residue
+products (error-free slicing where the moduli do not reach).
 The single-instance path does not shard: with --gpus N every rank runs its own
 replica (weak scaling) and value = max-over-ranks time / factorizations done.
 """
@@ -36,7 +37,10 @@ TOL = 1e-12
 # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean over the captured launches), valid only while the kernel's source is
 # the one that was captured; otherwise the bench line reports traffic as null.
-TRAFFIC = {}
+TRAFFIC = {
+    "tc_gemm.crt": {"source": "paper_2404_19163_gb300/csrc/k_tc.cu", "sha1": "a2b7fe18a439605d7c30c322b36261ef8db2693b",
+                    "bytes_per_launch": 1.364e9},
+}
 FP64_ITERS_WORKLOAD2 = 4   # updates the FP64 recursion needs on workload 2 (counted by the FP64 GPU path
                            # and by the oracle's own stop rule on the same input)
 

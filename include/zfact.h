@@ -103,7 +103,10 @@ typedef struct zfact_opts {
     double start_scale;  /* Z0 = NULL only: > 0 starts from Z0 = start_scale I (a learned proposal,
                             zfact_propose); 0 (default) from the Gershgorin scale I / sqrt(g_hi).  Either
                             way the cold start's first residual d0 = I - s^2 S and first update
-                            s (I + Q0) need no products */
+                            s (I + Q0) need no products.  With the 16-bit precisions, a start_scale whose
+                            bulk ends with Err >= min(1/4, Err_0) (no contraction the refinement could
+                            finish) is dropped and the call starts again from the Gershgorin scale; the
+                            time of both counts in info->ms, the history is the second run's */
 } zfact_opts;
 
 typedef struct zfact_info {

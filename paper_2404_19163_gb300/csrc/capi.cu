@@ -403,6 +403,23 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
     Zcur = c->mixed_result;
   } else {
     st = mixed_refine(c, S, Zcur, Znext, n, order, precision, o, &iters, &ridx, &inf, Z0_in == nullptr);
+    if (st == kRetryGershgorin) {
+      // the caller's start scale did not contract: the Gershgorin start, as if start_scale were 0
+      o.start_scale = 0.0;
+      iters = ridx = 0;
+      memset(&inf, 0, sizeof(inf));
+      inf.resid_f = NAN;
+      cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
+      if ((st = ctx_cuda(c, klaunch(c, "gershgorin", 2.0 * n * n, 8.0 * n * n, 2,
+                                    [&] { return launch_gershgorin(S, n, c->st_dev, c->stream); }),
+                         "gershgorin")))
+        return st;
+      if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 8.0 * n * n, 1,
+                                    [&] { return launch_scaled_identity_f64(Zcur, n, c->st_dev, c->stream); }),
+                         "Z0")))
+        return st;
+      st = mixed_refine(c, S, Zcur, Znext, n, order, precision, o, &iters, &ridx, &inf, true);
+    }
     if (st) return st;
     Zcur = c->mixed_result;
   }

@@ -145,21 +145,21 @@ ZF_HD inline void crt_parts(long long F, float (&a)[5]) {
     a[k] = sg * (crt_bits_f(0x4B000000u | (unsigned)((u >> (14 * k)) & 0x3FFFu)) - 8388608.0f);
 }
 
-// Symmetric residue of F modulo m from its parts, in FP32: x = sum_k a_k (2^(14k) mod m) is an
-// integer below 2^22 (exact), x - m rint(x / m) is congruent to F, and the float quotient errs
-// by less than 0.04, so one fix-up brings it into [-(m-1)/2, (m-1)/2] (|r| <= 32 for m = 64).
+// Symmetric residue of F modulo m from its first NP parts (NP = 4 when |F| < 2^56), in FP32:
+// x = sum_k a_k (2^(14k) mod m) is an integer below 2^22 (exact), x - m rint(x / m) is congruent to F,
+// and the float quotient errs by less than 0.04, so |r| < 0.55 m.  A second reduction of the same kind
+// brings r into [-m/2, m/2]: r / m is then known to 2^-22, and no integer r lies that close to m/2
+// except r = m/2 itself (m = 64), whose tie rint takes to 0.  So |r| <= (m-1)/2, or 32 for m = 64.  The
+// second reduction keeps the fix-up on the FMA pipe (a compare-and-select would load the ALU pipe,
+// which the residue kernels already keep the busier).
+template <int NP = 5>
 ZF_HD inline float crt_residue_f(const float (&a)[5], int m) {
   const float fm = (float)m;
-  const float x = fmaf(a[4], (float)crt_pow2_sym(m, 56),
-                       fmaf(a[3], (float)crt_pow2_sym(m, 42),
-                            fmaf(a[2], (float)crt_pow2_sym(m, 28), fmaf(a[1], (float)crt_pow2_sym(m, 14), a[0]))));
-  float r = fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
-  const float h = (float)(m / 2);
-  if (r > h)
-    r -= fm;
-  else if (r < -h)
-    r += fm;
-  return r;
+  float x = fmaf(a[3], (float)crt_pow2_sym(m, 42),
+                 fmaf(a[2], (float)crt_pow2_sym(m, 28), fmaf(a[1], (float)crt_pow2_sym(m, 14), a[0])));
+  if (NP > 4) x = fmaf(a[4], (float)crt_pow2_sym(m, 56), x);
+  const float r = fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
+  return fmaf(-fm, crt_rint(r * (1.0f / fm)), r);
 }
 
 // x mod m for an integer-valued float |x| <= 2^24 and m >= 13, inv = FP32(1 / m): congruent, and

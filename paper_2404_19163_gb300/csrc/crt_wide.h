@@ -65,19 +65,15 @@ ZF_HD inline void parts(unsigned long long mag_hi, unsigned long long mag_lo, bo
 }
 
 // Symmetric residue of F modulo m from its six parts: x = sum_k a_k (2^(14k) mod m) stays below
-// 2^23 in magnitude (exact in FP32); the rest is crt_residue_f's reduction.
+// 2^23 in magnitude (exact in FP32); the rest is crt_residue_f's two reductions (the first leaves
+// |r| < 0.58 m for m >= 13, the second brings it into [-m/2, m/2]).
 ZF_HD inline float residue_f(const float (&a)[kParts], int m) {
   const float fm = (float)m;
   float x = a[kParts - 1] * (float)crt_pow2_sym(m, 14 * (kParts - 1));
   for (int k = kParts - 2; k >= 1; --k) x = fmaf(a[k], (float)crt_pow2_sym(m, 14 * k), x);
   x += a[0];
-  float r = fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
-  const float h = (float)(m / 2);
-  if (r > h)
-    r -= fm;
-  else if (r < -h)
-    r += fm;
-  return r;
+  const float r = fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
+  return fmaf(-fm, crt_rint(r * (1.0f / fm)), r);
 }
 
 struct Plan {

@@ -132,5 +132,8 @@ int single_refine(zfact_ctx* c, const double* S, double* Za64, int n, int order,
 // Mixed-precision driver (mixed.cu): bulk tensor-core iterations, then Algorithm 3's refinement.
 // cold: Za holds the Gershgorin start Z0 = s I (s in the device state's gscale), whose first residual
 // and first update need no product.
+// Returns kRetryGershgorin (before any refinement) when a caller's start_scale left the bulk without
+// contraction (see zfact_opts.start_scale); the caller then starts again from the Gershgorin scale.
+constexpr int kRetryGershgorin = -100;
 int mixed_refine(zfact_ctx* c, const double* S, double* Za, double* Zb, int n, int order, int precision,
                  const zfact_opts& o, int* iters, int* ridx, zfact_info* inf, bool cold = false);

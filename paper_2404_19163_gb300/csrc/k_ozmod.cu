@@ -47,25 +47,25 @@ __device__ __forceinline__ long long fixed_point_m(double x, int e, int T) {
 // The residues of an element pair for moduli I.. (compile-time moduli, FP32 arithmetic of
 // crt_residue_f), each pair packed as two BF16 into one 4-byte store (an integer |r| <= 63
 // has its low 16 FP32 bits zero, so the BF16 value is the upper half).
-template <int I>
+template <int I, int NP>
 __device__ __forceinline__ void residues_pair_all(const float (&p0)[5], const float (&p1)[5], int nmod, uint16_t* o,
                                                   size_t stride) {
   if constexpr (I < kCrtMax) {
     if (I < nmod) {
-      const float r0 = crt_residue_f(p0, crt_modulus(I)), r1 = crt_residue_f(p1, crt_modulus(I));
+      const float r0 = crt_residue_f<NP>(p0, crt_modulus(I)), r1 = crt_residue_f<NP>(p1, crt_modulus(I));
       *reinterpret_cast<unsigned*>(o + (size_t)I * stride) =
           __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
-      residues_pair_all<I + 1>(p0, p1, nmod, o, stride);
+      residues_pair_all<I + 1, NP>(p0, p1, nmod, o, stride);
     }
   }
 }
 
-template <int I>
+template <int I, int NP>
 __device__ __forceinline__ void residues_one_all(const float (&p0)[5], int nmod, uint16_t* o, size_t stride) {
   if constexpr (I < kCrtMax) {
     if (I < nmod) {
-      o[(size_t)I * stride] = (uint16_t)(__float_as_uint(crt_residue_f(p0, crt_modulus(I))) >> 16);
-      residues_one_all<I + 1>(p0, nmod, o, stride);
+      o[(size_t)I * stride] = (uint16_t)(__float_as_uint(crt_residue_f<NP>(p0, crt_modulus(I))) >> 16);
+      residues_one_all<I + 1, NP>(p0, nmod, o, stride);
     }
   }
 }
@@ -77,7 +77,7 @@ __device__ __forceinline__ void parts_of(double x, int er, int T, float (&p)[5])
 // Residues of the rows of X (operand rows = rows of X): one block of NT threads per row finds
 // the row's exponent and writes the nmod residue planes, two elements per 4-byte store.  With
 // PAIRS > 0 the row stays in registers (n <= 2 NT PAIRS); PAIRS = 0 reads it twice.
-template <int NT, int PAIRS>
+template <int NT, int PAIRS, int NP>
 __global__ void __launch_bounds__(NT) k_ozm_rowres(const double* __restrict__ X, int n, int ld, int* __restrict__ e,
                                                   int T, int nmod, uint16_t* __restrict__ out, int ld16, int Rp) {
   __shared__ unsigned long long red[NT / 32];
@@ -119,26 +119,27 @@ __global__ void __launch_bounds__(NT) k_ozm_rowres(const double* __restrict__ X,
       float p0[5], p1[5];
       parts_of(v0[k], er, T, p0);
       parts_of(v1[k], er, T, p1);
-      residues_pair_all<0>(p0, p1, nmod, orow + 2 * c, stride);
+      residues_pair_all<0, NP>(p0, p1, nmod, orow + 2 * c, stride);
     }
   } else {
     for (int c = tid; c < npair; c += NT) {
       float p0[5], p1[5];
       parts_of(xr[2 * c], er, T, p0);
       parts_of(xr[2 * c + 1], er, T, p1);
-      residues_pair_all<0>(p0, p1, nmod, orow + 2 * c, stride);
+      residues_pair_all<0, NP>(p0, p1, nmod, orow + 2 * c, stride);
     }
   }
   if ((n & 1) && tid == 0) {
     float p0[5];
     parts_of(xr[n - 1], er, T, p0);
-    residues_one_all<0>(p0, nmod, orow + (n - 1), stride);
+    residues_one_all<0, NP>(p0, nmod, orow + (n - 1), stride);
   }
 }
 
 // Residues of X^T (operand rows = columns of X; exponents from launch_oz_exp(cols = true)): a
 // 64 x 32 tile of X (rows bi.., columns bj..) through shared memory, even and odd rows apart so
 // the transposed reads are conflict-free; each thread forms two adjacent operand columns (X rows).
+template <int NP>
 __global__ void k_ozm_tres(const double* __restrict__ X, int n, int ld, const int* __restrict__ e, int T, int nmod,
                            uint16_t* __restrict__ out, int ld16, int Rp) {
   __shared__ double te[32][33], to[32][33];
@@ -164,9 +165,9 @@ __global__ void k_ozm_tres(const double* __restrict__ X, int n, int ld, const in
     parts_of(to[tx][r], er, T, p1);
     uint16_t* o = out + (size_t)row * ld16 + col;
     if (col + 1 < n)
-      residues_pair_all<0>(p0, p1, nmod, o, stride);
+      residues_pair_all<0, NP>(p0, p1, nmod, o, stride);
     else
-      residues_one_all<0>(p0, nmod, o, stride);
+      residues_one_all<0, NP>(p0, nmod, o, stride);
   }
 }
 
@@ -343,13 +344,24 @@ cudaError_t launch_ozm_residues(const double* X, int n, int ld, bool trans, int*
   if (Rp > n)
     cudaMemset2DAsync(out + (size_t)n * ld16, sizeof(uint16_t) * (size_t)Rp * ld16, 0,
                       sizeof(uint16_t) * (size_t)(Rp - n) * ld16, nmod, s);
+  // rows of at most 55 bits (|F| < 2^56) need only four 14-bit parts
+  const bool four = T <= 55;
   if (trans) {
     dim3 grid((n + 31) / 32, (n + 63) / 64), block(32, 8);
-    k_ozm_tres<<<grid, block, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
+    if (four)
+      k_ozm_tres<4><<<grid, block, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
+    else
+      k_ozm_tres<5><<<grid, block, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
   } else if (n <= 2 * 256 * 8) {
-    k_ozm_rowres<256, 8><<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
+    if (four)
+      k_ozm_rowres<256, 8, 4><<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
+    else
+      k_ozm_rowres<256, 8, 5><<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
   } else {
-    k_ozm_rowres<256, 0><<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
+    if (four)
+      k_ozm_rowres<256, 0, 4><<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
+    else
+      k_ozm_rowres<256, 0, 5><<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
   }
   return cudaGetLastError();
 }

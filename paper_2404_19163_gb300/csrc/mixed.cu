@@ -200,7 +200,7 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
   int st = ZFACT_OK;
   double coef[8];
   coef[0] = 1.0;
-  for (int k = 1; k <= order; ++k) coef[k] = coef[k - 1] * (2.0 * k - 1.0) / (2.0 * k);
+  for (int k = 1; k <= 5; ++k) coef[k] = coef[k - 1] * (2.0 * k - 1.0) / (2.0 * k);
   const int ld = round_up(n, 64);
   const int bn = pick_bn(n);
   const size_t nn = (size_t)n * n;
@@ -212,7 +212,8 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
   if (!P64) return st;
   Mat16 Dr, Pr;
   if ((st = alloc16(c, "D16r", n, ld, true, &Dr))) return st;
-  if (order > 2 && (st = alloc16(c, "P16r", n, ld, true, &Pr))) return st;
+  // (the update's order may exceed the bulk's under a tolerance, see below)
+  if ((order > 2 || o.tol > 0) && (st = alloc16(c, "P16r", n, ld, true, &Pr))) return st;
   // slice count from the dynamic range of Z and S (see oz_slices_for); the scaled row norms of S's rows
   // and of Z's columns and rows, which set the moduli of the residue products
   void* cs = ctx_buf(c, "oz.colstats", oz_colstats_scratch_bytes(n) + sizeof(int) * (size_t)n, &st);
@@ -263,10 +264,21 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
     inf->resid_f = err;
     if (c->st_host->nonfinite || r == o.refine_steps) break;
     if (o.tol > 0 && err / sqrt((double)n) <= o.tol) break;
+    // The polynomial of this update: with a tolerance, the lowest order m' >= 2 whose error term
+    // bound Err^(m'+1) (the next residual is at most that: its coefficients sum below one) is half the
+    // target (one update then suffices, and every further order costs a product), else the bulk's order.
+    int ord = order;
+    if (o.tol > 0) {
+      for (int mr = 2; mr <= 5; ++mr)
+        if (pow(err, mr + 1.0) <= 0.5 * o.tol * sqrt((double)n)) {
+          ord = mr;
+          break;
+        }
+    }
     // |Q_ij| <= sum_k c_k |(d^k)_ij| <= sum_k c_k N^(k-1) max|d|^k
     const double dmax = c->st_host->amax[1];
     double qmax = 0.0, dk = dmax;
-    for (int k = 1; k <= order; ++k, dk *= (double)n * dmax) qmax += coef[k] * dk;
+    for (int k = 1; k <= ord; ++k, dk *= (double)n * dmax) qmax += coef[k] * dk;
     // Q = c1 d + sum_{k>=2} c_k d^k: the linear term exact in FP64, the powers by FP16 hi/lo products
     if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
                                   [&] { return launch_pow2_slot(c->st_dev, 1, 0, c->stream); }),
@@ -279,7 +291,7 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
                        "d16")))
       return st;
     const double* Pprev = D64;
-    for (int k = 2; k <= order; ++k) {
+    for (int k = 2; k <= ord; ++k) {
       Mat16 A = Dr;
       if (k > 2) {
         // 16-bit hi/lo copy of the previous power with its own scale
@@ -310,7 +322,7 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
                          }),
                          "Q")))
         return st;
-      if (k < order) {
+      if (k < ord) {
         // keep the power for the next product (P64 is overwritten by it)
         double* keep = (double*)ctx_buf(c, "P64keep", sizeof(double) * nn, &st);
         if (!keep) return st;
@@ -590,6 +602,12 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     done = c->st_host->nonfinite || c->st_host->stop;
   }
   *iters_out = iters;
+  // A caller's start scale (a learned proposal) whose bulk did not bring Err below min(1/4, Err_0):
+  // the refinement could not repair it within its steps, so start again from the Gershgorin scale.
+  if (cold && o.start_scale > 0.0 && o.fixed_iters <= 0) {
+    const double last = c->st_host->hist[iters];
+    if (c->st_host->nonfinite || !(last < 0.25) || !(last < err0)) return kRetryGershgorin;
+  }
   if (c->st_host->nonfinite) {
     c->mixed_result = Za64;
     return ZFACT_OK;

@@ -143,6 +143,16 @@ int main() {
       printf("residue of %lld mod %d wrong: %d / %g\n", F, m, r, rf);
       return 1;
     }
+    // four parts for |F| < 2^56 (rows of up to 55 bits): the same residue
+    const long long F4 = F >> 7;
+    float p4[5];
+    crt_parts(F4, p4);
+    const int r4 = ref_sym_residue((unsigned long long)(F4 < 0 ? -F4 : F4), F4 < 0, m);
+    const float rf4 = crt_residue_f<4>(p4, m);
+    if ((F4 - (long long)rf4) % m != 0 || (F4 - r4) % m != 0 || fabsf(rf4) > (float)(m / 2) || rf4 != floorf(rf4)) {
+      printf("four-part residue of %lld mod %d wrong: %d / %g\n", F4, m, r4, rf4);
+      return 1;
+    }
   }
   for (int i = 0; i < crtw::kMax; ++i) {  // crt_fmod_sym over |x| <= 2^24, every modulus down to 13
     const int m = crtw::modulus(i);

@@ -226,3 +226,17 @@ def test_start_scale_is_the_cold_start_with_that_scale(ctx, precision):
         assert err / math.sqrt(300) <= 1e-12
         e0 = np.linalg.norm(np.eye(300) - s * s * S)
         assert abs(r.hist[0] - e0) <= 1e-5 * e0
+
+
+def test_start_scale_that_does_not_contract_falls_back(ctx):
+    """A start scale s = 3 / sqrt(lambda_max) puts the largest eigenvalue of X0 = s^2 S at 9, where the
+    iteration diverges: the bulk cannot contract, so the call starts again from the Gershgorin scale and
+    still meets tol.  The returned history is the second run's (Err_0 = ||I - s0^2 S||_F)."""
+    S, Q, lam = synth.householder_spd(300, seed=12)
+    s0 = oracle.gershgorin_scale(S)
+    r = ctx.refine(dev(S), None, order=2, precision="bf16_split", tol=1e-12, start_scale=3.0 / math.sqrt(lam.max()))
+    assert r.status in (0, 100)   # 100: the Gershgorin start's ||I - X0||_F is above 1 (a warning)
+    _, err = oracle.residual(S, r.Z.cpu().numpy())
+    assert err / math.sqrt(300) <= 1e-12
+    e0 = np.linalg.norm(np.eye(300) - s0 * s0 * S)
+    assert abs(r.hist[0] - e0) <= 1e-5 * e0
