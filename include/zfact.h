@@ -281,6 +281,16 @@ typedef enum zfact_emulation {
 } zfact_emulation;
 int zfact_set_emulation(zfact_ctx* ctx, int scheme);
 
+/* ---- device-driven bulk loop ----------------------------------------------------------
+ * With the 16-bit precisions, the Algorithm 2 updates after the first run as one CUDA graph: a
+ * while node whose body holds two updates (the second under an if node, the two swap Z's buffers),
+ * each ending in a one-thread kernel that applies the stop test on the device and sets the loop's
+ * condition; the host waits once for the whole loop instead of once per update.  Every path of the
+ * loop ends after nmax updates.  The graph is built on first use and kept per problem size, order,
+ * precision and workspace layout.  on = 0 runs every update from the host (the same kernels, the
+ * same results); the default is 1.  Not in the paper (a GB300 execution choice).  Returns ZFACT_OK. */
+int zfact_set_loop_graphs(zfact_ctx* ctx, int on);
+
 /* ---- bounded-wait self-test -----------------------------------------------------------
  * Launches one block whose mbarrier wait, the bounded wait every tensor-core kernel uses, can never
  * complete: nothing arrives at the barrier.  The wait gives up after a short poll limit, records

@@ -52,6 +52,7 @@ void* ctx_buf(zfact_ctx* c, const char* name, size_t bytes, int* status) {
     c->bufs.erase(it);
   }
   void* p = nullptr;
+  ++c->ws_gen;  // captured loop graphs hold workspace addresses
   cudaError_t e = cudaMalloc(&p, need);
   if (e != cudaSuccess) {
     *status = ctx_cuda(c, e, name);
@@ -199,6 +200,8 @@ extern "C" void zfact_destroy(zfact_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->loop_graph_cache) cudaGraphExecDestroy(kv.second.exec);
+  c->loop_graph_cache.clear();
   for (auto& kv : c->bufs) cudaFree(kv.second.ptr);
   c->bufs.clear();
   kstats_flush(c);
@@ -452,6 +455,12 @@ extern "C" int zfact_set_workspace_limit(zfact_ctx* c, int64_t bytes) {
   if (!c) return ZFACT_ERR_ARG;
   if (bytes < 0) return ctx_fail(c, ZFACT_ERR_ARG, "negative workspace limit");
   c->ws_limit = (size_t)bytes;
+  return ZFACT_OK;
+}
+
+extern "C" int zfact_set_loop_graphs(zfact_ctx* c, int on) {
+  if (!c) return ZFACT_ERR_ARG;
+  c->loop_graphs = on != 0;
   return ZFACT_OK;
 }
 

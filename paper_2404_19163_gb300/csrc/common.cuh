@@ -32,7 +32,9 @@ struct IterState {
   int hist_len;           // entries of hist written
   int timeout_where;      // which wait gave up (diagnostics)
   unsigned int rho2[4];   // largest squared scaled row norm of CRT operands (FP32 bits, launch_ozm_rho)
-  int pad[3];
+  int loop_iter;          // bulk updates done, when the device drives the loop (mixed.cu loop graph)
+  int loop_limit;         // ... and the count it may not reach
+  int pad[1];
 };
 
 // ---------------------------------------------------------------- small device helpers

@@ -61,6 +61,15 @@ struct zfact_ctx {
   size_t ws_bytes = 0;  // workspace bytes allocated now
   // encoded TMA descriptors keyed by (address, rows, cols, ld, box rows, type)
   std::map<std::string, CUtensorMap> map_cache;
+  // device-driven bulk loop (mixed.cu): instantiated graphs keyed by the loop's configuration and the
+  // workspace generation (bumped whenever a workspace buffer is allocated or moved)
+  struct LoopGraph {
+    cudaGraphExec_t exec;
+    int launches[2];  // kernels of the graph's first and second update
+  };
+  std::map<std::string, LoopGraph> loop_graph_cache;
+  bool loop_graphs = true;  // zfact_set_loop_graphs
+  unsigned long long ws_gen = 0;
   // batched mode
   std::map<std::string, int> batch_bn;  // autotuned tile width per set of sizes
   std::string batch_sig;                // layout of the packed buffers (zeroed on change)

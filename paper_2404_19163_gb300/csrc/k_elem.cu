@@ -49,6 +49,7 @@ __global__ void k_finish_err(const double* __restrict__ partials, int np, IterSt
   }
   if (threadIdx.x == 0) {
     const double err = sqrt(red[0]);
+    if (idx < 0) idx = st->loop_iter + 1;  // device-driven loop: the update this residual follows
     if (idx < kHistMax) st->hist[idx] = err;
     st->hist_len = idx + 1;
     if (!isfinite(err)) {
@@ -192,6 +193,7 @@ __device__ float pow2_head(double bound, int headroom_log2) {
 
 __global__ void k_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next) {
   if (op == 0) {
+    if (idx < 0) idx = st->loop_iter + 1;  // device-driven loop, as in k_finish_err
     const double ad = (double)__uint_as_float(st->amaxf[1]);
     const double err = (idx >= 0 && idx < kHistMax) ? st->hist[idx] : ad;
     st->scale[0] = pow2_head(ad, 0);
@@ -377,6 +379,35 @@ cudaError_t launch_gershgorin(const double* S, int n, IterState* st, cudaStream_
   const int warps_per_block = 8;
   k_rowabs_max<<<(n + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(S, n, st);
   k_gscale<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_loop_init(IterState* st, int iters, int limit) {
+  st->loop_iter = iters;
+  st->loop_limit = limit;
+}
+
+// One update of the device-driven bulk loop is done (its residual's Err is in the history): count it and
+// decide whether the loop goes on.  Every path ends the loop once loop_limit updates are done.
+__global__ void k_loop_cond(IterState* st, cudaGraphConditionalHandle loop, cudaGraphConditionalHandle next,
+                            int set_next) {
+  const int it = st->loop_iter + 1;
+  st->loop_iter = it;
+  const unsigned go = (!st->stop && !st->nonfinite && st->error == 0 && it < st->loop_limit) ? 1u : 0u;
+  cudaGraphSetConditional(loop, go);
+  if (set_next) cudaGraphSetConditional(next, go);
+}
+}  // namespace
+
+cudaError_t launch_loop_init(IterState* st, int iters, int limit, cudaStream_t s) {
+  k_loop_init<<<1, 1, 0, s>>>(st, iters, limit);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_cond(IterState* st, cudaGraphConditionalHandle loop, cudaGraphConditionalHandle next,
+                             bool set_next, cudaStream_t s) {
+  k_loop_cond<<<1, 1, 0, s>>>(st, loop, next, set_next ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -57,6 +57,13 @@ cudaError_t launch_scaled_identity_f64(double* Z, int n, const IterState* st, cu
 // rule against st->hist[idx-1] (rule 0: Algorithm 2 with guards; rule 1: Err/sqrt(N) <= tol).
 cudaError_t launch_finish_err(const double* partials, int nparts, IterState* st, int idx, int rule,
                               double tol, int n, int check_stop, cudaStream_t s);
+// Device-driven bulk loop (a CUDA graph with a while node): st->loop_iter = iters, st->loop_limit = limit;
+// then, after each update's residual (whose finish_err takes idx = -1, i.e. loop_iter + 1), count the update
+// and set the loop's condition (and `next`, the guard of the graph's second update, when set_next) to
+// "no stop, no error, fewer than loop_limit updates".
+cudaError_t launch_loop_init(IterState* st, int iters, int limit, cudaStream_t s);
+cudaError_t launch_loop_cond(IterState* st, cudaGraphConditionalHandle loop, cudaGraphConditionalHandle next,
+                             bool set_next, cudaStream_t s);
 
 // 16-bit operand copies of an FP64 matrix (Eq. splitStyle): x = FP32[scale * src_ij],
 // hi = R16(x), lo = R16(x - hi) (lo skipped when lo == nullptr), written at (i, j), or at

@@ -15,7 +15,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <string>
 #include <utility>
+#include <vector>
 
 #include "ctx.h"
 #include "kernels.h"
@@ -264,13 +266,14 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
     inf->resid_f = err;
     if (c->st_host->nonfinite || r == o.refine_steps) break;
     if (o.tol > 0 && err / sqrt((double)n) <= o.tol) break;
-    // The polynomial of this update: with a tolerance, the lowest order m' >= 2 whose error term
-    // bound Err^(m'+1) (the next residual is at most that: its coefficients sum below one) is half the
-    // target (one update then suffices, and every further order costs a product), else the bulk's order.
+    // The polynomial of this update: with a tolerance, the lowest order m' >= 2 whose error term, estimated
+    // as ||d^(m'+1)||_F ~ Err^(m'+1) / N^(m'/2) (the spectrum of d spread over N eigenvalues), is half the
+    // target; else the bulk's order.  Each order costs a product; an estimate that falls short costs one more
+    // refinement step, which the loop takes.
     int ord = order;
     if (o.tol > 0) {
       for (int mr = 2; mr <= 5; ++mr)
-        if (pow(err, mr + 1.0) <= 0.5 * o.tol * sqrt((double)n)) {
+        if (pow(err, mr + 1.0) / pow((double)n, 0.5 * mr) <= 0.5 * o.tol * sqrt((double)n)) {
           ord = mr;
           break;
         }
@@ -336,6 +339,110 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
     ++ridx;
   }
   *ridx_out = ridx;
+  return ZFACT_OK;
+}
+
+// ---- device-driven bulk loop (zfact_set_loop_graphs)
+// Graph: while (cond) { update(Z_c -> Z_n); cond kernel; if (cond) { update(Z_n -> Z_c); cond kernel } }.
+// `body(parity)` enqueues one update on the context's stream (parity 0: Z_c -> Z_n, 1: back); it is
+// captured, not run.  Every cond kernel counts the update and ends the loop at st->loop_limit updates.
+// Returns ZFACT_OK with lg->exec == nullptr when the graph cannot be built (the caller then stays on the
+// host loop).
+template <class F>
+static int loop_graph_build(zfact_ctx* c, F&& body, zfact_ctx::LoopGraph* lg) {
+  lg->exec = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle hw = 0, hi = 0;
+  cudaGraphNode_t wnode = nullptr, inode = nullptr;
+  cudaGraphNodeParams wp = {}, ip = {};
+  const bool prof = c->profiling;
+  const int l0 = c->launches;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    ok = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp) == cudaSuccess &&
+         cudaGraphConditionalHandleCreate(&hi, wp.conditional.phGraph_out[0], 0, cudaGraphCondAssignDefault) ==
+             cudaSuccess;
+  }
+  c->profiling = false;  // no per-launch events inside the graph
+  for (int part = 0; ok && part < 2; ++part) {
+    cudaGraph_t target = part == 0 ? wp.conditional.phGraph_out[0] : ip.conditional.phGraph_out[0];
+    const int lstart = c->launches;
+    if (cudaStreamBeginCaptureToGraph(c->stream, target, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess) {
+      ok = false;
+      break;
+    }
+    int s2 = body(part);
+    if (!s2)
+      s2 = ctx_cuda(c, launch_loop_cond(c->st_dev, hw, hi, part == 0, c->stream), "loop condition");
+    std::vector<cudaGraphNode_t> leaves;
+    if (!s2 && part == 0) {
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      if (cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess)
+        leaves.assign(deps, deps + nd);
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->stream, &captured);
+    if (s2) {  // nothing is allocated inside an update: a failure here is the capture's, not the math's
+      ok = false;
+      break;
+    }
+    if (ec != cudaSuccess || (part == 0 && leaves.empty())) {
+      ok = false;
+      break;
+    }
+    lg->launches[part] = c->launches - lstart + 1;
+    if (part == 0) {
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = hi;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      ok = cudaGraphAddNode(&inode, wp.conditional.phGraph_out[0], leaves.data(), nullptr, leaves.size(), &ip) ==
+           cudaSuccess;
+    }
+  }
+  c->profiling = prof;
+  c->launches = l0;
+  if (ok) ok = cudaGraphInstantiate(&lg->exec, g, 0) == cudaSuccess;
+  if (!ok) lg->exec = nullptr;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();  // a graph that could not be built leaves no error behind: the host loop runs instead
+  return ZFACT_OK;
+}
+
+// Runs the loop graph for `key` (built on first use) from update `iters` to at most `lim` updates, waits for
+// it, and returns the updates it did in *g_iters (-1: no graph, use the host loop).
+template <class F>
+static int loop_graph_run(zfact_ctx* c, const std::string& key, int iters, int lim, F&& body, int* g_iters) {
+  *g_iters = -1;
+  int st = ZFACT_OK;
+  auto it = c->loop_graph_cache.find(key);
+  if (it == c->loop_graph_cache.end()) {
+    zfact_ctx::LoopGraph lg{};
+    if ((st = loop_graph_build(c, body, &lg))) return st;
+    if (!lg.exec) return ZFACT_OK;
+    if (c->loop_graph_cache.size() >= 32) {
+      for (auto& kv : c->loop_graph_cache) cudaGraphExecDestroy(kv.second.exec);
+      c->loop_graph_cache.clear();
+    }
+    it = c->loop_graph_cache.emplace(key, lg).first;
+  }
+  if ((st = ctx_cuda(c, launch_loop_init(c->st_dev, iters, lim, c->stream), "loop init"))) return st;
+  if ((st = ctx_cuda(c, klaunch(c, "bulk_graph", 0, 0, 0,
+                                [&] { return cudaGraphLaunch(it->second.exec, c->stream); }),
+                     "bulk loop graph")))
+    return st;
+  if ((st = ctx_read_state(c))) return st;
+  const int g = c->st_host->loop_iter - iters;
+  c->launches += 1 + ((g + 1) / 2) * it->second.launches[0] + (g / 2) * it->second.launches[1];
+  *g_iters = g;
   return ZFACT_OK;
 }
 
@@ -434,8 +541,9 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   Mat16* Zn = &Zb;
   Mat16* Ztn = &Ztb;
 
-  // d = I - Z^T S Z from the current 16-bit Z; Err -> hist[idx]
-  auto residual = [&](int idx, int check_stop) -> int {
+  // d = I - Z^T S Z from the 16-bit Z^T copy ztc (scale slot zcs); Err -> hist[idx] (idx < 0: the device's
+  // loop counter + 1)
+  auto residual = [&](int idx, int check_stop, Mat16* ztc, int zcs) -> int {
     int s2;
     if (scaled && (s2 = elem("scale At", 1, [&] { return launch_fp16_scales(sd, 1, 0, 0.f, 0.f, 0, c->stream); })))
       return s2;
@@ -445,10 +553,10 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     k1.o16h = At.h;
     k1.o16l = At.l;
     k1.ld16 = ld;
-    k1.sa_ptr = sp(zc_slot);
+    k1.sa_ptr = sp(zcs);
     k1.sb_ptr = sp(kSlotS);
     k1.out_scale = sp(kSlotAt);
-    if ((s2 = tc_product(c, k1, *Ztc, S16, ld, bn))) return s2;
+    if ((s2 = tc_product(c, k1, *ztc, S16, ld, bn))) return s2;
     cudaMemsetAsync(&sd->amaxf[1], 0, sizeof(unsigned int), c->stream);
     TcArgs k2 = tc_args(n, bf16);
     k2.epi = kEpiResid;
@@ -463,9 +571,9 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     k2.ld16 = ld;
     k2.partials = partials;
     k2.amax_bits = &sd->amaxf[1];
-    k2.sa_ptr = sp(zc_slot);
+    k2.sa_ptr = sp(zcs);
     k2.sb_ptr = sp(kSlotAt);
-    if ((s2 = tc_product(c, k2, *Ztc, At, ld, bn))) return s2;
+    if ((s2 = tc_product(c, k2, *ztc, At, ld, bn))) return s2;
     const int np = kTcPartsPerTile * tc_num_units(k2, bn);
     if ((s2 = ctx_cuda(c, klaunch(c, "finish_err", 0, 0, 1, [&] {
                          return launch_finish_err(partials, np, sd, idx, o.stop_rule, o.tol, n, check_stop, c->stream);
@@ -551,7 +659,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   };
 
   // ---- bulk phase (Algorithm 2)
-  if ((st = cold ? cold_residual() : residual(0, 0))) return st;
+  if ((st = cold ? cold_residual() : residual(0, 0, Ztc, zc_slot))) return st;
   if ((st = ctx_read_state(c))) return st;
   const double err0 = c->st_host->hist[0];
   if (!(err0 < 1.0)) inf->warn = ZFACT_WARN_NONCONTRACTIVE;
@@ -559,45 +667,78 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.nmax;
   // (the loop below runs no update exactly when this holds)
   if (cold && !(!done && 0 < limit && 0 + 1 + o.refine_steps + 1 < kHistMax) && (st = z0_copies())) return st;
-  int iters = 0;
-  while (!done && iters < limit && iters + 1 + o.refine_steps + 1 < kHistMax) {
-    const bool cold_update = cold && iters == 0;
-    if ((st = polynomial(cold_update ? Q0 : nullptr))) return st;
-    if (scaled && (st = elem("scale Z", 1, [&] {
-                     return launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zn_slot, c->stream);
-                   })))
-      return st;
+  // One bulk update Z_n = Z_c + Z_c Q (a cold start's first one elementwise: s (I + Q0)), then the residual
+  // of Z_n; idx < 0 takes the history index from the device (the graph-driven loop below).
+  auto update = [&](Mat16* zc, Mat16* zn, Mat16* ztn, int zcs, int zns, bool cold_update, int idx,
+                    int check) -> int {
+    int s2;
+    if ((s2 = polynomial(cold_update ? Q0 : nullptr))) return s2;
+    if (scaled && (s2 = elem("scale Z", 1, [&] { return launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zns, c->stream); })))
+      return s2;
     cudaMemsetAsync(&sd->amaxf[2], 0, sizeof(unsigned int), c->stream);
     if (cold_update) {
-      // Z1 = Z0 + Z0 Q0 = s (I + Q0): no product
-      if ((st = elem("cold update", 1, [&] {
-             return launch_cold_update(Q0, n, ld, sd, Zm, Zn->h, Zn->l, Ztn->h, Ztn->l, sp(zn_slot), bf16,
-                                       &sd->amaxf[2], c->stream);
+      if ((s2 = elem("cold update", 1, [&] {
+             return launch_cold_update(Q0, n, ld, sd, Zm, zn->h, zn->l, ztn->h, ztn->l, sp(zns), bf16, &sd->amaxf[2],
+                                       c->stream);
            })))
-        return st;
+        return s2;
+    } else {
+      TcArgs k4 = tc_args(n, bf16);
+      k4.epi = kEpiZupd;
+      k4.split_out = split;
+      k4.f32 = Zm;
+      k4.ld32 = ld;
+      k4.o16h = zn->h;
+      k4.o16l = zn->l;
+      k4.t16h = ztn->h;
+      k4.t16l = ztn->l;
+      k4.ld16 = ld;
+      k4.sa_ptr = sp(zcs);
+      k4.sb_ptr = sp(kSlotQ);
+      k4.out_scale = sp(zns);
+      k4.amax_bits = &sd->amaxf[2];
+      if ((s2 = tc_product(c, k4, *zc, Q16, ld, bn))) return s2;
     }
-    TcArgs k4 = tc_args(n, bf16);
-    k4.epi = kEpiZupd;
-    k4.split_out = split;
-    k4.f32 = Zm;
-    k4.ld32 = ld;
-    k4.o16h = Zn->h;
-    k4.o16l = Zn->l;
-    k4.t16h = Ztn->h;
-    k4.t16l = Ztn->l;
-    k4.ld16 = ld;
-    k4.sa_ptr = sp(zc_slot);
-    k4.sb_ptr = sp(kSlotQ);
-    k4.out_scale = sp(zn_slot);
-    k4.amax_bits = &sd->amaxf[2];
-    if (!cold_update && (st = tc_product(c, k4, *Zc, Q16, ld, bn))) return st;
-    if (scaled && (st = elem("amax Z", 1, [&] { return launch_fp16_scales(sd, 3, 0, 0.f, 0.f, 0, c->stream); })))
-      return st;
+    if (scaled && (s2 = elem("amax Z", 1, [&] { return launch_fp16_scales(sd, 3, 0, 0.f, 0.f, 0, c->stream); })))
+      return s2;
+    return residual(idx, check, ztn, zns);
+  };
+
+  int iters = 0;
+  const int lim = std::min(limit, kHistMax - o.refine_steps - 2);  // the loop's bound on updates
+  const int check = o.fixed_iters <= 0 ? 1 : 0;
+  while (!done && iters < lim) {
+    if (iters >= 1 && check && c->loop_graphs && c->lane < 0) {
+      // The rest of Algorithm 2 on the device: one CUDA graph whose while node runs two updates per
+      // pass (Z_c -> Z_n, then, guarded by an if node, Z_n -> Z_c) until the stop test fires or lim
+      // updates are done; no host round trip per update.
+      int g_iters = -1;
+      char key[256];
+      snprintf(key, sizeof(key), "%d:%d:%d:%d:%.17g:%p:%p:%d:%llu", n, order, precision, o.stop_rule, o.tol,
+               (void*)Zc->h, (const void*)S16.h, ld, (unsigned long long)c->ws_gen);
+      if ((st = loop_graph_run(c, key, iters, lim, [&](int parity) {
+             return parity == 0 ? update(Zc, Zn, Ztn, zc_slot, zn_slot, false, -1, 1)
+                                : update(Zn, Zc, Ztc, zn_slot, zc_slot, false, -1, 1);
+           }, &g_iters)))
+        return st;
+      if (g_iters < 0) {
+        c->loop_graphs = false;  // this device or driver cannot build it: the host loop from here on
+        continue;
+      }
+      if (g_iters & 1) {
+        std::swap(Zc, Zn);
+        std::swap(Ztc, Ztn);
+        std::swap(zc_slot, zn_slot);
+      }
+      iters += g_iters;
+      done = true;
+      break;
+    }
+    if ((st = update(Zc, Zn, Ztn, zc_slot, zn_slot, cold && iters == 0, iters + 1, check))) return st;
     std::swap(Zc, Zn);
     std::swap(Ztc, Ztn);
     std::swap(zc_slot, zn_slot);
     ++iters;
-    if ((st = residual(iters, o.fixed_iters <= 0 ? 1 : 0))) return st;
     if ((st = ctx_read_state(c))) return st;
     done = c->st_host->nonfinite || c->st_host->stop;
   }

@@ -10,8 +10,8 @@ the label is the (f, m) of least modelled time of the whole factorization to
     stop-test read-back:  ALPHA + BETA (m + 2) + (m + 4) N^3 C_BULK  per iteration, run to the
     Algorithm 2 stop;
   - refinement: from the bulk's last Err e, the FP64-accurate updates needed to reach tol
-    under e <- e^(m'+1) (m' the refinement's order: the lowest whose error term is at most half
-    the target, else m), each preceded by an FP64-accurate residual, plus the final residual:
+    under e <- e^(m'+1) / N^(m'/2) (m' the refinement's order: the lowest whose estimated error term
+    is at most half the target, else m), each preceded by an FP64-accurate residual, plus the final residual:
     T_RES0 + C_RES N^3 per residual and T_UPD0 + C_UPD N^3 per update (CRT residue products).
 The constants are GB300 measurements of the library's own kernels (bulk products and CRT
 refinement of the N = 4096 factorization; per-launch and read-back latencies of small N).
@@ -83,9 +83,10 @@ def work(hist, n, m, tau, tol=TOL, model=None):
     t = k * iter_time(n, m, model)
     e, target, updates = float(h[-1]), tol * math.sqrt(n), 0
     while e > target and updates < 4:
-        # the refinement's order: the lowest m' >= 2 with e^(m'+1) at most half the target, else m
-        mr = next((q for q in range(2, 6) if e ** (q + 1) <= 0.5 * target), m)
-        e = e ** (mr + 1)
+        # the refinement's order, as the library picks it: the lowest m' >= 2 whose estimated error term
+        # e^(m'+1) / N^(m'/2) is at most half the target, else m
+        mr = next((q for q in range(2, 6) if e ** (q + 1) / float(n) ** (0.5 * q) <= 0.5 * target), m)
+        e = e ** (mr + 1) / float(n) ** (0.5 * mr)
         updates += 1
     (r0, r1), (u0, u1) = model["res"], model["upd"]
     t += (updates + 1) * (r0 + r1 * n3) + updates * (u0 + u1 * n3)

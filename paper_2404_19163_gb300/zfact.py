@@ -32,7 +32,7 @@ EXPORTED = (
     "zfact_refine_batched", "zfact_features", "zfact_mlp_forward", "zfact_mlp_backward",
     "zfact_mlp_adam", "zfact_propose", "zfact_gemm", "zfact_split", "zfact_residual",
     "zfact_set_profiling", "zfact_kernel_stats", "zfact_residual_noalloc", "zfact_congruence",
-    "zfact_set_workspace_limit", "zfact_selftest_timeout", "zfact_set_emulation",
+    "zfact_set_workspace_limit", "zfact_selftest_timeout", "zfact_set_emulation", "zfact_set_loop_graphs",
 )
 
 
@@ -99,6 +99,7 @@ def load(path: Optional[str] = None):
     lib.zfact_set_workspace_limit.argtypes = [P, I64]
     lib.zfact_selftest_timeout.argtypes = [P]
     lib.zfact_set_emulation.argtypes = [P, I]
+    lib.zfact_set_loop_graphs.argtypes = [P, I]
     for name in EXPORTED:
         if getattr(lib, name).restype is ctypes.c_int or name in ("zfact_default_opts", "zfact_destroy",
                                                                       "zfact_last_error"):
@@ -266,6 +267,11 @@ class Context:
     def set_workspace_limit(self, nbytes: int = 0):
         """zfact_set_workspace_limit: cap the device workspace (0 = no cap)."""
         self._raise(self.lib.zfact_set_workspace_limit(self.h, int(nbytes)))
+
+    def set_loop_graphs(self, on: bool = True):
+        """zfact_set_loop_graphs: run the bulk's updates after the first as one device-driven CUDA graph
+        (default) or one by one from the host."""
+        self._raise(self.lib.zfact_set_loop_graphs(self.h, int(bool(on))))
 
     def set_emulation(self, scheme: str = "auto"):
         """zfact_set_emulation: "auto" (CRT residues, twenty moduli or up to 31 where the rows need more
