@@ -462,46 +462,53 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
       rho_s[i] = oz_rho_from(hrho[i], n[i]);
       rho_z[i] = oz_rho_from(hrho[count + i], n[i]);
     }
+    // Grouped launches over all instances where the batch allows (sizes within one residue chunk, rows of
+    // at most 83 bits, residues rather than slices); else per-instance lanes.
+    bool grouped_done = false;
+    if ((st = batched_grouped_residuals(c, count, n, order_idx, S, Z, slices, rho_s, rho_z, resid, &grouped_done)))
+      return st;
     // Lane l takes instances order_idx[l], order_idx[l + L], ... (largest first: its buffers never
     // grow), one after another on its stream with no host wait in between: each residual's Err, which
     // the lane's next residual overwrites in the state, is copied to the instance's slot on the lane.
-    double* rdev = (double*)ctx_buf(c, "b.resid", sizeof(double) * (size_t)count, &st);
-    if (!rdev) return st;
-    cudaEvent_t fork = ev_get(c);
-    cudaEvent_t join[zfact_ctx::kLanes];
-    for (int l = 0; l < L; ++l) join[l] = ev_get(c);
-    cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
-    cudaEventRecord(fork, c->stream);
-    const int nl = std::min(L, count);
-    for (int l = 0; l < nl; ++l) cudaStreamWaitEvent(c->lane_stream[l], fork, 0);
-    for (int j = 0; j < count; ++j) {
-      const int l = j % L, i = order_idx[j];
-      c->lane = l;
-      double* D64 = (double*)ctx_buf(c, lane_name(c, "D64").c_str(), sizeof(double) * (size_t)n[i] * n[i], &st);
-      if (!D64) {
+    if (!grouped_done) {
+      double* rdev = (double*)ctx_buf(c, "b.resid", sizeof(double) * (size_t)count, &st);
+      if (!rdev) return st;
+      cudaEvent_t fork = ev_get(c);
+      cudaEvent_t join[zfact_ctx::kLanes];
+      for (int l = 0; l < L; ++l) join[l] = ev_get(c);
+      cudaMemsetAsync(c->st_dev, 0, sizeof(IterState), c->stream);
+      cudaEventRecord(fork, c->stream);
+      const int nl = std::min(L, count);
+      for (int l = 0; l < nl; ++l) cudaStreamWaitEvent(c->lane_stream[l], fork, 0);
+      for (int j = 0; j < count; ++j) {
+        const int l = j % L, i = order_idx[j];
+        c->lane = l;
+        double* D64 = (double*)ctx_buf(c, lane_name(c, "D64").c_str(), sizeof(double) * (size_t)n[i] * n[i], &st);
+        if (!D64) {
+          c->lane = -1;
+          return st;
+        }
+        st = oz_prepare_S(c, S[i], n[i], slices[i], rho_s[i]);
+        if (!st) st = oz_residual(c, Z[i], D64, n[i], l, 0, 0.0, 0, rho_z[i]);
+        if (!st)
+          st = ctx_cuda(c, cudaMemcpyAsync(rdev + i, &c->st_dev->hist[l], sizeof(double), cudaMemcpyDeviceToDevice,
+                                           c->lane_stream[l]),
+                        "residual slot");
         c->lane = -1;
-        return st;
+        if (st) return st;
       }
-      st = oz_prepare_S(c, S[i], n[i], slices[i], rho_s[i]);
-      if (!st) st = oz_residual(c, Z[i], D64, n[i], l, 0, 0.0, 0, rho_z[i]);
-      if (!st)
-        st = ctx_cuda(c, cudaMemcpyAsync(rdev + i, &c->st_dev->hist[l], sizeof(double), cudaMemcpyDeviceToDevice,
-                                         c->lane_stream[l]),
-                      "residual slot");
-      c->lane = -1;
-      if (st) return st;
+      for (int l = 0; l < nl; ++l) {
+        cudaEventRecord(join[l], c->lane_stream[l]);
+        cudaStreamWaitEvent(c->stream, join[l], 0);
+      }
+      if ((st = ctx_cuda(c, cudaMemcpyAsync(resid.data(), rdev, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost,
+                                            c->stream),
+                         "residuals")))
+        return st;
+      if ((st = ctx_read_state(c))) return st;
+      c->ev_pool.push_back(fork);
+      for (int l = 0; l < L; ++l) c->ev_pool.push_back(join[l]);
     }
-    for (int l = 0; l < nl; ++l) {
-      cudaEventRecord(join[l], c->lane_stream[l]);
-      cudaStreamWaitEvent(c->stream, join[l], 0);
-    }
-    if ((st = ctx_cuda(c, cudaMemcpyAsync(resid.data(), rdev, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost,
-                                          c->stream),
-                       "residuals")))
-      return st;
-    if ((st = ctx_read_state(c))) return st;
-    c->ev_pool.push_back(fork);
-    for (int l = 0; l < L; ++l) c->ev_pool.push_back(join[l]);
   }
   cudaEventRecord(c->ev1, c->stream);
   cudaEventSynchronize(c->ev1);

@@ -40,6 +40,19 @@ cudaError_t launch_b_pack(const BatchTables& t, int count, int max_n, int mode, 
                           int ld, bool bf16, uint16_t* h16, uint16_t* l16, uint16_t* th16, uint16_t* tl16, float* m32,
                           cudaStream_t s);
 cudaError_t launch_b_unpack(const BatchTables& t, int count, int max_n, const float* m32, int ld, cudaStream_t s);
+}  // namespace zf
+
+#include <vector>
+struct zfact_ctx;
+// The FP64-accurate final residual of every instance as grouped launches (batched_resid.cu): resid[i] =
+// ||I - Z_i^T S_i Z_i||_F.  *done = false (nothing queued) when the batch is outside the grouped form (an
+// instance above one residue chunk, rows above 83 bits, slices requested): the caller then uses lanes.
+int batched_grouped_residuals(zfact_ctx* c, int count, const std::vector<int>& n, const std::vector<int>& order,
+                              const double* const* S, double* const* Z, const std::vector<int>& slices,
+                              const std::vector<double>& rho_s, const std::vector<double>& rho_z,
+                              std::vector<double>& resid, bool* done);
+
+namespace zf {
 cudaError_t launch_b_finish(const double* partials, const BatchTables& t, const BatchState& bs, int count,
                             int initial, int rule, double tol, int check_stop, int limit, cudaStream_t s);
 

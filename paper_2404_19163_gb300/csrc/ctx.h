@@ -125,6 +125,12 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
                 double rho_zt = -1.0);
 int oz_update(zfact_ctx* c, double* Z, const double* Q, int n, double qmax, double rho_zr = -1.0);
 double oz_rho_from(unsigned int rho2_bits, int n);
+// Bits the moduli product must exceed for T_A- and T_B-bit rows with scaled row norms rhoA, rhoB (-1:
+// unknown) over K = n terms, the moduli count for them (*wide: the wider set; 0: slices), and the K-blocks
+// of one residue chunk.
+double oz_product_bits(int TA, int TB, double rhoA, double rhoB, int n);
+int oz_moduli_count(const zfact_ctx* c, int TA, int TB, double bits, int* wide);
+int oz_crt_chunk_kb();
 int oz_update_slices(int n, double q);
 int oz_update_bits(int n, double q);
 int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, int n);

@@ -180,15 +180,16 @@ __global__ void k_ozm_tres(const double* __restrict__ X, int n, int ld, const in
 // reads one 4-byte word per plane per row (a warp reads 128 consecutive bytes of a plane).  With sym
 // only entries j >= i are formed (their digits are the only ones written) and mirrored through
 // shared memory.
+// One 32 x 128 output tile at (bi, bj) of a reconstruction (the kernels below place it); out may be null
+// (mode 2: only the tile's sum of d^2 into *partial_out).
 template <class Plan, class Acc, int KMAX>
-__global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restrict__ G, size_t gstride, int ld8,
-                                                         int nch, const __grid_constant__ Plan plan,
-                                                         const int* __restrict__ eA, const int* __restrict__ eB, int TA,
-                                                         int TB, int n, double* __restrict__ out, int ld64, int mode,
-                                                         int sym, double* __restrict__ partials) {
+__device__ __forceinline__ void combine8_tile(const uint8_t* __restrict__ G, size_t gstride, int ld8, int nch,
+                                              const Plan& plan, const int* __restrict__ eA,
+                                              const int* __restrict__ eB, int TA, int TB, int n,
+                                              double* __restrict__ out, int ld64, int mode, int sym,
+                                              double* partial_out, int bi, int bj) {
   __shared__ double tile[32][129];
   __shared__ double red[8];
-  const int bi = blockIdx.y * 32, bj = blockIdx.x * 128;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool active = !sym || bj + 127 >= bi;
   const int nmod = plan.nmod;
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
               if (j > i) ss_off = fma(v, v, ss_off);
             }
           }
-          if (!sym || j >= i) {
+          if (out && (!sym || j >= i)) {
             double* o = out + (size_t)i * ld64 + j;
             if (mode == 1)
               *o += v;
@@ -261,7 +262,7 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
         tile[r][4 * tx + k] = v;
       }
     }
-    if (sym) {
+    if (sym && out) {
       // (i, j) with j > i also goes to (j, i): rows bj.. of the output, columns bi..
       __syncthreads();
       for (int rr = ty; rr < 128; rr += 8) {
@@ -286,9 +287,35 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
       double t = 0.0;
 #pragma unroll
       for (int w = 0; w < 8; ++w) t += red[w];
-      partials[blockIdx.y * gridDim.x + blockIdx.x] = t;
+      if (partial_out) *partial_out = t;
     }
   }
+}
+
+template <class Plan, class Acc, int KMAX>
+__global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restrict__ G, size_t gstride, int ld8,
+                                                         int nch, const __grid_constant__ Plan plan,
+                                                         const int* __restrict__ eA, const int* __restrict__ eB, int TA,
+                                                         int TB, int n, double* __restrict__ out, int ld64, int mode,
+                                                         int sym, double* __restrict__ partials) {
+  combine8_tile<Plan, Acc, KMAX>(G, gstride, ld8, nch, plan, eA, eB, TA, TB, n, out, ld64, mode, sym,
+                                 partials ? partials + blockIdx.y * gridDim.x + blockIdx.x : nullptr, blockIdx.y * 32,
+                                 blockIdx.x * 128);
+}
+
+// Every instance of a group (grid.z): its digits, exponents and output rows start at its packed row.
+template <class Plan, class Acc, int KMAX>
+__global__ void __launch_bounds__(256, 2) k_gozm_combine8(const uint8_t* __restrict__ G, size_t gstride, int ld8,
+                                                          const __grid_constant__ Plan plan, const GroupRes g,
+                                                          const int* __restrict__ eA, const int* __restrict__ eB,
+                                                          double* __restrict__ out, int ld64, int mode, int sym,
+                                                          double* __restrict__ partials) {
+  const int inst = blockIdx.z, r0 = g.row0[inst], T = g.T[inst];
+  const size_t nb = (size_t)gridDim.x * gridDim.y;
+  combine8_tile<Plan, Acc, KMAX>(G + (size_t)r0 * ld8, gstride, ld8, 1, plan, eA + r0, eB + r0, T, T, g.n[inst],
+                                 out ? out + (size_t)r0 * ld64 : nullptr, ld64, mode, sym,
+                                 partials ? partials + inst * nb + blockIdx.y * gridDim.x + blockIdx.x : nullptr,
+                                 blockIdx.y * 32, blockIdx.x * 128);
 }
 
 // rho_r^2 = sum_k (x_rk 2^-e_r)^2 of every row r of X (e_r the row's exponent bound, as in the
@@ -333,6 +360,146 @@ __global__ void __launch_bounds__(256) k_ozm_rowrho(const double* __restrict__ X
     for (int w = 0; w < 8; ++w) t += reds[w];
     atomicMax(rho2, __float_as_uint(t));
   }
+}
+
+// ---- grouped forms (the batched mode's final residuals): instance = blockIdx.y (rows) or blockIdx.z (tiles)
+template <int NP>
+__global__ void __launch_bounds__(256) k_gozm_rowres(const GroupRes g, int nmod, uint16_t* __restrict__ out, int ld16,
+                                                     size_t plane) {
+  __shared__ unsigned long long red[8];
+  const int inst = blockIdx.y, n = g.n[inst], row = blockIdx.x;
+  if (row >= n) return;
+  const int r0 = g.row0[inst], T = g.T[inst], tid = threadIdx.x;
+  const double* xr = g.src ? g.src[inst] + (size_t)row * n : g.packed + (size_t)(r0 + row) * g.ldp;
+  unsigned long long m = 0ull;
+  for (int c = tid; c < n; c += 256) m = max_bits(m, abs_bits(xr[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  m = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = max_bits(m, red[w]);
+  const int er = m ? exp_of_bits(m) : -2000000000;
+  if (tid == 0) g.e[r0 + row] = er;
+  uint16_t* orow = out + (size_t)(r0 + row) * ld16;
+  const int ncols = (n + 63) & ~63;  // zeros from n up to the K padding the tensor-core loads read
+  for (int j = 2 * tid; j < ncols; j += 512) {
+    float p0[5], p1[5];
+    parts_of(j < n ? xr[j] : 0.0, er, T, p0);
+    parts_of(j + 1 < n ? xr[j + 1] : 0.0, er, T, p1);
+    residues_pair_all<0, NP>(p0, p1, nmod, orow + j, plane);
+  }
+}
+
+template <int NP>
+__global__ void k_gozm_tres(const GroupRes g, int nmod, uint16_t* __restrict__ out, int ld16, size_t plane) {
+  __shared__ double te[32][33], to[32][33];
+  const int inst = blockIdx.z, n = g.n[inst];
+  const int bi = blockIdx.y * 64, bj = blockIdx.x * 32;
+  const int ncols = (n + 63) & ~63;
+  if (bj >= n || bi >= ncols) return;  // the whole block (uniform)
+  const int r0 = g.row0[inst], T = g.T[inst];
+  const double* X = g.src[inst];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int rr = ty; rr < 64; rr += 8) {
+    const int i = bi + rr, j = bj + tx;
+    const double x = (i < n && j < n) ? X[(size_t)i * n + j] : 0.0;
+    if (rr & 1)
+      to[rr >> 1][tx] = x;
+    else
+      te[rr >> 1][tx] = x;
+  }
+  __syncthreads();
+  const int col = bi + 2 * tx;  // < ncols: bi + 63 < ncols since both are multiples of 64
+  for (int r = ty; r < 32; r += 8) {
+    const int row = bj + r;
+    if (row >= n) continue;
+    const int er = g.e[r0 + row];
+    float p0[5], p1[5];
+    parts_of(te[tx][r], er, T, p0);
+    parts_of(to[tx][r], er, T, p1);
+    residues_pair_all<0, NP>(p0, p1, nmod, out + (size_t)(r0 + row) * ld16 + col, plane);
+  }
+}
+
+__global__ void k_gozm_colmax(const GroupRes g, unsigned long long* __restrict__ cmax) {
+  __shared__ unsigned long long red[8][33];
+  const int inst = blockIdx.z, n = g.n[inst];
+  const int j = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 256;
+  if (blockIdx.x * 32 >= n || r0 >= n) return;  // the whole block (uniform)
+  const int r1 = r0 + 256 < n ? r0 + 256 : n;
+  const double* Z = g.src[inst];
+  unsigned long long m = 0ull;
+  if (j < n)
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) m = max_bits(m, abs_bits(Z[(size_t)r * n + j]));
+  red[threadIdx.y][threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < n) {
+    for (int y = 1; y < 8; ++y) m = max_bits(m, red[y][threadIdx.x]);
+    if (m) atomicMax(&cmax[g.row0[inst] + j], m);
+  }
+}
+
+__global__ void k_gozm_colfin(const GroupRes g, const unsigned long long* __restrict__ cmax) {
+  const int inst = blockIdx.y, n = g.n[inst], j = blockIdx.x * 256 + threadIdx.x;
+  if (j >= n) return;
+  const unsigned long long m = cmax[g.row0[inst] + j];
+  g.e[g.row0[inst] + j] = m ? exp_of_bits(m) : -2000000000;
+}
+
+// rho2[inst] = max over the instance's packed rows of rho_r^2 (as k_ozm_rowrho).
+__global__ void __launch_bounds__(256) k_gozm_rowrho(const GroupRes g, unsigned int* __restrict__ rho2) {
+  __shared__ unsigned long long redm[8];
+  __shared__ float reds[8];
+  const int inst = blockIdx.y, n = g.n[inst], row = blockIdx.x;
+  if (row >= n) return;
+  const double* xr = g.packed + (size_t)(g.row0[inst] + row) * g.ldp;
+  const int tid = threadIdx.x;
+  unsigned long long m = 0ull;
+  for (int c = tid; c < n; c += 256) m = max_bits(m, abs_bits(xr[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) redm[tid >> 5] = m;
+  __syncthreads();
+  m = redm[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = max_bits(m, redm[w]);
+  if (m == 0ull) return;
+  if (m >= 0x7FF0000000000000ull || m < (1ull << 52)) {
+    if (tid == 0) atomicMax(&rho2[inst], 0x7F800000u);
+    return;
+  }
+  const int e = exp_of_bits(m);
+  float acc = 0.0f;
+  for (int c = tid; c < n; c += 256) {
+    const float f = scaled_mag_f32(abs_bits(xr[c]), e);
+    acc = fmaf(f, f, acc);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) reds[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += reds[w];
+    atomicMax(&rho2[inst], __float_as_uint(t));
+  }
+}
+
+__global__ void k_gozm_finish(const double* __restrict__ partials, int nb, double* __restrict__ err) {
+  __shared__ double red[256];
+  const double* p = partials + (size_t)blockIdx.x * nb;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nb; k += 256) s += p[k];  // fixed order per thread
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) err[blockIdx.x] = sqrt(red[0]);
 }
 
 }  // namespace
@@ -399,6 +566,71 @@ cudaError_t launch_ozmw_combine8(const uint8_t* G, size_t gstride, int ld8, int 
   dim3 grid((n + 127) / 128, (n + 31) / 32), block(32, 8);
   k_ozm_combine8<crtw::Plan, crtw::Acc, crtw::kMax><<<grid, block, 0, s>>>(G, gstride, ld8, nch, plan, eA, eB, TA, TB,
                                                                          n, out, ld64, mode, sym ? 1 : 0, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozm_rowres(const GroupRes& g, int nmod, uint16_t* out, int ld16, size_t plane, int maxT,
+                               cudaStream_t s) {
+  if (nmod < 1 || nmod > kCrtMax || maxT > 62 || g.count < 1) return cudaErrorInvalidValue;
+  const dim3 grid(g.max_n, g.count);
+  if (maxT <= 55)
+    k_gozm_rowres<4><<<grid, 256, 0, s>>>(g, nmod, out, ld16, plane);
+  else
+    k_gozm_rowres<5><<<grid, 256, 0, s>>>(g, nmod, out, ld16, plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozm_tres(const GroupRes& g, int nmod, uint16_t* out, int ld16, size_t plane, int maxT,
+                             cudaStream_t s) {
+  if (nmod < 1 || nmod > kCrtMax || maxT > 62 || g.count < 1 || !g.src) return cudaErrorInvalidValue;
+  const dim3 grid((g.max_n + 31) / 32, (g.max_n + 63) / 64, g.count), block(32, 8);
+  if (maxT <= 55)
+    k_gozm_tres<4><<<grid, block, 0, s>>>(g, nmod, out, ld16, plane);
+  else
+    k_gozm_tres<5><<<grid, block, 0, s>>>(g, nmod, out, ld16, plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozm_colexp(const GroupRes& g, unsigned long long* scratch, size_t scratch_rows, cudaStream_t s) {
+  if (g.count < 1 || !g.src) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * scratch_rows, s);
+  if (e != cudaSuccess) return e;
+  k_gozm_colmax<<<dim3((g.max_n + 31) / 32, (g.max_n + 255) / 256, g.count), dim3(32, 8), 0, s>>>(g, scratch);
+  k_gozm_colfin<<<dim3((g.max_n + 255) / 256, g.count), 256, 0, s>>>(g, scratch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozm_rowrho(const GroupRes& g, unsigned int* rho2, cudaStream_t s) {
+  if (g.count < 1 || !g.packed) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(rho2, 0, sizeof(unsigned int) * (size_t)g.count, s);
+  if (e != cudaSuccess) return e;
+  k_gozm_rowrho<<<dim3(g.max_n, g.count), 256, 0, s>>>(g, rho2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozm_combine8(const uint8_t* G, size_t gstride, int ld8, const CrtPlan& plan, const GroupRes& g,
+                                 const int* eA, const int* eB, double* out, int ld64, int mode, bool sym,
+                                 double* partials, cudaStream_t s) {
+  if (plan.nmod < 1 || plan.nmod > kCrtMax || (ld8 % 4) != 0 || g.count < 1) return cudaErrorInvalidValue;
+  dim3 grid((g.max_n + 127) / 128, (g.max_n + 31) / 32, g.count), block(32, 8);
+  k_gozm_combine8<CrtPlan, CrtAcc, kCrtMax><<<grid, block, 0, s>>>(G, gstride, ld8, plan, g, eA, eB, out, ld64, mode,
+                                                                   sym ? 1 : 0, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozmw_combine8(const uint8_t* G, size_t gstride, int ld8, const crtw::Plan& plan,
+                                  const GroupRes& g, const int* eA, const int* eB, double* out, int ld64, int mode,
+                                  bool sym, double* partials, cudaStream_t s) {
+  if (plan.nmod < 1 || plan.nmod > crtw::kMax || (ld8 % 4) != 0 || g.count < 1) return cudaErrorInvalidValue;
+  dim3 grid((g.max_n + 127) / 128, (g.max_n + 31) / 32, g.count), block(32, 8);
+  k_gozm_combine8<crtw::Plan, crtw::Acc, crtw::kMax><<<grid, block, 0, s>>>(G, gstride, ld8, plan, g, eA, eB, out,
+                                                                            ld64, mode, sym ? 1 : 0, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozm_finish(const double* partials, int nb, int count, double* err, cudaStream_t s) {
+  if (count < 1 || nb < 1) return cudaErrorInvalidValue;
+  k_gozm_finish<<<count, 256, 0, s>>>(partials, nb, err);
   return cudaGetLastError();
 }
 

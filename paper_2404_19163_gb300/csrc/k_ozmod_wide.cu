@@ -132,6 +132,65 @@ __global__ void k_ozmw_tres(const double* __restrict__ X, int n, int ld, const i
   }
 }
 
+// Grouped forms (the batched mode's final residuals; layouts as k_ozmod.cu's k_gozm_rowres / k_gozm_tres).
+__global__ void __launch_bounds__(256) k_gozmw_rowres(const GroupRes g, int nmod, uint16_t* __restrict__ out,
+                                                      int ld16, size_t plane) {
+  __shared__ unsigned long long red[8];
+  const int inst = blockIdx.y, n = g.n[inst], row = blockIdx.x;
+  if (row >= n) return;
+  const int r0 = g.row0[inst], T = g.T[inst], tid = threadIdx.x;
+  const double* xr = g.src ? g.src[inst] + (size_t)row * n : g.packed + (size_t)(r0 + row) * g.ldp;
+  unsigned long long m = 0ull;
+  for (int c = tid; c < n; c += 256) m = max_bits(m, abs_bits(xr[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  __syncthreads();
+  m = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = max_bits(m, red[w]);
+  const int er = m ? exp_of_bits(m) : -2000000000;
+  if (tid == 0) g.e[r0 + row] = er;
+  uint16_t* orow = out + (size_t)(r0 + row) * ld16;
+  const int ncols = (n + 63) & ~63;
+  for (int j = 2 * tid; j < ncols; j += 512) {
+    float p0[crtw::kParts], p1[crtw::kParts];
+    parts_w(j < n ? xr[j] : 0.0, er, T, p0);
+    parts_w(j + 1 < n ? xr[j + 1] : 0.0, er, T, p1);
+    wres_pair<0>(p0, p1, nmod, orow + j, plane);
+  }
+}
+
+__global__ void k_gozmw_tres(const GroupRes g, int nmod, uint16_t* __restrict__ out, int ld16, size_t plane) {
+  __shared__ double te[32][33], to[32][33];
+  const int inst = blockIdx.z, n = g.n[inst];
+  const int bi = blockIdx.y * 64, bj = blockIdx.x * 32;
+  const int ncols = (n + 63) & ~63;
+  if (bj >= n || bi >= ncols) return;  // the whole block (uniform)
+  const int r0 = g.row0[inst], T = g.T[inst];
+  const double* X = g.src[inst];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int rr = ty; rr < 64; rr += 8) {
+    const int i = bi + rr, j = bj + tx;
+    const double x = (i < n && j < n) ? X[(size_t)i * n + j] : 0.0;
+    if (rr & 1)
+      to[rr >> 1][tx] = x;
+    else
+      te[rr >> 1][tx] = x;
+  }
+  __syncthreads();
+  const int col = bi + 2 * tx;
+  for (int r = ty; r < 32; r += 8) {
+    const int row = bj + r;
+    if (row >= n) continue;
+    const int er = g.e[r0 + row];
+    float p0[crtw::kParts], p1[crtw::kParts];
+    parts_w(te[tx][r], er, T, p0);
+    parts_w(to[tx][r], er, T, p1);
+    wres_pair<0>(p0, p1, nmod, out + (size_t)(r0 + row) * ld16 + col, plane);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int* e, int T, int nmod, uint16_t* out,
@@ -147,6 +206,19 @@ cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int
   } else {
     k_ozmw_rowres<<<n, 256, 0, s>>>(X, n, ld, e, T, nmod, out, ld16, Rp);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozmw_rowres(const GroupRes& g, int nmod, uint16_t* out, int ld16, size_t plane, cudaStream_t s) {
+  if (nmod < 1 || nmod > crtw::kMax || g.count < 1) return cudaErrorInvalidValue;
+  k_gozmw_rowres<<<dim3(g.max_n, g.count), 256, 0, s>>>(g, nmod, out, ld16, plane);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gozmw_tres(const GroupRes& g, int nmod, uint16_t* out, int ld16, size_t plane, cudaStream_t s) {
+  if (nmod < 1 || nmod > crtw::kMax || g.count < 1 || !g.src) return cudaErrorInvalidValue;
+  const dim3 grid((g.max_n + 31) / 32, (g.max_n + 63) / 64, g.count), block(32, 8);
+  k_gozmw_tres<<<grid, block, 0, s>>>(g, nmod, out, ld16, plane);
   return cudaGetLastError();
 }
 

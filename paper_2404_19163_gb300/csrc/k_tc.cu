@@ -61,6 +61,7 @@ struct UnitPlan {
   int inst, n, row0, skip;
 };
 
+template <int BN>
 __device__ __forceinline__ UnitPlan plan_unit(int u, const TcArgs& a, int kblocks_all) {
   UnitPlan pl;
   pl.inst = 0;
@@ -87,8 +88,10 @@ __device__ __forceinline__ UnitPlan plan_unit(int u, const TcArgs& a, int kblock
   if (a.oz_s > 0) {
     // group-major order: the CTAs running at the same time form different tiles of the same
     // (group, K-chunk) and so read the same slice panels, which then stay in L2
-    pl.group = u / a.oz_tiles;
-    pl.tile = u % a.oz_tiles;
+    // (grouped residue products: the instance's own tile count; its units are tiles x moduli x chunks)
+    const int ntiles = a.ninst > 0 ? tiles_of(pl.n, pl.n, a.sym, BN) : a.oz_tiles;
+    pl.group = u / ntiles;
+    pl.tile = u % ntiles;
     pl.t = pl.group / a.oz_nch;
     const int c = pl.group % a.oz_nch;
     if (a.oz_diag) {
@@ -378,7 +381,7 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
         }
         w[q] = word;
       }
-      put8(a.d8 + (size_t)group * a.g_stride, a.ld32, i, col0, n, a.sym != 0, w);
+      put8(a.d8 + (size_t)group * a.g_stride + (size_t)row0 * a.ld32, a.ld32, i, col0, n, a.sym != 0, w);
       break;
     }
     case kEpiZupd64: {
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       int it = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const UnitPlan pl = plan_unit(u, a, kblocks);
+        const UnitPlan pl = plan_unit<BN>(u, a, kblocks);
         if (pl.skip) continue;
         int bm, bn;
         decode_unit(pl.tile, a, pl.n, BN, bm, bn);
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       int it = 0, ui = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const UnitPlan pl = plan_unit(u, a, kblocks);
+        const UnitPlan pl = plan_unit<BN>(u, a, kblocks);
         if (pl.skip) continue;
         const int buf = ui & 1;
         const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
     if (a.sb_ptr) us /= *a.sb_ptr;
     float amax = 0.0f;
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
-      const UnitPlan pl = plan_unit(u, a, kblocks);
+      const UnitPlan pl = plan_unit<BN>(u, a, kblocks);
       if (pl.skip) continue;
       const int buf = ui & 1;
       const uint32_t uph = (uint32_t)(ui >> 1) & 1u;

@@ -134,6 +134,47 @@ cudaError_t launch_ozmw_combine8(const uint8_t* G, size_t gstride, int ld8, int 
                                  const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
                                  bool sym, double* partials, cudaStream_t s);
 
+// ---- grouped residue products (the batched mode's final residuals, batched.cu)
+// Instance i of a group: size n[i], its operand rows at packed rows row0[i] ... (one leading dimension for
+// the group), fixed-point bits T[i].  A source is either per-instance matrices src[i] (n_i x n_i, leading
+// dimension n_i) or one packed FP64 matrix (rows row0[i] + r, leading dimension ldp).  Exponents e are
+// packed like the rows (e[row0[i] + r]).  Residue planes: plane t of operand row row0[i] + r at
+// out + t * plane + (row0[i] + r) * ld16; columns n_i ... up to a multiple of 64 are written as zeros.
+struct GroupRes {
+  const int* n;
+  const int* row0;
+  const int* T;
+  const double* const* src;
+  const double* packed;
+  int ldp;
+  int* e;
+  int count, max_n;
+};
+// Row residues (rows of src[i] or of the packed matrix; e written), T <= 62, nmod <= kCrtMax.
+cudaError_t launch_gozm_rowres(const GroupRes& g, int nmod, uint16_t* out, int ld16, size_t plane, int maxT,
+                               cudaStream_t s);
+// Residues of the columns of src[i] (e from launch_gozm_colexp), T <= 62, nmod <= kCrtMax.
+cudaError_t launch_gozm_tres(const GroupRes& g, int nmod, uint16_t* out, int ld16, size_t plane, int maxT,
+                             cudaStream_t s);
+// The same with the wider moduli (T <= 83, nmod <= crtw::kMax).
+cudaError_t launch_gozmw_rowres(const GroupRes& g, int nmod, uint16_t* out, int ld16, size_t plane, cudaStream_t s);
+cudaError_t launch_gozmw_tres(const GroupRes& g, int nmod, uint16_t* out, int ld16, size_t plane, cudaStream_t s);
+// Column exponents of src[i] into g.e (packed), scratch: 8 * (packed rows) bytes.
+cudaError_t launch_gozm_colexp(const GroupRes& g, unsigned long long* scratch, size_t scratch_rows, cudaStream_t s);
+// Largest rho_r^2 of the rows of each instance's packed matrix rows (as launch_ozm_rho) into rho2[i].
+cudaError_t launch_gozm_rowrho(const GroupRes& g, unsigned int* rho2, cudaStream_t s);
+// CRT reconstruction of every instance (plan, modes as launch_ozm_combine8; TA = TB = T[i]); out packed
+// (row0[i], leading dimension ld64) or null (mode 2: only the Err partials, ozm_combine_blocks(max_n) per
+// instance from partials + i * ozm_combine_blocks(max_n)).
+cudaError_t launch_gozm_combine8(const uint8_t* G, size_t gstride, int ld8, const CrtPlan& plan, const GroupRes& g,
+                                 const int* eA, const int* eB, double* out, int ld64, int mode, bool sym,
+                                 double* partials, cudaStream_t s);
+cudaError_t launch_gozmw_combine8(const uint8_t* G, size_t gstride, int ld8, const crtw::Plan& plan,
+                                  const GroupRes& g, const int* eA, const int* eB, double* out, int ld64, int mode,
+                                  bool sym, double* partials, cudaStream_t s);
+// err[i] = sqrt(sum of instance i's nb partials), in a fixed order.
+cudaError_t launch_gozm_finish(const double* partials, int nb, int count, double* err, cudaStream_t s);
+
 // ---- error-free slicing (k_ozaki.cu)
 // e[r] = exponent bounding column r of X (cols = true; rows: nothing, the row kernels find their own).
 // scratch: oz_colstats_scratch_bytes(n) bytes of device memory, 8-byte aligned.

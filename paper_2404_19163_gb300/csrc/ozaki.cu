@@ -114,6 +114,13 @@ double oz_rho_from(unsigned int rho2_bits, int n) {
   return sqrt((double)t * (1.0 + (n / 8.0 + 40.0) * ldexp(1.0, -22)));
 }
 
+// The bound and moduli choice of the products above, for the grouped residuals of the batched mode.
+double oz_product_bits(int TA, int TB, double rhoA, double rhoB, int n) { return oz_prod_bits(TA, TB, rhoA, rhoB, n); }
+int oz_moduli_count(const zfact_ctx* c, int TA, int TB, double bits, int* wide) {
+  return oz_moduli_for(c, TA, TB, bits, wide);
+}
+int oz_crt_chunk_kb() { return kCrtChunkKb; }
+
 namespace {
 
 int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx, bool trans, int T, int nmod,

@@ -116,3 +116,31 @@ def test_batched_with_refinement_reaches_fp64(ctx):
         assert inf["refine_iters"] >= 1 and inf["resid_f"] / math.sqrt(n) <= 1e-12
         assert e / math.sqrt(n) <= 1e-12 and abs(inf["resid_f"] - e) <= 1e-12
         assert inf["hist_len"] > inf["iters"] + 1
+
+
+@pytest.mark.parametrize("emu", ["auto", "slices"])
+def test_batched_final_residuals_grouped(ctx, emu):
+    """Under the default scheme every instance's FP64-accurate final residual comes from grouped launches
+    (two residue-product launches for the whole batch, which fits one group), and each equals the
+    oracle's residual of the returned Z; with slices requested the per-instance lanes run instead."""
+    import torch
+    sizes = [300, 64, 513, 1, 129, 700, 257, 100, 450, 33]
+    Ss = mats(sizes, seed=3)
+    St = [torch.from_numpy(S).cuda() for S in Ss]
+    ctx.set_emulation(emu)
+    ctx.set_profiling(True)
+    ctx.kernel_stats(reset=True)
+    try:
+        Zb, hist, infos, status = ctx.refine_batched(St, None, precision="bf16_split", hist_cap=32)
+        stats = {k["name"]: k for k in ctx.kernel_stats(reset=True)}
+    finally:
+        ctx.set_profiling(False)
+        ctx.set_emulation("auto")
+    assert all(s in (0, 100) for s in status), status
+    if emu == "auto":
+        assert stats["tc_gemm.crt"]["launches"] == 2, stats.get("tc_gemm.crt")
+    else:
+        assert "tc_gemm.crt" not in stats and stats["tc_gemm.ozaki"]["launches"] >= len(sizes)
+    for k, S in enumerate(Ss):
+        _, e = oracle.residual(S, Zb[k].cpu().numpy())
+        assert abs(infos[k]["resid_f"] - e) <= 1e-12 + 1e-9 * e, (k, infos[k]["resid_f"], e)
