@@ -200,6 +200,7 @@ extern "C" void zfact_destroy(zfact_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  if (c->gr_pinned) cudaFreeHost(c->gr_pinned);
   for (auto& kv : c->loop_graph_cache) cudaGraphExecDestroy(kv.second.exec);
   c->loop_graph_cache.clear();
   for (auto& kv : c->bufs) cudaFree(kv.second.ptr);

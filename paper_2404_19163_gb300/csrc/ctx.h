@@ -70,6 +70,9 @@ struct zfact_ctx {
   std::map<std::string, LoopGraph> loop_graph_cache;
   bool loop_graphs = true;  // zfact_set_loop_graphs
   unsigned long long ws_gen = 0;
+  // pinned host words for the grouped residuals' read-backs and tables (batched_resid.cu)
+  int* gr_pinned = nullptr;
+  size_t gr_pinned_n = 0;
   // batched mode
   std::map<std::string, int> batch_bn;  // autotuned tile width per set of sizes
   std::string batch_sig;                // layout of the packed buffers (zeroed on change)
