@@ -38,8 +38,8 @@ TOL = 1e-12
 # dram__bytes_write.sum, mean over the captured launches), valid only while the kernel's source is
 # the one that was captured; otherwise the bench line reports traffic as null.
 TRAFFIC = {
-    "tc_gemm.crt": {"source": "paper_2404_19163_gb300/csrc/k_tc.cu", "sha1": "a2b7fe18a439605d7c30c322b36261ef8db2693b",
-                    "bytes_per_launch": 1.364e9},
+    "tc_gemm.crt": {"source": "paper_2404_19163_gb300/csrc/k_tc.cu", "sha1": "c52920f2f41aa8c33e60919d3f25768c9aad8043",
+                    "bytes_per_launch": 1.365e9},
 }
 FP64_ITERS_WORKLOAD2 = 4   # updates the FP64 recursion needs on workload 2 (counted by the FP64 GPU path
                            # and by the oracle's own stop rule on the same input)
@@ -520,6 +520,48 @@ def run_case_residual(args):
     print(json.dumps({"case": "residual_ozaki", "N": n, "ms": round(ms, 3), "err": err}), flush=True)
 
 
+def run_case_learn(args):
+    """Profiling case: the learned start's kernels alone.  The 16 features of workload 2's S
+    (row statistics, d0, E^2 on the tensor cores, traces) W + K times, then W + K full-batch
+    training steps (forward/backward and Adam) of the 16-64-64-5 network on 20 000 feature rows
+    drawn from a seeded normal; prints its own JSON line."""
+    import numpy as np
+    import torch
+    from paper_2404_19163_gb300 import Context, learn, build as zbuild
+    zbuild.build()
+    S = torch.from_numpy(workload()).cuda()
+    g = np.random.default_rng(7)
+    rows = 20000
+    X = torch.from_numpy(g.standard_normal((rows, 16)).astype(np.float32)).cuda()
+    ts = torch.from_numpy(g.uniform(0.5, 1.5, rows).astype(np.float32)).cuda()
+    to = torch.from_numpy(g.integers(0, 4, rows).astype(np.int32)).cuda()
+    with Context(0) as ctx:
+        P = torch.from_numpy(learn.init_params(0)).cuda()
+        M, V = torch.zeros_like(P), torch.zeros_like(P)
+        mu, sd = X.mean(0), X.std(0) + 1e-6
+        for _ in range(args.warmup):
+            ctx.features(S)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            f = ctx.features(S)
+        torch.cuda.synchronize()
+        ms_feat = (time.perf_counter() - t0) * 1e3 / args.steps
+        for step in range(1, args.warmup + 1):
+            grad, loss = ctx.mlp_backward(P, mu, sd, X, ts, to, 1.0)
+            ctx.mlp_adam(P, grad, M, V, step)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for step in range(args.warmup + 1, args.warmup + args.steps + 1):
+            grad, loss = ctx.mlp_backward(P, mu, sd, X, ts, to, 1.0)
+            ctx.mlp_adam(P, grad, M, V, step)
+        torch.cuda.synchronize()
+        ms_train = (time.perf_counter() - t0) * 1e3 / args.steps
+    print(json.dumps({"case": "learn", "N": int(S.shape[0]), "features_ms": round(ms_feat, 3),
+                      "train_step_ms": round(ms_train, 3), "rows": rows, "loss": loss,
+                      "features": [float(x) for x in f]}), flush=True)
+
+
 def batched_leg(args, rank=0, ws=1, local=0, frames_timed=None, fp64_comparator=False):
     """Workload 4: 128 cluster overlaps, N_i ~ U[256, 3072], frames of a trajectory (sites
     displaced by N(0, 0.02^2) per frame); frame 0 is a cold start (untimed), the next frames are
@@ -796,7 +838,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the workload 3 and 4 legs that the default line carries as extra keys")
-    ap.add_argument("--case", default=None, choices=[None, "residual", "factor"])
+    ap.add_argument("--case", default=None, choices=[None, "residual", "factor", "learn"])
     ap.add_argument("--workload", default="single", choices=["single", "batched", "ill", "paper"])
     ap.add_argument("--paper-sizes", default="1024,4096,16384")
     ap.add_argument("--tol-ill", type=float, default=1e-12)
@@ -808,6 +850,9 @@ def main():
         return
     if args.case == "factor":
         run_case_factor(args)
+        return
+    if args.case == "learn":
+        run_case_learn(args)
         return
     if args.workload == "batched":
         rank, ws, local = dist_setup()

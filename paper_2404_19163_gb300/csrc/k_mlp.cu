@@ -1,7 +1,8 @@
 // Learned start proposal (not in the paper; its warm-start motivation is Sec. 6):
 // features of an overlap matrix and a 16 -> 64 -> 64 -> 5 GELU MLP (FP32) with its
 // forward, backward and Adam kernels.  Gradients are reduced over the batch in a fixed
-// order (per-sample gradients, then one thread per parameter), so training is deterministic.
+// order (per sample the factors of each weight gradient, then per chunk of samples and per parameter the
+// sum over the chunk, then over the chunks), so training is deterministic.
 #include <math.h>
 
 #include "mlp.h"
@@ -10,6 +11,11 @@ namespace zf {
 namespace {
 
 constexpr int I0 = 16, H = 64, O = 5;
+// per-sample factors of the weight gradients (feature index of each block) and the chunk of samples
+// one k_mlp_wgrad block sums
+constexpr int A_X = 0, A_GZ1 = A_X + I0, A_H1 = A_GZ1 + H, A_GZ2 = A_H1 + H, A_H2 = A_GZ2 + H, A_GY = A_H2 + H,
+              A_N = A_GY + O;
+constexpr int kWgChunk = 64;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * I0, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H,
               OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + O * H, NPAR = OFF_B3 + O;
 static_assert(NPAR == kMlpParams, "parameter layout");
@@ -19,11 +25,11 @@ __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
-// One thread per sample: forward (and, with grads != nullptr, the per-sample gradient of
+// One thread per sample: forward (and, with act != nullptr, the per-sample factors of the gradient of
 // l_b = (y0 - t)^2 + w CE(softmax(y1..4), m) divided by the batch size).
 __global__ void k_mlp(const float* __restrict__ P, const float* __restrict__ mean, const float* __restrict__ stdv,
                       const float* __restrict__ X, int batch, float* __restrict__ Y, const float* __restrict__ tgt,
-                      const int* __restrict__ ord, float w, float* __restrict__ grads, double* __restrict__ losses) {
+                      const int* __restrict__ ord, float w, float* __restrict__ act, double* __restrict__ losses) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
   float x[I0], z1[H], h1[H], z2[H], h2[H], y[O];
@@ -47,7 +53,7 @@ __global__ void k_mlp(const float* __restrict__ P, const float* __restrict__ mea
   }
   if (Y)
     for (int o = 0; o < O; ++o) Y[(size_t)b * O + o] = y[o];
-  if (!grads) return;
+  if (!act) return;
   // loss and output gradient
   const float r = y[0] - tgt[b];
   float mx = y[1];
@@ -63,45 +69,73 @@ __global__ void k_mlp(const float* __restrict__ P, const float* __restrict__ mea
   float gy[O];
   gy[0] = 2.0f * r * inv_b;
   for (int k = 0; k < O - 1; ++k) gy[1 + k] = w * (e[k] / se - (k == m ? 1.0f : 0.0f)) * inv_b;
-  float* g = grads + (size_t)b * NPAR;
-  // layer 3
-  for (int o = 0; o < O; ++o) {
-    for (int k = 0; k < H; ++k) g[OFF_W3 + o * H + k] = gy[o] * h2[k];
-    g[OFF_B3 + o] = gy[o];
-  }
+  // the factors of every weight gradient, feature-major (act[f * batch + b]): x, gz1 (W1, b1),
+  // h1, gz2 (W2, b2), h2, gy (W3, b3); the products are summed over the batch by k_mlp_wgrad
+  auto put = [&](int f, float v) { act[(size_t)f * batch + b] = v; };
+  for (int k = 0; k < I0; ++k) put(A_X + k, x[k]);
+  for (int k = 0; k < H; ++k) put(A_H1 + k, h1[k]);
+  for (int k = 0; k < H; ++k) put(A_H2 + k, h2[k]);
+  for (int o = 0; o < O; ++o) put(A_GY + o, gy[o]);
   float gz2[H];
   for (int k = 0; k < H; ++k) {
     float s = 0.0f;
     for (int o = 0; o < O; ++o) s = fmaf(P[OFF_W3 + o * H + k], gy[o], s);
     gz2[k] = s * gelu_grad(z2[k]);
-  }
-  for (int j = 0; j < H; ++j) {
-    for (int k = 0; k < H; ++k) g[OFF_W2 + j * H + k] = gz2[j] * h1[k];
-    g[OFF_B2 + j] = gz2[j];
+    put(A_GZ2 + k, gz2[k]);
   }
   for (int k = 0; k < H; ++k) {
     float s = 0.0f;
     for (int j = 0; j < H; ++j) s = fmaf(P[OFF_W2 + j * H + k], gz2[j], s);
-    z1[k] = s * gelu_grad(z1[k]);  // reuse z1 as gz1
-  }
-  for (int j = 0; j < H; ++j) {
-    for (int k = 0; k < I0; ++k) g[OFF_W1 + j * I0 + k] = z1[j] * x[k];
-    g[OFF_B1 + j] = z1[j];
+    put(A_GZ1 + k, s * gelu_grad(z1[k]));
   }
 }
 
-// grad[p] = sum_b grads[b][p] in sample order; loss = mean_b losses[b] (thread 0).
-__global__ void k_mlp_reduce(const float* __restrict__ grads, int batch, float* __restrict__ grad,
-                             const double* __restrict__ losses, double* loss_out) {
+// Weight gradients of a chunk of kWgChunk samples: every parameter's sum over the chunk's samples in
+// sample order (the chunk's factors staged sample-major in shared memory), and the chunk's loss sum.
+__global__ void __launch_bounds__(256) k_mlp_wgrad(const float* __restrict__ act, int batch,
+                                                   const double* __restrict__ losses, float* __restrict__ part,
+                                                   double* __restrict__ lpart) {
+  extern __shared__ float sm[];  // [kWgChunk][A_N]
+  const int b0 = blockIdx.x * kWgChunk, nb = min(kWgChunk, batch - b0);
+  for (int e = threadIdx.x; e < A_N * kWgChunk; e += blockDim.x) {
+    const int f = e / kWgChunk, q = e % kWgChunk;
+    sm[q * A_N + f] = q < nb ? act[(size_t)f * batch + b0 + q] : 0.0f;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < NPAR; p += blockDim.x) {
+    int fa, fb = -1;  // gradient of p = sum_q act[fa] * act[fb] (fb < 0: the bias, act[fa] alone)
+    if (p < OFF_B1) fa = A_GZ1 + p / I0, fb = A_X + p % I0;
+    else if (p < OFF_W2) fa = A_GZ1 + (p - OFF_B1);
+    else if (p < OFF_B2) fa = A_GZ2 + (p - OFF_W2) / H, fb = A_H1 + (p - OFF_W2) % H;
+    else if (p < OFF_W3) fa = A_GZ2 + (p - OFF_B2);
+    else if (p < OFF_B3) fa = A_GY + (p - OFF_W3) / H, fb = A_H2 + (p - OFF_W3) % H;
+    else fa = A_GY + (p - OFF_B3);
+    float s = 0.0f;
+    if (fb >= 0)
+      for (int q = 0; q < nb; ++q) s = fmaf(sm[q * A_N + fa], sm[q * A_N + fb], s);
+    else
+      for (int q = 0; q < nb; ++q) s += sm[q * A_N + fa];
+    part[(size_t)blockIdx.x * NPAR + p] = s;
+  }
+  if (threadIdx.x == 0) {
+    double l = 0.0;
+    for (int q = 0; q < nb; ++q) l += losses[b0 + q];
+    lpart[blockIdx.x] = l;
+  }
+}
+
+// grad[p] = sum over chunks of the chunk sums, in chunk order; loss = the mean of the losses (thread 0).
+__global__ void k_mlp_reduce(const float* __restrict__ part, int nchunks, int batch, float* __restrict__ grad,
+                             const double* __restrict__ lpart, double* loss_out) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < NPAR) {
     float s = 0.0f;
-    for (int b = 0; b < batch; ++b) s += grads[(size_t)b * NPAR + p];
+    for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * NPAR + p];
     grad[p] = s;
   }
   if (p == 0 && loss_out) {
     double l = 0.0;
-    for (int b = 0; b < batch; ++b) l += losses[b];
+    for (int c = 0; c < nchunks; ++c) l += lpart[c];
     *loss_out = l / batch;
   }
 }
@@ -183,10 +217,19 @@ __global__ void k_feat_rowstats(const double* __restrict__ rows, int n, double* 
 __global__ void k_feat_d0(const double* __restrict__ S, int n, const double* __restrict__ st, double* __restrict__ D0) {
   const double inv = 1.0 / st[0];
   const double t1 = 1.0 - st[2] * inv;
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = e / n, j = e % n;
+  const size_t total = (size_t)n * n, stride = (size_t)gridDim.x * blockDim.x;
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  // (i, j) of e, advanced by the stride's row and column steps (no division per element)
+  size_t i = e / n, j = e % n;
+  const size_t si = stride / n, sj = stride % n;
+  for (; e < total; e += stride) {
     D0[e] = (i == j ? 1.0 - t1 : 0.0) - S[e] * inv;
+    i += si;
+    j += sj;
+    if (j >= (size_t)n) {
+      j -= n;
+      ++i;
+    }
   }
 }
 
@@ -195,13 +238,14 @@ __global__ void k_feat_traces(const double* __restrict__ D0, const double* __res
                               double* __restrict__ part) {
   __shared__ double sh[4][256];
   double a = 0, b = 0, c = 0, d = 0;
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+  const size_t total = (size_t)n * n, stride = (size_t)gridDim.x * blockDim.x;
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (size_t r = t; r < (size_t)n; r += stride) a += D0[r * (n + 1)];
+  for (size_t e = t; e < total; e += stride) {
     const double x = D0[e], p = P[e];
-    if (e / n == e % n) a += x;
-    b += x * x;
-    c += p * x;
-    d += p * p;
+    b = fma(x, x, b);
+    c = fma(p, x, c);
+    d = fma(p, p, d);
   }
   sh[0][threadIdx.x] = a;
   sh[1][threadIdx.x] = b;
@@ -217,12 +261,24 @@ __global__ void k_feat_traces(const double* __restrict__ D0, const double* __res
     for (int q = 0; q < 4; ++q) part[4 * blockIdx.x + q] = sh[q][0];
 }
 
-__global__ void k_feat_final(const double* __restrict__ part, int nblocks, const double* __restrict__ st, int n,
-                             float* __restrict__ f) {
+// The block partials summed in a fixed order (thread t takes blocks t, t + 256, ..., then a tree), and
+// the 16 features.
+__global__ void __launch_bounds__(256) k_feat_final(const double* __restrict__ part, int nblocks,
+                                                    const double* __restrict__ st, int n, float* __restrict__ f) {
+  __shared__ double sh[4][256];
+  double v[4] = {0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int q = 0; q < 4; ++q) v[q] += part[4 * b + q];
+  for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = v[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
   if (threadIdx.x != 0) return;
-  double s[4] = {0, 0, 0, 0};
-  for (int b = 0; b < nblocks; ++b)
-    for (int q = 0; q < 4; ++q) s[q] += part[4 * b + q];
+  double s[4];
+  for (int q = 0; q < 4; ++q) s[q] = sh[q][0];
   const double g = st[0];
   // central moments of the spectrum of d0 from E = d0 - t1 I, then the raw moments t_k
   const double t1 = 1.0 - st[2] / g;
@@ -251,14 +307,22 @@ __global__ void k_feat_final(const double* __restrict__ part, int nblocks, const
 }  // namespace
 
 cudaError_t launch_mlp(const float* P, const float* mean, const float* stdv, const float* X, int batch, float* Y,
-                       const float* tgt, const int* ord, float w, float* grads, double* losses, cudaStream_t s) {
-  k_mlp<<<(batch + 63) / 64, 64, 0, s>>>(P, mean, stdv, X, batch, Y, tgt, ord, w, grads, losses);
+                       const float* tgt, const int* ord, float w, float* act, double* losses, cudaStream_t s) {
+  k_mlp<<<(batch + 63) / 64, 64, 0, s>>>(P, mean, stdv, X, batch, Y, tgt, ord, w, act, losses);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_reduce(const float* grads, int batch, float* grad, const double* losses, double* loss,
-                              cudaStream_t s) {
-  k_mlp_reduce<<<(NPAR + 127) / 128, 128, 0, s>>>(grads, batch, grad, losses, loss);
+int mlp_act_floats(int batch) { return A_N * batch; }
+int mlp_chunks(int batch) { return (batch + kWgChunk - 1) / kWgChunk; }
+
+cudaError_t launch_mlp_reduce(const float* act, int batch, float* part, const double* losses, double* lpart,
+                              float* grad, double* loss, cudaStream_t s) {
+  const int smem = (int)sizeof(float) * A_N * kWgChunk;
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int nc = mlp_chunks(batch);
+  k_mlp_wgrad<<<nc, 256, smem, s>>>(act, batch, losses, part, lpart);
+  k_mlp_reduce<<<(NPAR + 127) / 128, 128, 0, s>>>(part, nc, batch, grad, lpart, loss);
   return cudaGetLastError();
 }
 
@@ -291,7 +355,7 @@ cudaError_t launch_feat_traces(const double* D0, const double* P, int n, double*
                                cudaStream_t s) {
   const int nb = feat_trace_blocks(n);
   k_feat_traces<<<nb, 256, 0, s>>>(D0, P, n, part);
-  k_feat_final<<<1, 32, 0, s>>>(part, nb, st, n, f);
+  k_feat_final<<<1, 256, 0, s>>>(part, nb, st, n, f);
   return cudaGetLastError();
 }
 

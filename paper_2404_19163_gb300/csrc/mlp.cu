@@ -113,20 +113,26 @@ extern "C" int zfact_mlp_backward(zfact_ctx* c, const float* params, const float
     return ctx_fail(c, ZFACT_ERR_ARG, "bad arguments");
   cudaSetDevice(c->device);
   int st = ZFACT_OK;
-  float* gs = (float*)ctx_buf(c, "mlp.gs", sizeof(float) * (size_t)batch * kMlpParams, &st);
-  if (!gs) return st;
-  double* ls = (double*)ctx_buf(c, "mlp.ls", sizeof(double) * ((size_t)batch + 1), &st);
+  const int nc = mlp_chunks(batch);
+  float* act = (float*)ctx_buf(c, "mlp.act", sizeof(float) * ((size_t)mlp_act_floats(batch) + (size_t)nc * kMlpParams),
+                               &st);
+  if (!act) return st;
+  float* part = act + mlp_act_floats(batch);
+  double* ls = (double*)ctx_buf(c, "mlp.ls", sizeof(double) * ((size_t)batch + nc + 1), &st);
   if (!ls) return st;
-  if ((st = ctx_cuda(c, klaunch(c, "mlp", 0, 0, 2, [&] {
+  double* lpart = ls + batch;
+  double* lmean = lpart + nc;
+  if ((st = ctx_cuda(c, klaunch(c, "mlp", 0, 0, 3, [&] {
                        cudaError_t e = launch_mlp(params, mean, stdv, x, batch, nullptr, target_scale, target_order,
-                                                  w_order, gs, ls, c->stream);
-                       if (e == cudaSuccess) e = launch_mlp_reduce(gs, batch, grad, ls, ls + batch, c->stream);
+                                                  w_order, act, ls, c->stream);
+                       if (e == cudaSuccess)
+                         e = launch_mlp_reduce(act, batch, part, ls, lpart, grad, lmean, c->stream);
                        return e;
                      }),
                      "mlp backward")))
     return st;
   double l = 0;
-  if ((st = ctx_cuda(c, cudaMemcpyAsync(&l, ls + batch, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss")))
+  if ((st = ctx_cuda(c, cudaMemcpyAsync(&l, lmean, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss")))
     return st;
   if ((st = ctx_cuda(c, cudaStreamSynchronize(c->stream), "mlp sync"))) return st;
   if (loss) *loss = l;
