@@ -771,8 +771,8 @@ def run_paper(args):
     """The paper's synthetic overlap (Sec. 5.1): S = (T + T^T)/2 shifted to lambda_min = 0.5,
     Z0 = S^{-1/2} + 0.005 U.  For every N, each method of Table I that the library offers runs from
     that Z0 under Algorithm 2's stop (Fig. 2): the (h)(h)+(h)(l)+(l)(h) split with and without the
-    FP64-accurate refinement, (h)(h) with and without a single-precision refinement step, single,
-    and double (N <= 4096).  Per method: iterations, the Frobenius history, the stop ratios
+    FP64-accurate refinement, (h)(h) with and without a single-precision refinement step, (h)(h)half
+    (FP16 accumulation), single, and double (N <= 4096).  Per method: iterations, the Frobenius history, the stop ratios
     Err_n / Err_{n-1}^3 (Fig. 1, Fig. 2 top), the FP64-accurate residual of the result and the time
     (Fig. 3), with cuSOLVER's eigh as the diagonalization comparator.  One JSON line."""
     import torch
@@ -784,6 +784,7 @@ def run_paper(args):
                ("split", dict(precision="fp16_split", refine_steps=0)),
                ("hh+refi_fp32", dict(precision="fp16", refine_mode="fp32", refine_steps=1)),
                ("hh", dict(precision="fp16", refine_steps=0)),
+               ("hh_half", dict(precision="fp16_half", refine_steps=0)),
                ("single", dict(precision="fp32")),
                ("double", dict(precision="fp64"))]
     rows = []

@@ -69,7 +69,10 @@ typedef enum zfact_precision {
     ZFACT_P_BF16 = 3,        /* "(h)(h)" with BF16 operands, FP32 accumulation (tcgen05) */
     ZFACT_P_FP16 = 4,        /* "(h)(h)" with FP16 operands (power-of-two scaled), FP32 accumulation */
     ZFACT_P_FP16_SPLIT = 5,  /* "(h)(h)+(h)(l)+(l)(h)": FP16 hi+lo split operands, FP32 accumulation */
-    ZFACT_P_BF16_SPLIT = 6   /* the same split with BF16 hi+lo */
+    ZFACT_P_BF16_SPLIT = 6,  /* the same split with BF16 hi+lo */
+    ZFACT_P_FP16_HALF = 7    /* "(h)(h)half": FP16 operands and FP16 accumulation (tcgen05 with an FP16
+                                accumulator); operands scaled by powers of two to at most 1 in
+                                magnitude so that sums of up to 65504 terms stay in FP16's range */
 } zfact_precision;
 
 /* How the refinement (Algorithm 3) forms d = I - Z^T S Z in FP64 accuracy. */
@@ -221,12 +224,14 @@ int zfact_kernel_stats(zfact_ctx* ctx, zfact_kstat* out, int cap, int* n, int re
 /* C = A B for N x N FP64 matrices with the operands rounded to the 16-bit format of
  * `precision` (BF16 / FP16 / the hi+lo splits; FP64 = plain FP64 product; FP32 = FP32 operands
  * and CUDA-core FP32 product, scales ignored) and FP32
- * tensor-core accumulation; C returned in FP64.  scale_a / scale_b are the power-of-two
+ * tensor-core accumulation (FP16_HALF: FP16 operands and an FP16 accumulator, rounded to FP16
+ * after every K = 16 step; the scaled partial sums must stay below 65504 in magnitude); C returned
+ * in FP64.  scale_a / scale_b are the power-of-two
  * factors applied before rounding (undone after).  DEVICE pointers. */
 int zfact_gemm(zfact_ctx* ctx, int precision, int64_t N, const double* A, double scale_a,
                const double* B, double scale_b, double* C);
 /* Eq. splitStyle: hi = R16[FP32[scale*A]], lo = R16[FP32[scale*A] - hi] elementwise for
- * n values, R16 the BF16 (precision = BF16/BF16_SPLIT) or FP16 rounding, round to nearest
+ * n values, R16 the BF16 (precision = BF16/BF16_SPLIT) or FP16 (FP16, FP16_SPLIT, FP16_HALF) rounding, round to nearest
  * even.  hi/lo are DEVICE arrays of n uint16 bit patterns. */
 int zfact_split(zfact_ctx* ctx, int precision, const double* A, int64_t n, double scale,
                 uint16_t* hi, uint16_t* lo);

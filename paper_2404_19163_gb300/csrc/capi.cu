@@ -295,8 +295,11 @@ static int check_common(zfact_ctx* c, const double* S, int64_t N, int order, int
   if (N < 1 || N > 65536) return ctx_fail(c, ZFACT_ERR_ARG, "N=%lld out of range [1, 65536]", (long long)N);
   if (order < 2 || order > 5) return ctx_fail(c, ZFACT_ERR_ARG, "order=%d out of range [2, 5]", order);
   if (precision != ZFACT_P_FP64 && precision != ZFACT_P_FP32 && precision != ZFACT_P_BF16 &&
-      precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT && precision != ZFACT_P_BF16_SPLIT)
+      precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT && precision != ZFACT_P_BF16_SPLIT &&
+      precision != ZFACT_P_FP16_HALF)
     return ctx_fail(c, ZFACT_ERR_ARG, "unknown precision %d", precision);
+  if (precision == ZFACT_P_FP16_HALF && N > 32768)
+    return ctx_fail(c, ZFACT_ERR_ARG, "an FP16 accumulator takes N <= 32768 (N=%lld)", (long long)N);
   return ZFACT_OK;
 }
 

@@ -184,12 +184,19 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor for kind::f16 with FP32 accumulation, both operands K-major.
-//   bits 4-5 D format (1 = F32), 7-9 A format, 10-12 B format (0 = F16, 1 = BF16),
-//   15/16 A/B major (0 = K), 17-22 N >> 3, 24-28 M >> 4.
-__host__ __device__ constexpr uint32_t idesc_f16(int m, int n, bool bf16) {
-  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(n >> 3) << 17) |
-         ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor for kind::f16, both operands K-major.
+//   bits 4-5 D format (1 = F32, 0 = F16), 7-9 A format, 10-12 B format (0 = F16, 1 = BF16),
+//   15/16 A/B major (0 = K), 17-22 N >> 3, 24-28 M >> 4.  An F16 accumulator takes F16 operands.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n, bool bf16, bool acc16 = false) {
+  return ((acc16 ? 0u : 1u) << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+         ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+// An FP16 accumulator occupies one 32-bit tensor-memory column per element, the value in the low 16
+// bits (column j holds D[:, j], as with FP32): widen what tmem_ld32 returned to FP32.
+__device__ __forceinline__ void widen_acc16(float (&v)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    v[i] = __half2float(__ushort_as_half((unsigned short)(__float_as_uint(v[i]) & 0xFFFFu)));
 }
 
 }  // namespace zf

@@ -191,17 +191,18 @@ __device__ float pow2_head(double bound, int headroom_log2) {
   return ldexpf(1.0f, p);
 }
 
-__global__ void k_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next) {
+// head: extra headroom (log2) of every scale; an FP16 accumulator takes operands scaled to at most 1
+__global__ void k_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next, int head) {
   if (op == 0) {
     if (idx < 0) idx = st->loop_iter + 1;  // device-driven loop, as in k_finish_err
     const double ad = (double)__uint_as_float(st->amaxf[1]);
     const double err = (idx >= 0 && idx < kHistMax) ? st->hist[idx] : ad;
-    st->scale[0] = pow2_head(ad, 0);
-    st->scale[1] = pow2_head((double)c1 * ad + (double)c2 * err * err, 0);
+    st->scale[0] = pow2_head(ad, head);
+    st->scale[1] = pow2_head((double)c1 * ad + (double)c2 * err * err, head);
   } else if (op == 1) {
-    st->scale[4] = pow2_head(st->amax[0] * st->amax[6], 0);
+    st->scale[4] = pow2_head(st->amax[0] * st->amax[6], head);
   } else if (op == 2) {
-    st->scale[zslot_next] = pow2_head(st->amax[6], 4);
+    st->scale[zslot_next] = pow2_head(st->amax[6], 4 + head);
   } else {
     st->amax[6] = (double)__uint_as_float(st->amaxf[2]);
   }
@@ -209,8 +210,9 @@ __global__ void k_fp16_scales(IterState* st, int op, int idx, float c1, float c2
 
 }  // namespace
 
-cudaError_t launch_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next, cudaStream_t s) {
-  k_fp16_scales<<<1, 1, 0, s>>>(st, op, idx, c1, c2, zslot_next);
+cudaError_t launch_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next, int head,
+                               cudaStream_t s) {
+  k_fp16_scales<<<1, 1, 0, s>>>(st, op, idx, c1, c2, zslot_next, head);
   return cudaGetLastError();
 }
 

@@ -556,13 +556,13 @@ __global__ void k_axpby64(double* out, double a, const double* X, double b, cons
     out[e] = a * X[e] + b * Y[e];
 }
 
-__global__ void k_pow2_slot(IterState* st, int amax_slot, int scale_slot) {
+__global__ void k_pow2_slot(IterState* st, int amax_slot, int scale_slot, int head) {
   const double bound = st->amax[amax_slot];
   float sc = 1.0f;
   if (bound > 0.0 && isfinite(bound)) {
     int e;
     frexp(bound, &e);
-    int p = 14 - e;
+    int p = 14 - head - e;
     p = p > 60 ? 60 : (p < -60 ? -60 : p);
     sc = ldexpf(1.0f, p);
   }
@@ -571,8 +571,8 @@ __global__ void k_pow2_slot(IterState* st, int amax_slot, int scale_slot) {
 
 }  // namespace
 
-cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, cudaStream_t s) {
-  k_pow2_slot<<<1, 1, 0, s>>>(st, amax_slot, scale_slot);
+cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, int head, cudaStream_t s) {
+  k_pow2_slot<<<1, 1, 0, s>>>(st, amax_slot, scale_slot, head);
   return cudaGetLastError();
 }
 

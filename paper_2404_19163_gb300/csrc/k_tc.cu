@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_f16(BM, BN, a.bf16 != 0);
+      const uint32_t idesc = idesc_f16(BM, BN, a.bf16 != 0, a.acc16 != 0);
       int it = 0, ui = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
@@ -575,6 +575,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       for (int c = half * CH; c < (half + 1) * CH; ++c) {
         float v[32];
         tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
+        if (a.acc16) widen_acc16(v);
         const int col0 = bn * BN + c * 32;
         if (a.sym && col0 + 31 < bm * BM) continue;  // chunk entirely below the diagonal block
         epi_chunk<EPI>(a, i, col0, v, ss, amax, osc, us, pl.group, pl.n, pl.row0, cd);

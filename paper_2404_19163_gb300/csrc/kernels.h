@@ -78,7 +78,8 @@ cudaError_t launch_cvt16_f32(const float* src, int n, int ld_src, uint16_t* hi, 
 //   op 1 (before K1): scale[4] (A^T) from amax[0] (Gershgorin row sum of S) * amax[6] (|Z|max)
 //   op 2 (before K4): scale[zslot_next] from 16 * amax[6]
 //   op 3 (after K4): amax[6] = amaxf[2] (|Z|max of the new iterate)
-cudaError_t launch_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next, cudaStream_t s);
+cudaError_t launch_fp16_scales(IterState* st, int op, int idx, float c1, float c2, int zslot_next, int head,
+                               cudaStream_t s);
 // Flat split of n values (zfact_split).
 cudaError_t launch_split_flat(const double* A, int64_t n, double scale, uint16_t* hi, uint16_t* lo, bool bf16,
                               cudaStream_t s);
@@ -196,7 +197,7 @@ cudaError_t launch_oz_combine(const float* G, size_t gstride, int ld32, int sl, 
 int resid_from_x_blocks(int n);
 int oz_combine_blocks(int n);  // partials written by launch_oz_combine in mode 2
 // st->scale[scale_slot] = power of two s with st->amax[amax_slot] * s <= 2^14.
-cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, cudaStream_t s);
+cudaError_t launch_pow2_slot(IterState* st, int amax_slot, int scale_slot, int head, cudaStream_t s);
 // D = I - X (FP64), per-block sums of D_ij^2 into partials.
 cudaError_t launch_resid_from_x(const double* X, double* D, int n, double* partials, cudaStream_t s);
 cudaError_t launch_axpby64(double* out, double a, const double* X, double b, const double* Y, size_t total,

@@ -284,7 +284,7 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
     for (int k = 1; k <= ord; ++k, dk *= (double)n * dmax) qmax += coef[k] * dk;
     // Q = c1 d + sum_{k>=2} c_k d^k: the linear term exact in FP64, the powers by FP16 hi/lo products
     if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
-                                  [&] { return launch_pow2_slot(c->st_dev, 1, 0, c->stream); }),
+                                  [&] { return launch_pow2_slot(c->st_dev, 1, 0, 0, c->stream); }),
                        "scale d")))
       return st;
     if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
@@ -301,7 +301,7 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
         if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 3, [&] {
                              cudaError_t e = launch_amax_f64(Pprev, n, c->st_dev, 4, c->stream);
                              if (e != cudaSuccess) return e;
-                             e = launch_pow2_slot(c->st_dev, 4, 4, c->stream);
+                             e = launch_pow2_slot(c->st_dev, 4, 4, 0, c->stream);
                              if (e != cudaSuccess) return e;
                              return launch_cvt16(Pprev, n, n, Pr.h, Pr.l, ld, 1.0, &c->st_dev->scale[4], false, false,
                                                  c->stream);
@@ -450,9 +450,14 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
                  const zfact_opts& o, int* iters_out, int* ridx_out, zfact_info* inf, bool cold) {
   const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
   const bool split = (precision == ZFACT_P_FP16_SPLIT || precision == ZFACT_P_BF16_SPLIT);
+  // (h)(h)half: FP16 operands and an FP16 accumulator in the bulk products
+  const bool half = precision == ZFACT_P_FP16_HALF;
   // FP16 has a 5-bit exponent: every FP16 operand carries a power-of-two scale (exact, so it
-  // changes no significand bit) chosen from a bound on its magnitude; BF16 needs none.
+  // changes no significand bit) chosen from a bound on its magnitude; BF16 needs none.  With an FP16
+  // accumulator the scales leave 14 more bits of headroom (operands at most 1, so a product's partial
+  // sums stay below its length, far from FP16's 65504, for N up to 32768).
   const bool scaled = !bf16;
+  const int head16 = half ? 14 : 0;
   IterState* sd = c->st_dev;
   auto sp = [&](int k) -> const float* { return scaled ? &sd->scale[k] : nullptr; };
   const int ld = round_up(n, 64);
@@ -511,9 +516,9 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
            // (which also resets the start scale: a caller's start_scale applies again)
            if (e == cudaSuccess && cold && o.start_scale > 0.0) e = launch_set_gscale(sd, o.start_scale, c->stream);
            if (e == cudaSuccess) e = launch_amax_f64(S, n, sd, kSlotS, c->stream);
-           if (e == cudaSuccess) e = launch_pow2_slot(sd, kSlotS, kSlotS, c->stream);
+           if (e == cudaSuccess) e = launch_pow2_slot(sd, kSlotS, kSlotS, head16, c->stream);
            if (e == cudaSuccess) e = launch_amax_f64(Za64, n, sd, 6, c->stream);
-           if (e == cudaSuccess) e = launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zc_slot, c->stream);
+           if (e == cudaSuccess) e = launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zc_slot, head16, c->stream);
            return e;
          })))
       return st;
@@ -545,9 +550,10 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   // loop counter + 1)
   auto residual = [&](int idx, int check_stop, Mat16* ztc, int zcs) -> int {
     int s2;
-    if (scaled && (s2 = elem("scale At", 1, [&] { return launch_fp16_scales(sd, 1, 0, 0.f, 0.f, 0, c->stream); })))
+    if (scaled && (s2 = elem("scale At", 1, [&] { return launch_fp16_scales(sd, 1, 0, 0.f, 0.f, 0, head16, c->stream); })))
       return s2;
     TcArgs k1 = tc_args(n, bf16);
+    k1.acc16 = half ? 1 : 0;
     k1.epi = kEpiStore16;
     k1.split_out = split;
     k1.o16h = At.h;
@@ -559,6 +565,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     if ((s2 = tc_product(c, k1, *ztc, S16, ld, bn))) return s2;
     cudaMemsetAsync(&sd->amaxf[1], 0, sizeof(unsigned int), c->stream);
     TcArgs k2 = tc_args(n, bf16);
+    k2.acc16 = half ? 1 : 0;
     k2.epi = kEpiResid;
     k2.sym = 1;
     k2.split_out = split;
@@ -583,7 +590,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     if (scaled) {
       // FP16: the scale of d needs its maximum, known only after the residual epilogue
       if ((s2 = elem("d16", 2, [&] {
-             cudaError_t e = launch_fp16_scales(sd, 0, idx, (float)coef[1], (float)coef[2], 0, c->stream);
+             cudaError_t e = launch_fp16_scales(sd, 0, idx, (float)coef[1], (float)coef[2], 0, head16, c->stream);
              if (e == cudaSuccess)
                e = launch_cvt16_f32(D32, n, ld, D16.h, D16.l, ld, false, false, sp(kSlotD), c->stream);
              return e;
@@ -612,7 +619,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
       return s2;
     if (scaled) {
       if ((s2 = elem("d16", 2, [&] {
-             cudaError_t e = launch_fp16_scales(sd, 0, 0, (float)coef[1], (float)coef[2], 0, c->stream);
+             cudaError_t e = launch_fp16_scales(sd, 0, 0, (float)coef[1], (float)coef[2], 0, head16, c->stream);
              if (e == cudaSuccess)
                e = launch_cvt16_f32(D32, n, ld, D16.h, D16.l, ld, false, false, sp(kSlotD), c->stream);
              return e;
@@ -630,6 +637,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
     Mat16* Pout = &Pa;
     for (int k = 2; k <= order; ++k) {
       TcArgs kp = tc_args(n, bf16);
+      kp.acc16 = half ? 1 : 0;
       kp.epi = kEpiPoly;
       kp.sym = 1;
       kp.split_out = split;
@@ -673,7 +681,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
                     int check) -> int {
     int s2;
     if ((s2 = polynomial(cold_update ? Q0 : nullptr))) return s2;
-    if (scaled && (s2 = elem("scale Z", 1, [&] { return launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zns, c->stream); })))
+    if (scaled && (s2 = elem("scale Z", 1, [&] { return launch_fp16_scales(sd, 2, 0, 0.f, 0.f, zns, head16, c->stream); })))
       return s2;
     cudaMemsetAsync(&sd->amaxf[2], 0, sizeof(unsigned int), c->stream);
     if (cold_update) {
@@ -684,6 +692,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
         return s2;
     } else {
       TcArgs k4 = tc_args(n, bf16);
+      k4.acc16 = half ? 1 : 0;
       k4.epi = kEpiZupd;
       k4.split_out = split;
       k4.f32 = Zm;
@@ -699,7 +708,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
       k4.amax_bits = &sd->amaxf[2];
       if ((s2 = tc_product(c, k4, *zc, Q16, ld, bn))) return s2;
     }
-    if (scaled && (s2 = elem("amax Z", 1, [&] { return launch_fp16_scales(sd, 3, 0, 0.f, 0.f, 0, c->stream); })))
+    if (scaled && (s2 = elem("amax Z", 1, [&] { return launch_fp16_scales(sd, 3, 0, 0.f, 0.f, 0, head16, c->stream); })))
       return s2;
     return residual(idx, check, ztn, zns);
   };

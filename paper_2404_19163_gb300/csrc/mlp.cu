@@ -37,7 +37,7 @@ static int features_device(zfact_ctx* c, const double* S, int n, float* f, doubl
                        cudaError_t e = launch_feat_rows(S, n, rows, rst, c->stream);
                        if (e == cudaSuccess) e = launch_feat_d0(S, n, rst, D0, c->stream);
                        if (e == cudaSuccess) e = launch_amax_f64(D0, n, sd, 7, c->stream);
-                       if (e == cudaSuccess) e = launch_pow2_slot(sd, 7, 7, c->stream);
+                       if (e == cudaSuccess) e = launch_pow2_slot(sd, 7, 7, 0, c->stream);
                        if (e == cudaSuccess)
                          e = launch_cvt16(D0, n, n, Dh, Dl, ld, 1.0, &sd->scale[7], false, false, c->stream);
                        return e;

@@ -47,7 +47,8 @@ extern "C" int zfact_gemm(zfact_ctx* c, int precision, int64_t N, const double* 
   }
   const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
   const bool split = (precision == ZFACT_P_FP16_SPLIT || precision == ZFACT_P_BF16_SPLIT);
-  if (!bf16 && precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT)
+  const bool half = precision == ZFACT_P_FP16_HALF;
+  if (!bf16 && !half && precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT)
     return ctx_fail(c, ZFACT_ERR_ARG, "unknown precision %d", precision);
   const int ld = (n + 63) / 64 * 64;
   const size_t bytes = (size_t)n * ld * sizeof(uint16_t);
@@ -71,6 +72,7 @@ extern "C" int zfact_gemm(zfact_ctx* c, int precision, int64_t N, const double* 
   memset(&a, 0, sizeof(a));
   a.M = a.N = a.K = n;
   a.bf16 = bf16;
+  a.acc16 = half ? 1 : 0;
   a.epi = kEpiF64;
   a.unscale = (float)(1.0 / (scale_a * scale_b));
   a.f64 = C;
@@ -86,7 +88,7 @@ extern "C" int zfact_split(zfact_ctx* c, int precision, const double* A, int64_t
   if (!A || !hi || !lo || n < 0) return ctx_fail(c, ZFACT_ERR_ARG, "bad arguments");
   if (n == 0) return ZFACT_OK;
   const bool bf16 = (precision == ZFACT_P_BF16 || precision == ZFACT_P_BF16_SPLIT);
-  if (!bf16 && precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT)
+  if (!bf16 && precision != ZFACT_P_FP16 && precision != ZFACT_P_FP16_SPLIT && precision != ZFACT_P_FP16_HALF)
     return ctx_fail(c, ZFACT_ERR_ARG, "split needs a 16-bit precision");
   cudaSetDevice(c->device);
   int st = ctx_cuda(c, launch_split_flat(A, n, scale, hi, lo, bf16, c->stream), "split");

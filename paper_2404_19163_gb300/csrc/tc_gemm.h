@@ -33,6 +33,7 @@ struct TcArgs {
   int epi;            // TcEpi
   int bf16;           // operand/output 16-bit format: 1 = BF16, 0 = FP16
   int split_out;      // write the lo part of 16-bit outputs too
+  int acc16;          // FP16 accumulator (kind::f16 with D format F16; FP16 operands only)
   float unscale;      // 1 / (scale_A * scale_B), a power of two
   const float* sa_ptr;     // device: extra A scale (unscale /= *sa_ptr), nullptr = none
   const float* sb_ptr;     // device: extra B scale

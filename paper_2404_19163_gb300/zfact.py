@@ -22,7 +22,7 @@ OK = 0
 ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_NONFINITE, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = 1, 2, 3, 4, 5, 6, 7
 WARN_NONCONTRACTIVE = 100
 
-PRECISION = {"fp64": 0, "fp32": 1, "bf16": 3, "fp16": 4, "fp16_split": 5, "bf16_split": 6}
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 3, "fp16": 4, "fp16_split": 5, "bf16_split": 6, "fp16_half": 7}
 REFINE_MODE = {"native": 0, "ozaki": 1, "fp32": 2}
 EMULATION = {"auto": 0, "slices": 1, "wide": 2}
 MLP_NPARAMS = 5573

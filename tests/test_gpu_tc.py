@@ -214,3 +214,44 @@ def test_unknown_refine_mode_rejected(ctx):
     with pytest.raises(ZfactError) as ei:
         ctx.refine(dev(S), None, order=2, precision="bf16", refine_mode=7)
     assert ei.value.code == 1
+
+
+@pytest.mark.parametrize("n", [64, 129, 256, 520])
+def test_gemm_fp16_accumulator(ctx, n):
+    """Table I's (h)(h)half: FP16 operands and an FP16 accumulator.  Against the oracle's FP64
+    product of the same FP16 operands the error is the accumulator's rounding: at most one FP16
+    rounding (relative 2^-11, absolute 2^-25 below FP16's normal range) of a partial sum bounded by
+    (|A16| |B16|)_ij after each K = 16 step and once at the end.  The FP32-accumulating product of
+    the same operands is far more accurate, which shows the accumulator really is FP16."""
+    g = np.random.default_rng(100 + n)
+    A = g.standard_normal((n, n))
+    B = g.standard_normal((n, n)) * 0.5
+    sa, sb = 2.0 ** -3, 2.0 ** -2   # scaled operands at most about 1
+    C = ctx.gemm(dev(A), dev(B), "fp16_half", sa, sb).cpu().numpy()
+    C32 = ctx.gemm(dev(A), dev(B), "fp16", sa, sb).cpu().numpy()
+    Ah, _ = oracle.split16(A, "fp16", sa)
+    Bh, _ = oracle.split16(B, "fp16", sb)
+    ref = oracle.mm16(Ah, Bh)
+    absp = np.abs(Ah).astype(np.float64) @ np.abs(Bh).astype(np.float64)
+    steps = -(-n // 16) + 2
+    bound = steps * (2.0 ** -11 * absp + 2.0 ** -25)
+    err = np.abs(C * (sa * sb) - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    err32 = np.abs(C32 * (sa * sb) - ref)
+    assert np.max(err) > 30 * np.max(err32), (float(np.max(err)), float(np.max(err32)))
+
+
+def test_fp16_half_bulk_contracts_and_refines(ctx):
+    """(h)(h)half bulk: Algorithm 2 contracts Err from the cold start and stops at a floor above
+    the FP32-accumulating (h)(h)'s; Algorithm 3's FP64-accurate refinement then reaches 1e-12."""
+    S = synth.cubic_overlap(n_side=8)
+    n = S.shape[0]
+    rh = ctx.refine(dev(S), None, order=2, precision="fp16_half", refine_steps=0)
+    r16 = ctx.refine(dev(S), None, order=2, precision="fp16", refine_steps=0)
+    bh = min(rh.hist[:rh.info["iters"] + 1])
+    b16 = min(r16.hist[:r16.info["iters"] + 1])
+    assert rh.info["iters"] >= 2 and bh < 1e-2 * rh.hist[0], rh.hist
+    assert bh > b16, (rh.hist, r16.hist)
+    r = ctx.refine(dev(S), None, order=2, precision="fp16_half", tol=1e-12, refine_steps=4)
+    _, e = oracle.residual(S, r.Z.cpu().numpy())
+    assert e / math.sqrt(n) <= 1e-12
