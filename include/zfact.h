@@ -271,10 +271,10 @@ int zfact_set_workspace_limit(zfact_ctx* ctx, int64_t bytes);
  * of the operands (rows rounded to T-bit fixed point, relative to the row's largest entry):
  *   ZFACT_EMU_AUTO (default): modular residues (Ozaki, Uchino, Imamura, "Ozaki Scheme II: A
  *     GEMM-oriented emulation of floating-point matrix multiplication using an integer modular
- *     technique", 2025): one BF16 tensor-core product per modulus (<= 127, pairwise coprime)
- *     and a Chinese-remainder reconstruction.  Twenty moduli (product just below 2^127) where the
- *     bound N 2^(T_A + T_B) on the integer product fits them, up to 31 (product just below 2^183,
- *     rows of up to 83 bits: an ill-conditioned Z) where it does not; error-free slices beyond;
+ *     technique", 2025): one BF16 tensor-core product per modulus (<= 256, pairwise coprime)
+ *     and a Chinese-remainder reconstruction.  Sixteen moduli (product about 2^125.4) where the
+ *     bound on the integer product fits them, up to 24 (product about 2^184.6, rows of up to
+ *     83 bits: an ill-conditioned Z) where it does not; error-free slices beyond;
  *   ZFACT_EMU_SLICES: error-free slices always (the Ozaki et al. 2012 scheme above);
  *   ZFACT_EMU_WIDE: the same as ZFACT_EMU_AUTO (kept for callers that asked for the wider moduli
  *     before they were part of the default).

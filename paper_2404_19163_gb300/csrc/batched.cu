@@ -462,8 +462,8 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
       rho_s[i] = oz_rho_from(hrho[i], n[i]);
       rho_z[i] = oz_rho_from(hrho[count + i], n[i]);
     }
-    // Grouped launches over all instances where the batch allows (sizes within one residue chunk, rows of
-    // at most 83 bits, residues rather than slices); else per-instance lanes.
+    // Grouped launches over all instances where the batch allows (rows of at most 83 bits, residues
+    // rather than slices); else per-instance lanes.
     bool grouped_done = false;
     if ((st = batched_grouped_residuals(c, count, n, order_idx, S, Z, slices, rho_s, rho_z, resid, &grouped_done)))
       return st;

@@ -65,7 +65,7 @@ int batched_grouped_residuals(zfact_ctx* c, int count, const std::vector<int>& n
   for (int j = 0; j < count; ++j) {
     const int i = order[j];
     T[i] = 6 * slices[i];
-    if (n[i] > chunk_kb * 64 || T[i] > 83) return ZFACT_OK;  // outside the grouped form: lanes
+    if (T[i] > 83) return ZFACT_OK;  // outside the grouped form: lanes
     bool w1 = false, w2 = false;
     const double b1 = oz_product_bits(T[i], T[i], rho_z[i], rho_s[i], n[i]);
     const double b2 = oz_product_bits(T[i], T[i], rho_z[i], -1.0, n[i]);
@@ -185,7 +185,7 @@ int batched_grouped_residuals(zfact_ctx* c, int count, const std::vector<int>& n
     b.s = c->lane_stream[l];
   }
 
-  // the plan of exactly k moduli: the twenty-moduli one where k fits it, else the wider set's
+  // the plan of exactly k moduli: the sixteen-moduli one where k fits it, else the wider set's
   struct Plans {
     CrtPlan p;
     crtw::Plan wp;
@@ -270,7 +270,8 @@ int batched_grouped_residuals(zfact_ctx* c, int count, const std::vector<int>& n
     a.oz_s = k;
     a.oz_diag = 1;
     a.oz_nch = 1;
-    a.oz_chunk_kb = chunk_kb;
+    a.oz_chunk_kb = (g.max_n + 63) / 64;  // every unit runs over its instance's whole K
+    a.oz_sub_kb = chunk_kb;               // in exact sub-chunks reduced in the epilogue
     a.oz_ra = g.rows;
     a.oz_rb = g.rows;
     a.ninst = g.cnt;

@@ -14,34 +14,32 @@
 
 namespace zf {
 
-constexpr int kCrtMax = 20;       // moduli available; their product is just below 2^127
-constexpr int kCrtMaxChunks = 4;  // K-chunks per reconstruction: their reduced sums stay below 2^9
-constexpr int kCrtMaxResidue = 63;  // largest |residue|: chunks of K <= 2^24 / 63^2 stay exact
+constexpr int kCrtMax = 16;        // moduli available; their product is just below 2^125.5
+constexpr int kCrtMaxChunks = 4;   // digit planes per reconstruction (K-chunks reduced outside the product)
+constexpr int kCrtMaxResidue = 128;  // largest |residue|: K-chunks of 2^24 / 128^2 = 1024 terms stay exact
+constexpr int kCrtSubKb = (1 << 24) / (kCrtMaxResidue * kCrtMaxResidue) / 64;  // 64-wide K-blocks per chunk
 
-// Pairwise coprime moduli, largest first: primes and prime powers up to 127, and 17 last so
-// that all twenty multiply to less than 2^127 (about 126.97 bits).
+// Pairwise coprime moduli up to 256, largest first: 2^8, then products of small primes and primes,
+// so that the first k carry about 7.9 bits each and all sixteen multiply to about 2^125.38 (below the
+// 2^127 the four-limb reconstruction takes).  Residues |r| <= 128 are exact in BF16 (8 significand bits).
 ZF_HD constexpr int crt_modulus(int i) {
   switch (i) {
-    case 0: return 127;
-    case 1: return 125;
-    case 2: return 121;
-    case 3: return 113;
-    case 4: return 109;
-    case 5: return 107;
-    case 6: return 103;
-    case 7: return 101;
-    case 8: return 97;
-    case 9: return 89;
-    case 10: return 83;
-    case 11: return 81;
-    case 12: return 79;
-    case 13: return 73;
-    case 14: return 71;
-    case 15: return 67;
-    case 16: return 64;
-    case 17: return 61;
-    case 18: return 59;
-    case 19: return 17;
+    case 0: return 256;
+    case 1: return 255;  // 3 5 17
+    case 2: return 253;  // 11 23
+    case 3: return 251;
+    case 4: return 247;  // 13 19
+    case 5: return 241;
+    case 6: return 239;
+    case 7: return 233;
+    case 8: return 229;
+    case 9: return 227;
+    case 10: return 223;
+    case 11: return 217;  // 7 31
+    case 12: return 211;
+    case 13: return 199;
+    case 14: return 197;
+    case 15: return 193;
     default: return 1;
   }
 }
@@ -146,10 +144,11 @@ ZF_HD inline void crt_parts(long long F, float (&a)[5]) {
 }
 
 // Symmetric residue of F modulo m from its first NP parts (NP = 4 when |F| < 2^56), in FP32:
-// x = sum_k a_k (2^(14k) mod m) is an integer below 2^22 (exact), x - m rint(x / m) is congruent to F,
-// and the float quotient errs by less than 0.04, so |r| < 0.55 m.  A second reduction of the same kind
-// brings r into [-m/2, m/2]: r / m is then known to 2^-22, and no integer r lies that close to m/2
-// except r = m/2 itself (m = 64), whose tie rint takes to 0.  So |r| <= (m-1)/2, or 32 for m = 64.  The
+// x = sum_k a_k (2^(14k) mod m), with |a_k| < 2^14 and the symmetric |2^(14k) mod m| <= 128, is an
+// integer below 5 2^21 < 2^24 in magnitude (exact); x - m rint(x / m) is congruent to F, and the float
+// quotient errs by less than 0.01, so |r| < 0.52 m.  A second reduction of the same kind brings r into
+// [-m/2, m/2]: r / m is then known to 2^-22, and no integer r lies that close to m/2 except r = m/2
+// itself (m = 256), whose tie rint takes to an even quotient.  So |r| <= 128 for every modulus.  The
 // second reduction keeps the fix-up on the FMA pipe (a compare-and-select would load the ALU pipe,
 // which the residue kernels already keep the busier).
 template <int NP = 5>
@@ -170,9 +169,9 @@ ZF_HD inline float crt_residue_f(const float (&a)[5], int m) {
 ZF_HD inline float crt_fmod_sym(float x, float m, float inv) { return fmaf(-m, crt_rint(x * inv), x); }
 
 // The CRT digit of an exact residue-product sum v (integer-valued float, |v| <= 2^24): y = (v mod m) w
-// mod m in [0, m), w = (M / m)^-1 mod m the plan's weight of this modulus.  |v mod m| <= 0.66 m <= 84
-// and w < 127, so the product stays an exact integer below 2^14, and its reduction errs by far less
-// than one step (|y| <= m / 2 before the shift into [0, m)).
+// mod m in [0, m), w = (M / m)^-1 mod m the plan's weight of this modulus.  |v mod m| <= 0.66 m <= 169
+// and w < 256, so the product stays an exact integer below 2^16, and its second reduction leaves
+// |y| <= 0.66 m, which the shift of negative values by m takes into [0, m).
 ZF_HD inline float crt_digit(float v, float m, float inv, float w) {
   float y = crt_fmod_sym(crt_fmod_sym(v, m, inv) * w, m, inv);
   return y < 0.0f ? y + m : y;
@@ -190,7 +189,7 @@ struct CrtPlan {
   unsigned M[4];
 };
 
-// Accumulates sum_i y_i P_i (y_i congruent to (C mod m_i) w_i modulo m_i, y_i < 2^9) per 32-bit limb
+// Accumulates sum_i y_i P_i (y_i congruent to (C mod m_i) w_i modulo m_i, y_i < 2^10) per 32-bit limb
 // without carries (each limb sum stays below 2^46) and sum_i y_i / m_i in FP32.  That sum equals q + C / M for
 // an integer q; with |C| < M / 4 and an FP32 error far below 1/4, q = round(sum) and
 // C = sum_i y_i P_i - q M, formed modulo 2^128 (exact, since |C| < 2^125).
@@ -201,9 +200,9 @@ struct CrtAcc {
     L[0] = L[1] = L[2] = L[3] = 0ull;
     S = 0.0f;
   }
-  // Adds a sum y of CRT digits of modulus t (one per K-chunk, each in [0, m_t), so y < 2^9).  The
+  // Adds a sum y of CRT digits of modulus t (one per digit plane, each in [0, m_t), so y < 2^10).  The
   // digits need no reduction: any y congruent to (C mod m_t) w_t gives sum_t y_t P_t = C (mod M), and
-  // sum_t y_t / m_t is still q + C / M for an integer q (below 2^10 here, far from FP32's limits).
+  // sum_t y_t / m_t is still q + C / M for an integer q (below 2^7 here, far from FP32's limits).
   ZF_HD void add_y(const CrtPlan& p, int t, unsigned y) {
     S = fmaf(crt_u2f(y), p.inv[t], S);
     for (int l = 0; l < 4; ++l) L[l] += (unsigned long long)y * p.P[t][l];
@@ -226,7 +225,7 @@ struct CrtAcc {
   }
 };
 
-// The moduli count that makes M = m_0 ... m_{k-1} exceed 2^bits (0 if all twenty do not), with
+// The moduli count that makes M = m_0 ... m_{k-1} exceed 2^bits (0 if all sixteen do not), with
 // the reconstruction constants.
 inline int crt_plan(double bits, CrtPlan* p) {
   unsigned __int128 M = 1;

@@ -1,8 +1,8 @@
-// Wider CRT arithmetic for residue products whose bound passes the twenty moduli of crt.h:
-// up to 31 pairwise coprime moduli (M below 2^183) in six 32-bit limbs, and fixed-point rows of
-// up to 84 bits as six 14-bit parts.  The first twenty moduli are crt.h's, in the same order,
-// so a plan of at most twenty moduli is the same plan.  Every modulus is at most 127, so the
-// residues, the K-chunk length (4224) and the FP32 reductions are those of crt.h.
+// Wider CRT arithmetic for residue products whose bound passes the sixteen moduli of crt.h:
+// up to 24 pairwise coprime moduli (M below 2^184.7) in six 32-bit limbs, and fixed-point rows of
+// up to 84 bits as six 14-bit parts.  The first sixteen moduli are crt.h's, in the same order,
+// so a plan of at most sixteen moduli is the same plan.  Every modulus is at most 256, so the
+// residues, the K-chunk length (1024) and the FP32 reductions are those of crt.h.
 //
 // Used by the residue kernels of k_ozmod_wide.cu (residues) and k_ozmod.cu (reconstruction); the
 // arithmetic is checked on the host against exact big-integer products (tests/test_crt_host.py).
@@ -12,25 +12,22 @@
 namespace zf {
 namespace crtw {
 
-constexpr int kMax = 31;    // moduli
+constexpr int kMax = 24;    // moduli
 constexpr int kLimbs = 6;   // 32-bit limbs of M and of the digit sums
 constexpr int kParts = 6;   // 14-bit parts of a fixed-point row value (|F| <= 2^84)
 
-// crt.h's twenty moduli, then the primes and prime powers left below 64 that are coprime to them.
+// crt.h's sixteen moduli, then the next primes below 193 (coprime to all of them).
 ZF_HD constexpr int modulus(int i) {
   if (i < kCrtMax) return crt_modulus(i);
   switch (i) {
-    case 20: return 53;
-    case 21: return 49;
-    case 22: return 47;
-    case 23: return 43;
-    case 24: return 41;
-    case 25: return 37;
-    case 26: return 31;
-    case 27: return 29;
-    case 28: return 23;
-    case 29: return 19;
-    case 30: return 13;
+    case 16: return 191;
+    case 17: return 181;
+    case 18: return 179;
+    case 19: return 173;
+    case 20: return 167;
+    case 21: return 163;
+    case 22: return 157;
+    case 23: return 151;
     default: return 1;
   }
 }
@@ -65,8 +62,8 @@ ZF_HD inline void parts(unsigned long long mag_hi, unsigned long long mag_lo, bo
 }
 
 // Symmetric residue of F modulo m from its six parts: x = sum_k a_k (2^(14k) mod m) stays below
-// 2^23 in magnitude (exact in FP32); the rest is crt_residue_f's two reductions (the first leaves
-// |r| < 0.58 m for m >= 13, the second brings it into [-m/2, m/2]).
+// 6 2^21 < 2^24 in magnitude (exact in FP32); the rest is crt_residue_f's two reductions (the first
+// leaves |r| < 0.52 m, the second brings it into [-m/2, m/2]).
 ZF_HD inline float residue_f(const float (&a)[kParts], int m) {
   const float fm = (float)m;
   float x = a[kParts - 1] * (float)crt_pow2_sym(m, 14 * (kParts - 1));
@@ -85,8 +82,8 @@ struct Plan {
   unsigned M[kLimbs];
 };
 
-// sum_t y_t P_t per 32-bit limb (each limb sum below 2^44) and sum_t y_t / m_t in FP32 (error far
-// below 1/4 for 31 terms); C = sum_t y_t P_t - q M modulo 2^192, exact while |C| < M / 4 < 2^181.
+// sum_t y_t P_t per 32-bit limb (each limb sum below 2^47) and sum_t y_t / m_t in FP32 (error far
+// below 1/4 for 24 terms); C = sum_t y_t P_t - q M modulo 2^192, exact while |C| < M / 4 < 2^183.
 struct Acc {
   unsigned long long L[kLimbs];
   float S;
@@ -94,8 +91,8 @@ struct Acc {
     for (int l = 0; l < kLimbs; ++l) L[l] = 0ull;
     S = 0.0f;
   }
-  // A sum y of CRT digits of modulus t (see CrtAcc::add_y): below 2^9, so every limb sum stays
-  // below 2^46 over 31 moduli.
+  // A sum y of CRT digits of modulus t (see CrtAcc::add_y): below 2^10, so every limb sum stays
+  // below 2^47 over 24 moduli.
   ZF_HD void add_y(const Plan& p, int t, unsigned y) {
     S = fmaf(crt_u2f(y), p.inv[t], S);
     for (int l = 0; l < kLimbs; ++l) L[l] += (unsigned long long)y * p.P[t][l];
@@ -127,7 +124,7 @@ struct Acc {
   }
 };
 
-// The moduli count that makes M exceed 2^bits (0 if all 31 do not), with the constants.  M and
+// The moduli count that makes M exceed 2^bits (0 if all 24 do not), with the constants.  M and
 // M / m_i are formed in 32-bit limbs (products and quotients by small integers only).
 inline int plan(double bits, Plan* p) {
   unsigned M[kLimbs + 1] = {1u};

@@ -133,7 +133,7 @@ double oz_rho_from(unsigned int rho2_bits, int n);
 // of one residue chunk.
 double oz_product_bits(int TA, int TB, double rhoA, double rhoB, int n);
 int oz_moduli_count(const zfact_ctx* c, int TA, int TB, double bits, int* wide);
-int oz_crt_chunk_kb();
+int oz_crt_chunk_kb();  // K-blocks of one exact FP32 residue-product sum
 int oz_update_slices(int n, double q);
 int oz_update_bits(int n, double q);
 int oz_congruence(zfact_ctx* c, const double* H, const double* Z, double* out, int n);

@@ -5,12 +5,13 @@
 // Every row r of an FP64 operand is scaled by 2^(T - e_r) (e_r: the row's exponent bound) and
 // rounded to an integer F with |F| <= 2^T.  The product C' = F_A F_B^T of two such integer
 // matrices is exact and bounded by K 2^(T_A + T_B).  It is formed modulo pairwise coprime
-// moduli m_i <= 127: the symmetric residues of F (|r| <= 63) are exact in BF16, one residue
-// product over K <= 4224 terms stays an integer below 2^24 (exact in the FP32 accumulator), and
+// moduli m_i <= 256: the symmetric residues of F (|r| <= 128) are exact in BF16, a residue
+// product over K <= 1024 terms stays an integer of at most 2^24 (exact in the FP32 accumulator;
+// longer products are reduced modulo m_i every 1024 terms inside the product's epilogue), and
 // the Chinese remainder theorem recovers C' from its residues once M = prod m_i > 4 |C'|.  The
 // result is C_ij = 2^(eA_i + eB_j - T_A - T_B) C'_ij: the only errors are the two roundings to
 // T-bit fixed point and the final conversion to FP64.  The moduli count grows linearly with the
-// bits kept (about 6.4 bits per product), where slicing grows quadratically (s(s+1)/2 pairs).
+// bits kept (about 7.9 bits per product), where slicing grows quadratically (s(s+1)/2 pairs).
 #include <math.h>
 
 #include "crt_wide.h"
@@ -45,7 +46,7 @@ __device__ __forceinline__ long long fixed_point_m(double x, int e, int T) {
 }
 
 // The residues of an element pair for moduli I.. (compile-time moduli, FP32 arithmetic of
-// crt_residue_f), each pair packed as two BF16 into one 4-byte store (an integer |r| <= 63
+// crt_residue_f), each pair packed as two BF16 into one 4-byte store (an integer |r| <= 128
 // has its low 16 FP32 bits zero, so the BF16 value is the upper half).
 template <int I, int NP>
 __device__ __forceinline__ void residues_pair_all(const float (&p0)[5], const float (&p1)[5], int nmod, uint16_t* o,

@@ -1,6 +1,6 @@
 // Wider CRT residue products (crt_wide.h): rows of up to 83 bits kept as 128-bit fixed point, up to
-// 31 moduli, six-limb reconstruction.  Used by the default scheme for products whose bound passes
-// the twenty moduli of k_ozmod.cu (an ill-conditioned Z, whose residual asks for 60 to 83 bits per
+// 24 moduli, six-limb reconstruction.  Used by the default scheme for products whose bound passes
+// the sixteen moduli of k_ozmod.cu (an ill-conditioned Z, whose residual asks for 60 to 83 bits per
 // row).  Same layouts as k_ozmod.cu, whose reconstruction kernel
 // takes the wider plan too.
 #include <math.h>

@@ -368,8 +368,8 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
       break;
     }
     case kEpiCrt8: {
-      // the accumulator is an exact integer below 2^24 (residues <= 63 over K-chunks of 4224); its
-      // CRT digit in [0, m) < 2^7 is all the reconstruction needs from this product
+      // v is an exact integer of at most 2^24 in magnitude (the sub-chunk residue sums of the unit,
+      // each reduced modulo m); its CRT digit in [0, m) < 2^8 is all the reconstruction needs
       uint32_t w[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -499,15 +499,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
         const UnitPlan pl = plan_unit<BN>(u, a, kblocks);
         if (pl.skip) continue;
-        const int buf = ui & 1;
-        const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
-        ++ui;
-        if (!mbar_wait(&tempty[buf], uph ^ 1u, a.err_flag, 2)) break;
-        tc_fence_after();
-        const uint32_t dtm = tmem_base + (uint32_t)(buf * BN);
-        uint32_t acc = 0;
+        // the residue products hand the accumulator to the epilogue every `sub` K-blocks (an exact
+        // FP32 sum of at most that many blocks), each time in the other tensor-memory buffer
+        const int sub = (EPI == kEpiCrt8 && a.oz_sub_kb > 0) ? a.oz_sub_kb : (1 << 30);
+        int buf = 0, done_kb = 0;
+        uint32_t dtm = 0, acc = 0;
+        auto take_buffer = [&]() -> bool {
+          buf = ui & 1;
+          const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
+          ++ui;
+          if (!mbar_wait(&tempty[buf], uph ^ 1u, a.err_flag, 2)) return false;
+          tc_fence_after();
+          dtm = tmem_base + (uint32_t)(buf * BN);
+          acc = 0;
+          return true;
+        };
+        if (!take_buffer()) break;
         for (int pi = 0; pi < pl.npairs && ok; ++pi) {
           for (int kb = pl.kb0; kb < pl.kb1; ++kb, ++it) {
+            if (done_kb == sub) {
+              tc_commit(&tfull[buf]);
+              if (!take_buffer()) {
+                ok = false;
+                break;
+              }
+              done_kb = 0;
+            }
+            ++done_kb;
             const int st = it % C::STAGES;
             const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
             if (!mbar_wait(&full[st], ph, a.err_flag, 3)) {
@@ -544,52 +562,114 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc_gemm(const __grid_constant__
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
       const UnitPlan pl = plan_unit<BN>(u, a, kblocks);
       if (pl.skip) continue;
-      const int buf = ui & 1;
-      const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
-      ++ui;
-      if (!mbar_wait(&tfull[buf], uph, a.err_flag, 5)) break;
-      tc_fence_after();
-      int bm, bn;
-      decode_unit(pl.tile, a, pl.n, BN, bm, bn);
-      const int i = bm * BM + q * 32 + lane;
-      double ss = 0.0;
-      CrtDigitConst cd{1.0f, 1.0f, 0.0f};
       if constexpr (EPI == kEpiCrt8) {
+        // the unit's accumulator arrives in sub-chunks (as many as the MMA issuer hands over); each
+        // exact FP32 sum is reduced modulo m and added, in 16-bit halves of one int per column pair
+        // (|sum| <= 0.66 m per sub-chunk, 64 sub-chunks at most for N <= 65536, so below 2^14 each),
+        // to the running residue sum the digit is formed from
+        const int sub = a.oz_sub_kb > 0 ? a.oz_sub_kb : (1 << 30);
+        const int total_kb = pl.npairs * (pl.kb1 - pl.kb0);
+        const int nsub = (int)(((long long)total_kb + sub - 1) / sub);
+        int bm, bn;
+        decode_unit(pl.tile, a, pl.n, BN, bm, bn);
+        const int i = bm * BM + q * 32 + lane;
+        CrtDigitConst cd;
         cd.m = (float)crtw::modulus(pl.t);
         cd.inv = 1.0f / cd.m;
+        cd.w = 0.0f;
 #pragma unroll
         for (int t = 0; t < 32; ++t)
           if (t == pl.t) cd.w = a.crt_w[t];
-      }
-      if constexpr (EPI == kEpiPoly || EPI == kEpiZupd) {
-        // the FP32 input row segments of this half (one 128-byte line per chunk) into L1 ahead of use
-        const float* src = (EPI == kEpiPoly) ? a.f32_in : a.f32;
-        if (src && i < (a.ninst > 0 ? pl.n : a.M)) {
-          const float* r = src + ((size_t)pl.row0 + i) * a.ld32 + (size_t)bn * BN + half * CH * 32;
+        int racc[CH][16];
 #pragma unroll
-          for (int c = 0; c < CH; ++c)
-            if (bn * BN + (half * CH + c) * 32 < pl.n) asm volatile("prefetch.global.L1 [%0];" ::"l"(r + c * 32));
+        for (int cc = 0; cc < CH; ++cc)
+#pragma unroll
+          for (int p2 = 0; p2 < 16; ++p2) racc[cc][p2] = 0;
+        bool got = true;
+        for (int sc = 0; sc < nsub; ++sc) {
+          const int buf = ui & 1;
+          const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
+          ++ui;
+          if (!mbar_wait(&tfull[buf], uph, a.err_flag, 5)) {
+            got = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int cc = 0; cc < CH; ++cc) {
+            const int c = half * CH + cc;
+            if (a.sym && bn * BN + c * 32 + 31 < bm * BM) continue;  // chunk entirely below the diagonal
+            float v[32];
+            tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
+#pragma unroll
+            for (int p2 = 0; p2 < 16; ++p2) {
+              const int r0 = (int)crt_fmod_sym(v[2 * p2], cd.m, cd.inv);
+              const int r1 = (int)crt_fmod_sym(v[2 * p2 + 1], cd.m, cd.inv);
+              racc[cc][p2] += r1 * 65536 + r0;
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty[buf]);
         }
-      }
-#pragma unroll 1
-      for (int c = half * CH; c < (half + 1) * CH; ++c) {
-        float v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
-        if (a.acc16) widen_acc16(v);
-        const int col0 = bn * BN + c * 32;
-        if (a.sym && col0 + 31 < bm * BM) continue;  // chunk entirely below the diagonal block
-        epi_chunk<EPI>(a, i, col0, v, ss, amax, osc, us, pl.group, pl.n, pl.row0, cd);
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[buf]);
-      if constexpr (EPI == kEpiResid) {
-        // fixed-order warp reduction; one partial per (tile, quadrant, half), summed in order later
+        if (!got) break;
+        double ss_unused = 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        const size_t pidx = a.ninst > 0 ? (size_t)a.g_part0[pl.inst] + (size_t)pl.tile * kTcPartsPerTile
-                                        : (size_t)u * kTcPartsPerTile;
-        if (lane == 0) a.partials[pidx + half * 4 + q] = ss;
+        for (int cc = 0; cc < CH; ++cc) {
+          const int c = half * CH + cc;
+          const int col0 = bn * BN + c * 32;
+          if (a.sym && col0 + 31 < bm * BM) continue;
+          float v[32];
+#pragma unroll
+          for (int p2 = 0; p2 < 16; ++p2) {
+            const int lo16 = (int)(short)(racc[cc][p2] & 0xFFFF);
+            v[2 * p2] = (float)lo16;
+            v[2 * p2 + 1] = (float)((racc[cc][p2] - lo16) >> 16);
+          }
+          epi_chunk<EPI>(a, i, col0, v, ss_unused, amax, osc, us, pl.group, pl.n, pl.row0, cd);
+        }
+        continue;
+      } else {
+        const int buf = ui & 1;
+        const uint32_t uph = (uint32_t)(ui >> 1) & 1u;
+        ++ui;
+        if (!mbar_wait(&tfull[buf], uph, a.err_flag, 5)) break;
+        tc_fence_after();
+        int bm, bn;
+        decode_unit(pl.tile, a, pl.n, BN, bm, bn);
+        const int i = bm * BM + q * 32 + lane;
+        double ss = 0.0;
+        const CrtDigitConst cd{1.0f, 1.0f, 0.0f};
+        if constexpr (EPI == kEpiPoly || EPI == kEpiZupd) {
+          // the FP32 input row segments of this half (one 128-byte line per chunk) into L1 ahead of use
+          const float* src = (EPI == kEpiPoly) ? a.f32_in : a.f32;
+          if (src && i < (a.ninst > 0 ? pl.n : a.M)) {
+            const float* r = src + ((size_t)pl.row0 + i) * a.ld32 + (size_t)bn * BN + half * CH * 32;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+              if (bn * BN + (half * CH + c) * 32 < pl.n) asm volatile("prefetch.global.L1 [%0];" ::"l"(r + c * 32));
+          }
+        }
+#pragma unroll 1
+        for (int c = half * CH; c < (half + 1) * CH; ++c) {
+          float v[32];
+          tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + c * 32), v);
+          if (a.acc16) widen_acc16(v);
+          const int col0 = bn * BN + c * 32;
+          if (a.sym && col0 + 31 < bm * BM) continue;  // chunk entirely below the diagonal block
+          epi_chunk<EPI>(a, i, col0, v, ss, amax, osc, us, pl.group, pl.n, pl.row0, cd);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if constexpr (EPI == kEpiResid) {
+          // fixed-order warp reduction; one partial per (tile, quadrant, half), summed in order later
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+          const size_t pidx = a.ninst > 0 ? (size_t)a.g_part0[pl.inst] + (size_t)pl.tile * kTcPartsPerTile
+                                          : (size_t)u * kTcPartsPerTile;
+          if (lane == 0) a.partials[pidx + half * 4 + q] = ss;
+        }
       }
     }
     if (a.amax_bits) {

@@ -19,11 +19,12 @@ constexpr int kOzBits = 6;             // bits per slice
 constexpr int kOzSlicesResid = 9;      // 54 bits: residual products of a well-scaled Z
 constexpr int kOzSlicesUpdateMin = 4;  // 24 bits: the least Z Q is formed with (see oz_update_slices)
 constexpr int kOzSlicesMax = 14;
-// Target bytes of group partials (slices) or digits (CRT) per launch: K-chunks are batched up to it.  One
-// K-chunk of every group or modulus is the least a launch holds, so a product may exceed it: the CRT digits
-// of one chunk take k N^2 bytes (up to 8.3 GB for 31 moduli at N = 16384), the FP32 partials of one slicing
-// chunk 4 s N^2 bytes (up to 15 GB for 14 slices at N = 16384); both fit GB300's HBM many times over, and a
-// workspace cap (zfact_set_workspace_limit) turns them into ZFACT_ERR_NOMEM before anything is allocated.
+// Target bytes of the slicing products' group partials per launch: K-chunks are batched up to it.  One
+// K-chunk of every group is the least a launch holds, so a product may exceed it: the FP32 partials of one
+// slicing chunk take 4 s N^2 bytes (up to 15 GB for 14 slices at N = 16384).  The CRT products keep one digit
+// plane per modulus whatever K is, k N^2 bytes (6.4 GB for 24 moduli at N = 16384).  Both fit GB300's HBM
+// many times over, and a workspace cap (zfact_set_workspace_limit) turns them into ZFACT_ERR_NOMEM before
+// anything is allocated.
 constexpr size_t kOzGBudget = (size_t)6 << 30;
 
 struct OzOperand {
@@ -34,8 +35,6 @@ struct OzOperand {
   int wide = 0;         // residues modulo the wider moduli of crt_wide.h
 };
 
-// K-blocks per residue chunk: |residue| <= 63, so a chunk of K terms sums below K 63^2 <= 2^24.
-constexpr int kCrtChunkKb = (int)((1 << 24) / (kCrtMaxResidue * kCrtMaxResidue) / 64);
 
 int ld16_of(int n) { return (n + 63) / 64 * 64; }
 int rp_of(int n) { return (n + 255) / 256 * 256; }
@@ -89,7 +88,7 @@ double oz_prod_bits(int TA, int TB, double rhoA, double rhoB, int n) {
   return b < worst ? b : worst;
 }
 
-// Moduli for a product of `bits`: the twenty of crt.h where they suffice, else the wider ones
+// Moduli for a product of `bits`: the sixteen of crt.h where they suffice, else the wider ones
 // (*wide = 1), else 0 (the product needs slices).
 int oz_moduli_for(const zfact_ctx* c, int TA, int TB, double bits, int* wide) {
   *wide = 0;
@@ -119,7 +118,7 @@ double oz_product_bits(int TA, int TB, double rhoA, double rhoB, int n) { return
 int oz_moduli_count(const zfact_ctx* c, int TA, int TB, double bits, int* wide) {
   return oz_moduli_for(c, TA, TB, bits, wide);
 }
-int oz_crt_chunk_kb() { return kCrtChunkKb; }
+int oz_crt_chunk_kb() { return kCrtSubKb; }
 
 namespace {
 
@@ -139,7 +138,7 @@ int oz_make_mod(zfact_ctx* c, const char* name, const double* X, int n, int ldx,
   op->s = nmod;
   op->T = T;
   op->nmod = nmod;
-  // the twenty-moduli kernel holds rows of up to 62 bits; wider rows or more planes take the wide one
+  // the sixteen-moduli kernel holds rows of up to 62 bits; wider rows or more planes take the wide one
   // (both write the same residues of the same fixed-point rows)
   wide = (wide || T > 62 || nmod > kCrtMax) ? 1 : 0;
   op->wide = wide;
@@ -165,8 +164,8 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
   int st = ZFACT_OK;
   CrtPlan plan;
   crtw::Plan wplan;
-  // the first k moduli whose product exceeds 2^bits: crt.h's twenty where they suffice, else the wider
-  // moduli (the same twenty first); the operands hold at least k residue planes
+  // the first k moduli whose product exceeds 2^bits: crt.h's sixteen where they suffice, else the wider
+  // moduli (the same sixteen first); the operands hold at least k residue planes
   bool wide = false;
   int k = crt_plan(bits, &plan);
   if (k < 1) {
@@ -177,13 +176,10 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
     return ctx_fail(c, ZFACT_ERR_ARG, "residue operands do not match (%d, %d, %d moduli)", k, A.nmod, B.nmod);
   const int ld = ld16_of(n);
   const int kblocks = (n + 63) / 64;
-  const int nch_total = (kblocks + kCrtChunkKb - 1) / kCrtChunkKb;
-  const size_t slot_bytes = (size_t)n * ld;  // one digit plane
-  int nch_b = (int)(kOzGBudget / (slot_bytes * k));
-  if (nch_b < 1) nch_b = 1;
-  if (nch_b > kCrtMaxChunks) nch_b = kCrtMaxChunks;
-  if (nch_b > nch_total) nch_b = nch_total;
-  uint8_t* G = (uint8_t*)ctx_buf(c, lane_name(c, "oz.G").c_str(), slot_bytes * k * nch_b, &st);
+  // one digit plane per modulus: every unit runs over all of K, its exact FP32 sums of kCrtSubKb
+  // K-blocks reduced modulo m and summed in the epilogue
+  const size_t slot_bytes = (size_t)n * ld;
+  uint8_t* G = (uint8_t*)ctx_buf(c, lane_name(c, "oz.G").c_str(), slot_bytes * k, &st);
   if (!G) return st;
   TcMaps maps;
   memset(&maps, 0, sizeof(maps));
@@ -191,59 +187,53 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
   int r1 = ctx_make_map(c, &maps.a[0], A.sl, k * A.Rp, n, ld, 128, true);
   int r2 = ctx_make_map(c, &maps.b[0], B.sl, k * B.Rp, n, ld, bn, true);
   if (r1 || r2) return ctx_fail(c, ZFACT_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d, %d)", r1, r2);
-  for (int c0 = 0; c0 < nch_total; c0 += nch_b) {
-    const int nch = (nch_total - c0) < nch_b ? (nch_total - c0) : nch_b;
-    TcArgs a;
-    memset(&a, 0, sizeof(a));
-    a.M = a.N = a.K = n;
-    a.nseg = 1;
-    a.sym = sym ? 1 : 0;
-    a.epi = kEpiCrt8;
-    a.bf16 = 1;
-    a.unscale = 1.0f;
-    a.d8 = G;
-    a.ld32 = ld;
-    a.g_stride = (size_t)n * ld;
-    for (int t = 0; t < k; ++t) a.crt_w[t] = wide ? wplan.fw[t] : plan.fw[t];
-    a.oz_s = k;
-    a.oz_diag = 1;
-    a.oz_nch = nch;
-    a.oz_chunk_kb = kCrtChunkKb;
-    a.oz_c0 = c0;
-    a.oz_ra = A.Rp;
-    a.oz_rb = B.Rp;
-    a.oz_tiles = tc_num_units(a, bn) / (k * nch);
-    a.err_flag = &c->st_dev->error;
-    // algorithmic work: k residue products over this launch's share of K
-    const int kb_lo = c0 * kCrtChunkKb,
-              kb_hi = (c0 + nch) * kCrtChunkKb < kblocks ? (c0 + nch) * kCrtChunkKb : kblocks;
-    const double kk = (double)(kb_hi - kb_lo) * 64.0 < n ? (double)(kb_hi - kb_lo) * 64.0 : (double)n;
-    const double flops = k * 2.0 * n * n * kk * (sym ? 0.5 : 1.0);
-    const double bytes = k * 2.0 * 2.0 * n * kk + 1.0 * k * nch * (double)n * n * (sym ? 0.5 : 1.0);
-    kstat_note(c, "fp64_equiv", flops / k);
-    if ((st = ctx_cuda(c, klaunch(c, "tc_gemm.crt", flops, bytes, 1,
-                                  [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, cur_stream(c)); }),
-                       "tcgen05 residue products")))
-      return st;
-    int md = (c0 == 0) ? mode : 1;
-    const bool fuse = partials && fused_resid && sym && c0 == 0 && nch == nch_total;
-    if (fuse) {
-      md = 2;
-      *fused_resid = true;
-      if (nparts) *nparts = ozm_combine_blocks(n);
-    }
-    // digits read (the upper triangle when sym), FP64 result written (read too when accumulating)
-    const double cbytes = (1.0 * k * nch * n * (double)n + (md == 1 ? 16.0 : 8.0) * n * n) * (sym ? 0.5 : 1.0);
-    if ((st = ctx_cuda(c, klaunch(c, wide ? "oz_crt.wide" : "oz_crt", 0, cbytes, 1, [&] {
-                         if (wide)
-                           return launch_ozmw_combine8(G, (size_t)n * ld, ld, nch, wplan, A.e, B.e, A.T, B.T, n, out,
-                                                       ld64, md, sym, partials, cur_stream(c));
-                         return launch_ozm_combine8(G, (size_t)n * ld, ld, nch, plan, A.e, B.e, A.T, B.T, n, out, ld64,
-                                                    md, sym, partials, cur_stream(c));
-                       }),
-                       "oz crt combine")))
-      return st;
+  TcArgs a;
+  memset(&a, 0, sizeof(a));
+  a.M = a.N = a.K = n;
+  a.nseg = 1;
+  a.sym = sym ? 1 : 0;
+  a.epi = kEpiCrt8;
+  a.bf16 = 1;
+  a.unscale = 1.0f;
+  a.d8 = G;
+  a.ld32 = ld;
+  a.g_stride = (size_t)n * ld;
+  for (int t = 0; t < k; ++t) a.crt_w[t] = wide ? wplan.fw[t] : plan.fw[t];
+  a.oz_s = k;
+  a.oz_diag = 1;
+  a.oz_nch = 1;
+  a.oz_chunk_kb = kblocks;
+  a.oz_sub_kb = kCrtSubKb;
+  a.oz_c0 = 0;
+  a.oz_ra = A.Rp;
+  a.oz_rb = B.Rp;
+  a.oz_tiles = tc_num_units(a, bn) / k;
+  a.err_flag = &c->st_dev->error;
+  // algorithmic work: k residue products
+  const double flops = k * 2.0 * n * n * (double)n * (sym ? 0.5 : 1.0);
+  const double bytes = k * 2.0 * 2.0 * n * (double)n + 1.0 * k * (double)n * n * (sym ? 0.5 : 1.0);
+  kstat_note(c, "fp64_equiv", flops / k);
+  if ((st = ctx_cuda(c, klaunch(c, "tc_gemm.crt", flops, bytes, 1,
+                                [&] { return launch_tc_gemm(a, maps, bn, c->num_sms, cur_stream(c)); }),
+                     "tcgen05 residue products")))
+    return st;
+  int md = mode;
+  if (partials && fused_resid && sym) {
+    md = 2;
+    *fused_resid = true;
+    if (nparts) *nparts = ozm_combine_blocks(n);
   }
+  // digits read (the upper triangle when sym), FP64 result written (read too when accumulating)
+  const double cbytes = (1.0 * k * n * (double)n + (md == 1 ? 16.0 : 8.0) * n * n) * (sym ? 0.5 : 1.0);
+  if ((st = ctx_cuda(c, klaunch(c, wide ? "oz_crt.wide" : "oz_crt", 0, cbytes, 1, [&] {
+                       if (wide)
+                         return launch_ozmw_combine8(G, (size_t)n * ld, ld, 1, wplan, A.e, B.e, A.T, B.T, n, out, ld64,
+                                                     md, sym, partials, cur_stream(c));
+                       return launch_ozm_combine8(G, (size_t)n * ld, ld, 1, plan, A.e, B.e, A.T, B.T, n, out, ld64, md,
+                                                  sym, partials, cur_stream(c));
+                     }),
+                     "oz crt combine")))
+    return st;
   return ZFACT_OK;
 }
 

@@ -59,6 +59,9 @@ struct TcArgs {
   size_t g_stride;              // kEpiG32 / kEpiCrt8: elements between group slots
   uint8_t* d8;                  // kEpiCrt8: digit planes (slot t * oz_nch + c)
   float crt_w[32];              // kEpiCrt8: digit weight w_t of modulus t in this product's plan
+  int oz_sub_kb;                // kEpiCrt8: K-blocks per exact FP32 accumulation; a unit's K range is
+                                // taken in sub-chunks of this many blocks, each reduced modulo m_t in
+                                // the epilogue and summed there (0: the whole range at once)
   // Grouped mode (ninst > 0): independent square problems stacked along the rows of every
   // operand and output buffer (common leading dimensions).  Scheduling slot j covers units
   // [g_prefix[j], g_prefix[j+1]) of instance g_inst[j]; instance i has size g_n[i], first row

@@ -274,7 +274,7 @@ class Context:
         self._raise(self.lib.zfact_set_loop_graphs(self.h, int(bool(on))))
 
     def set_emulation(self, scheme: str = "auto"):
-        """zfact_set_emulation: "auto" (CRT residues, twenty moduli or up to 31 where the rows need more
+        """zfact_set_emulation: "auto" (CRT residues, sixteen moduli or up to 24 where the rows need more
         bits, else slices), "slices", or "wide" (the same as "auto")."""
         self._raise(self.lib.zfact_set_emulation(self.h, EMULATION[scheme] if isinstance(scheme, str) else int(scheme)))
 

@@ -1,6 +1,7 @@
 // Host check of the CRT arithmetic of the residue products (paper_2404_19163_gb300/csrc/crt.h)
-// against exact 128-bit integer products: residues, exact chunked residue dot products, and the
-// reconstruction, including the extreme bound N 2^(2T) where the moduli are used up.
+// against exact 128-bit integer products: residues, exact chunked residue dot products (K-chunks of
+// 1024 terms, each sum reduced modulo m and the reductions summed, as the tensor-core epilogue does),
+// and the reconstruction, including the extreme bound N 2^(2T) where the moduli are used up.
 #include <math.h>
 #include <stdio.h>
 
@@ -44,8 +45,8 @@ int main() {
   int fails = 0;
   long cases = 0;
   const int Ts[] = {24, 40, 47, 53, 54};
-  const int Ks[] = {1, 2, 64, 1000, 4096, 4224, 4225, 8448, 16384};
-  const int chunk = 4224;
+  const int Ks[] = {1, 2, 64, 1000, 1024, 1025, 4096, 4224, 16384};
+  const int chunk = kCrtSubKb * 64;
   for (int T : Ts)
     for (int K : Ks) {
       CrtPlan p;
@@ -75,15 +76,14 @@ int main() {
         __int128 exact = 0;
         for (int l = 0; l < K; ++l) exact += (__int128)a[l] * b[l];
         // two reconstructions: the integer reference (exact residues and reductions), and the FP32
-        // path of the kernels (crt_residue_f, the per-chunk digit crt_digit of the tensor-core
-        // epilogue, the digit sums over chunks, add_y)
+        // path of the kernels (crt_residue_f, the epilogue's per-chunk reduction crt_fmod_sym and the
+        // sum of those reductions, its digit crt_digit, add_y)
         CrtAcc acc, accf;
         acc.clear();
         accf.clear();
         for (int t = 0; t < k; ++t) {
           const int m = p.m[t];
-          long long R = 0;
-          unsigned ysum = 0;
+          long long R = 0, Rsum = 0;
           for (int c0 = 0; c0 < K; c0 += chunk) {
             long long part = 0, partf = 0;
             for (int l = c0; l < K && l < c0 + chunk; ++l) {
@@ -107,16 +107,25 @@ int main() {
               return 1;
             }
             R += part;
-            const float y = crt_digit((float)partf, p.fm[t], p.inv[t], p.fw[t]);
-            if (y != floorf(y) || y < 0.0f || y >= (float)m ||
-                ((long long)y - (long long)ref_mod((long long)ref_mod(partf, m) * p.w[t], m)) % m != 0) {
-              printf("digit of %lld mod %d wrong: %g\n", partf, m, y);
+            const float rc = crt_fmod_sym((float)partf, p.fm[t], p.inv[t]);
+            if (rc != floorf(rc) || fabsf(rc) > 0.66f * m || ((long long)rc - partf) % m != 0) {
+              printf("chunk reduction of %lld mod %d wrong: %g\n", partf, m, rc);
               return 1;
             }
-            ysum += (unsigned)y;
+            Rsum += (long long)rc;
+          }
+          if (Rsum > 32767 || Rsum < -32768) {
+            printf("summed chunk reductions %lld leave 16 bits\n", Rsum);
+            return 1;
+          }
+          const float y = crt_digit((float)Rsum, p.fm[t], p.inv[t], p.fw[t]);
+          if (y != floorf(y) || y < 0.0f || y >= (float)m ||
+              ((long long)y - (long long)ref_mod((long long)ref_mod(Rsum, m) * p.w[t], m)) % m != 0) {
+            printf("digit of %lld mod %d wrong: %g\n", Rsum, m, y);
+            return 1;
           }
           ref_add(acc, p, t, R);
-          accf.add_y(p, t, ysum);
+          accf.add_y(p, t, (unsigned)y);
         }
         const double want = to_double(exact);
         for (const CrtAcc* A : {&acc, &accf}) {
@@ -154,7 +163,7 @@ int main() {
       return 1;
     }
   }
-  for (int i = 0; i < crtw::kMax; ++i) {  // crt_fmod_sym over |x| <= 2^24, every modulus down to 13
+  for (int i = 0; i < crtw::kMax; ++i) {  // crt_fmod_sym over |x| <= 2^24, every modulus
     const int m = crtw::modulus(i);
     const float inv = 1.0f / (float)m;
     for (long long x = -(1ll << 24); x <= (1ll << 24); x += (x > -(1ll << 24) + 5000 && x < (1ll << 24) - 5000) ? 331 : 1) {
@@ -181,7 +190,8 @@ int main() {
       }
   }
   CrtPlan p;
-  if (crt_plan(122.0, &p) != 19 || crt_plan(124.0, &p) != 20 || crt_plan(127.0, &p) != 0) {
+  if (crt_plan(110.0, &p) != 14 || crt_plan(117.0, &p) != 15 || crt_plan(118.0, &p) != 16 ||
+      crt_plan(125.5, &p) != 0) {
     printf("moduli counts wrong\n");
     return 1;
   }

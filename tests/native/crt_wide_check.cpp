@@ -1,7 +1,8 @@
 // Host check of the wider CRT arithmetic (paper_2404_19163_gb300/csrc/crt_wide.h).  Reads cases
 // (T, K, then K pairs of fixed-point values as sign, high and low 64-bit words of the magnitude),
-// forms the residue products as the tensor cores would (exact chunk sums of K <= 4224 terms, each
-// below 2^24, reduced to their CRT digits as the tensor-core epilogue does) and prints the
+// forms the residue products as the tensor cores would (exact chunk sums of K <= 1024 terms, each
+// of at most 2^24, reduced modulo m and summed, then that sum's CRT digit, as the tensor-core
+// epilogue does) and prints the
 // reconstructed product; the Python side compares it with the exact
 // big-integer product.  Also checks every residue against the magnitude modulo m.
 #include <math.h>
@@ -18,7 +19,7 @@ int main(int argc, char** argv) {
   FILE* f = fopen(argv[1], "r");
   if (!f) return 2;
   int T, K;
-  const int chunk = 4224;
+  const int chunk = kCrtSubKb * 64;
   while (fscanf(f, "%d %d", &T, &K) == 2) {
     std::vector<float> pa((size_t)K * crtw::kParts), pb((size_t)K * crtw::kParts);
     std::vector<unsigned __int128> ma(K), mb(K);
@@ -54,7 +55,7 @@ int main(int argc, char** argv) {
     acc.clear();
     for (int t = 0; t < k; ++t) {
       const int m = p.m[t];
-      unsigned ysum = 0;
+      long long rsum = 0;
       for (int c0 = 0; c0 < K; c0 += chunk) {
         long long part = 0;
         for (int l = c0; l < K && l < c0 + chunk; ++l) {
@@ -78,16 +79,23 @@ int main(int argc, char** argv) {
           printf("chunk %lld\n", part);
           return 1;
         }
-        // the tensor-core epilogue's digit of this chunk sum, then the combine's digit sum
-        const float y = crt_digit((float)part, p.fm[t], p.inv[t], p.fw[t]);
-        const long long rm = ((part % m) + m) % m;
-        if (y != floorf(y) || y < 0.0f || y >= (float)m || ((long long)y - (rm * p.w[t]) % m) % m != 0) {
-          printf("digit %d %d %d\n", T, K, m);
+        // the tensor-core epilogue's reduction of this chunk sum, summed over the chunks
+        const float rc = crt_fmod_sym((float)part, p.fm[t], p.inv[t]);
+        if (rc != floorf(rc) || fabsf(rc) > 0.66f * m || ((long long)rc - part) % m != 0) {
+          printf("reduction %d %d %d\n", T, K, m);
           return 1;
         }
-        ysum += (unsigned)y;
+        rsum += (long long)rc;
       }
-      acc.add_y(p, t, ysum);
+      // the digit of the summed reductions
+      const float y = crt_digit((float)rsum, p.fm[t], p.inv[t], p.fw[t]);
+      const long long rm = ((rsum % m) + m) % m;
+      if (rsum > 32767 || rsum < -32768 || y != floorf(y) || y < 0.0f || y >= (float)m ||
+          ((long long)y - (rm * p.w[t]) % m) % m != 0) {
+        printf("digit %d %d %d\n", T, K, m);
+        return 1;
+      }
+      acc.add_y(p, t, (unsigned)y);
     }
     printf("%d %d %d %.17g\n", T, K, k, acc.value(p, 0));
   }

@@ -78,9 +78,9 @@ def test_ozaki_residual_exact_on_integer_inputs(ctx, n, zbits, sbits):
 @pytest.mark.parametrize("n", [300, 4300, 8192])
 def test_residual_exact_on_scaled_integer_inputs(ctx, n):
     """Integer Z scaled by 2^-20 and integer S, so max|Z|^2 times S's largest row sum is below one
-    and the residual keeps 54 bits per operand: CRT residues under the default scheme (19 moduli
-    and two K-chunks at N = 4300; 20 moduli at N = 8192, whose chunks take two launches and an
-    unfused d = I - X).  Every product is an integer times a power of two that FP64 holds, so d
+    and the residual keeps 54 bits per operand: CRT residues under the default scheme (up to sixteen
+    moduli; at N = 4300 and 8192 each residue product is summed in K-chunks of 1024 reduced modulo m
+    in the epilogue).  Every product is an integer times a power of two that FP64 holds, so d
     must equal I - Z^T S Z bit for bit (columns sampled above N = 300)."""
     import torch
     g = np.random.default_rng(n)
@@ -105,7 +105,7 @@ def test_residual_exact_with_norm_bound_moduli(ctx, n):
     """Rows far from the worst case: Z = 2^-10 (I + sparse integers), S an integer matrix with
     64 on the diagonal and sparse small entries off it.  Every row's scaled 2-norm is about 1/2
     (one dominant entry), so by Cauchy-Schwarz the integer products need about log2(N) bits fewer
-    than the bound N 2^(2T) that holds for any rows: 17 moduli instead of 19.  d must still equal
+    than the bound N 2^(2T) that holds for any rows: 14 moduli instead of 16.  d must still equal
     I - Z^T S Z bit for bit, and the tensor-core flops show how many moduli ran (k 2 N^3 for Z^T S,
     k N^3 for the symmetric Z^T A)."""
     import torch
@@ -129,7 +129,7 @@ def test_residual_exact_with_norm_bound_moduli(ctx, n):
     if ctx.emu == "auto":
         k = stats["tc_gemm.crt"]["flops"] / (3.0 * n ** 3)
         assert stats["tc_gemm.crt"]["launches"] == 2 and abs(k - round(k)) < 1e-9, stats["tc_gemm.crt"]
-        assert round(k) == 17, k
+        assert round(k) == 14, k
 
 
 def test_ozaki_residual_unaligned_operand_bit_identical(ctx):

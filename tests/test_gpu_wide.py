@@ -1,6 +1,6 @@
 """Wide CRT residues (zfact_set_emulation("wide")): FP64-accurate products whose operand rows
-need more than the twenty moduli hold (an ill-conditioned Z: 60 to 83 bits per row), formed
-modulo up to 31 moduli with a six-limb reconstruction, against the FP64 oracle.
+need more than the sixteen moduli hold (an ill-conditioned Z: 60 to 83 bits per row), formed
+modulo up to 24 moduli with a six-limb reconstruction, against the FP64 oracle.
 
 The bit-exact cases use integer S and Z = Z_int 2^-k: every entry of S Z, Z^T S and
 Z^T S Z is an integer multiple of a power of two that FP64 holds, the rows' fixed point
@@ -65,7 +65,7 @@ def test_wide_residual_exact_on_scaled_integer_inputs(ctx, n, k):
 
 @pytest.mark.parametrize("n", [64, 257, 600])
 def test_wide_residual_ill_conditioned_matches_oracle(ctx, n):
-    """cond 1e5 with max|Z| ~ 300: more than 62 bits per row, past the twenty moduli."""
+    """cond 1e5 with max|Z| ~ 300: more than 62 bits per row, past the sixteen moduli."""
     import torch
     S, Q, lam = synth.householder_spd(n, seed=91 + n, lam_lo=1e-5, lam_hi=1.0)
     g = np.random.default_rng(91 + n)
