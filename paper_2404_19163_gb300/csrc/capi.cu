@@ -72,6 +72,30 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int out_copy_start(zfact_ctx* c, const double* Z) {
+  if (!c->out_host) return ZFACT_OK;
+  if (!c->out_stream && cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return ctx_fail(c, ZFACT_ERR_CUDA, "output stream");
+  if (!c->out_ev && cudaEventCreateWithFlags(&c->out_ev, cudaEventDisableTiming) != cudaSuccess)
+    return ctx_fail(c, ZFACT_ERR_CUDA, "output event");
+  cudaEvent_t e = ev_get(c);
+  cudaEventRecord(e, c->stream);
+  cudaStreamWaitEvent(c->out_stream, e, 0);
+  c->ev_pool.push_back(e);
+  int st = ctx_cuda(c, cudaMemcpyAsync(c->out_host, Z, c->out_bytes, cudaMemcpyDeviceToHost, c->out_stream),
+                    "early copy of Z");
+  if (st) return st;
+  cudaEventRecord(c->out_ev, c->out_stream);
+  c->out_src = Z;
+  return ZFACT_OK;
+}
+
+void out_copy_fence(zfact_ctx* c) {
+  if (!c->out_src) return;
+  cudaStreamWaitEvent(c->stream, c->out_ev, 0);
+  c->out_src = nullptr;
+}
+
 // ----------------------------------------------------------------- per-kernel accounting
 int kstat_id(zfact_ctx* c, const char* name) {
   for (size_t i = 0; i < c->kstats.size(); ++i)
@@ -211,6 +235,8 @@ extern "C" void zfact_destroy(zfact_ctx* c) {
   if (c->st_host) cudaFreeHost(c->st_host);
   cudaEventDestroy(c->ev0);
   cudaEventDestroy(c->ev1);
+  if (c->out_ev) cudaEventDestroy(c->out_ev);
+  if (c->out_stream) cudaStreamDestroy(c->out_stream);
   for (int l = 0; l < zfact_ctx::kLanes; ++l)
     if (c->lane_stream[l]) cudaStreamDestroy(c->lane_stream[l]);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -362,6 +388,17 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   int iters = 0, ridx = 0;
   double* Zcur = Za;
   double* Znext = Zb;
+  // whatever happens below, no early copy into the caller's buffer (mixed path) outlives this call
+  struct OutGuard {
+    zfact_ctx* c;
+    ~OutGuard() {
+      if (c->out_src) cudaStreamSynchronize(c->out_stream);
+      c->out_src = nullptr;
+      c->out_host = nullptr;
+    }
+  } out_guard{c};
+  c->out_host = nullptr;
+  c->out_src = nullptr;
   if (precision == ZFACT_P_FP64) {
     double* A = (double*)ctx_buf(c, "A64", bytes, &st);
     if (!A) return st;
@@ -409,8 +446,16 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
     if (st) return st;
     Zcur = c->mixed_result;
   } else {
+    // a pinned host Z takes the result by an early copy that overlaps the final residual (a pageable
+    // one would make that copy block the host, so it is copied at the end as usual)
+    cudaPointerAttributes pa;
+    const bool pinned = cudaPointerGetAttributes(&pa, Z_out) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    if (!pinned) cudaGetLastError();
+    c->out_host = pinned ? (void*)Z_out : nullptr;
+    c->out_bytes = bytes;
     st = mixed_refine(c, S, Zcur, Znext, n, order, precision, o, &iters, &ridx, &inf, Z0_in == nullptr);
     if (st == kRetryGershgorin) {
+      out_copy_fence(c);  // the retry writes the Z an early copy may be reading
       // the caller's start scale did not contract: the Gershgorin start, as if start_scale were 0
       o.start_scale = 0.0;
       iters = ridx = 0;
@@ -431,8 +476,14 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
     Zcur = c->mixed_result;
   }
 
-  // ---- output
-  if ((st = ctx_cuda(c, cudaMemcpyAsync(Z_out, Zcur, bytes, cudaMemcpyDefault, c->stream), "copy Z out"))) return st;
+  // ---- output (the early copy already holds the final Z when it read this array after its last write)
+  if (c->out_src && c->out_src == Zcur) {
+    cudaStreamWaitEvent(c->stream, c->out_ev, 0);
+  } else {
+    out_copy_fence(c);
+    if ((st = ctx_cuda(c, cudaMemcpyAsync(Z_out, Zcur, bytes, cudaMemcpyDefault, c->stream), "copy Z out")))
+      return st;
+  }
   cudaEventRecord(c->ev1, c->stream);
   if ((st = ctx_read_state(c))) return st;
   float ms = 0.f;

@@ -39,6 +39,13 @@ struct zfact_ctx {
   zf::IterState* st_host = nullptr;    // pinned host mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double* mixed_result = nullptr;      // device FP64 Z produced by the mixed driver
+  // The result's copy to a caller's pinned host Z, started on out_stream after each refinement update so
+  // that it overlaps the FP64-accurate residual that follows (out_src: the device Z it reads, or null)
+  void* out_host = nullptr;
+  size_t out_bytes = 0;
+  const double* out_src = nullptr;
+  cudaStream_t out_stream = nullptr;
+  cudaEvent_t out_ev = nullptr;
   char err[512];
   // per-kernel accounting
   bool profiling = false;
@@ -82,6 +89,10 @@ int kstat_id(zfact_ctx* c, const char* name);
 // Adds FLOPs to the statistics of `name` without a launch or a time: the FP64 product count of an
 // FP64-accurate product ("fp64_equiv": 2 N^2 K, half on symmetric tiles), whatever scheme formed it.
 void kstat_note(zfact_ctx* c, const char* name, double flops);
+// Early output copy (see zfact_ctx::out_host): start it from Z after the work queued so far; order the
+// context's stream after the copy in flight (before Z is written again, or the call returns).
+int out_copy_start(zfact_ctx* c, const double* Z);
+void out_copy_fence(zfact_ctx* c);
 cudaEvent_t ev_get(zfact_ctx* c);
 void kstats_flush(zfact_ctx* c);  // stream must be idle
 

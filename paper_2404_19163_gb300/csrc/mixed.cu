@@ -335,7 +335,9 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
         Pprev = keep;
       }
     }
+    out_copy_fence(c);  // an early copy of the previous Z reads the array the update writes
     if ((st = oz_update(c, Z64, Q64, n, qmax, rho_zr))) return st;
+    if ((st = out_copy_start(c, Z64))) return st;
     ++ridx;
   }
   *ridx_out = ridx;

@@ -79,3 +79,26 @@ def test_headline_configuration_n4096(ctx):
     Z, err_or = _check(ctx, S, St, r)
     # the FP64 GPU path's factor is another valid factor; the two agree to the bulk's accuracy
     assert r.info["iters"] >= 2 and r.info["refine_iters"] >= 1
+
+
+@pytest.mark.parametrize("refine_steps", [3, 0])
+def test_pinned_host_output_is_the_device_result(ctx, refine_steps):
+    """A pinned host Z (the end-to-end path) receives the result by a copy started after the last
+    refinement update, overlapping the final residual; it must hold exactly the device result, also
+    when no update follows the copy's source (bulk only) and when S comes from the host too."""
+    import torch
+    S = synth.cubic_overlap(n_side=10)
+    n = S.shape[0]
+    St = torch.from_numpy(S).cuda()
+    kw = dict(order=2, precision="bf16_split", tol=TOL if refine_steps else 0.0, refine_steps=refine_steps)
+    rd = ctx.refine(St, None, **kw)
+    Zh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    Sh = torch.from_numpy(S).pin_memory()
+    rh = ctx.refine(Sh, None, Z=Zh, **kw)
+    assert torch.equal(Zh, rd.Z.cpu())
+    assert rh.info["iters"] == rd.info["iters"] and rh.info["refine_iters"] == rd.info["refine_iters"]
+    assert rh.info["resid_f"] == rd.info["resid_f"] or (math.isnan(rh.info["resid_f"]) and math.isnan(rd.info["resid_f"]))
+    # a pageable host Z takes the copy at the end
+    Zp = np.empty((n, n))
+    ctx.refine(St, None, Z=Zp, **kw)
+    assert np.array_equal(Zp, rd.Z.cpu().numpy())
