@@ -14,7 +14,7 @@
 
 namespace zf {
 
-constexpr int kCrtMax = 16;        // moduli available; their product is just below 2^125.5
+constexpr int kCrtMax = 16;        // moduli available; their product is just below 2^125.38
 constexpr int kCrtMaxChunks = 4;   // digit planes per reconstruction (K-chunks reduced outside the product)
 constexpr int kCrtMaxResidue = 128;  // largest |residue|: K-chunks of 2^24 / 128^2 = 1024 terms stay exact
 constexpr int kCrtSubKb = (1 << 24) / (kCrtMaxResidue * kCrtMaxResidue) / 64;  // 64-wide K-blocks per chunk
@@ -143,22 +143,20 @@ ZF_HD inline void crt_parts(long long F, float (&a)[5]) {
     a[k] = sg * (crt_bits_f(0x4B000000u | (unsigned)((u >> (14 * k)) & 0x3FFFu)) - 8388608.0f);
 }
 
-// Symmetric residue of F modulo m from its first NP parts (NP = 4 when |F| < 2^56), in FP32:
-// x = sum_k a_k (2^(14k) mod m), with |a_k| < 2^14 and the symmetric |2^(14k) mod m| <= 128, is an
-// integer below 5 2^21 < 2^24 in magnitude (exact); x - m rint(x / m) is congruent to F, and the float
-// quotient errs by less than 0.01, so |r| < 0.52 m.  A second reduction of the same kind brings r into
-// [-m/2, m/2]: r / m is then known to 2^-22, and no integer r lies that close to m/2 except r = m/2
-// itself (m = 256), whose tie rint takes to an even quotient.  So |r| <= 128 for every modulus.  The
-// second reduction keeps the fix-up on the FMA pipe (a compare-and-select would load the ALU pipe,
-// which the residue kernels already keep the busier).
+// Residue of F modulo m from its first NP parts (NP = 4 when |F| < 2^56), in FP32: x = sum_k a_k
+// (2^(14k) mod m), with |a_k| < 2^14 and the symmetric |2^(14k) mod m| <= m/2, is an integer with
+// |x / m| < 5 2^13, below 2^24 (exact).  r = x - m rint(x / m) is congruent to F; the FP32 quotient
+// (1/m and the product each rounded once) errs by at most |x / m| 2^-23 < 0.0049, so rint is at most one
+// step from the nearest integer and |r| <= m (1/2 + 0.0049) < 128.8 for m <= 255, |r| <= 128; for
+// m = 256 the quotient is exact and |r| <= 128 too.  (Not always the symmetric residue, but within the
+// bound the residue products need.)
 template <int NP = 5>
 ZF_HD inline float crt_residue_f(const float (&a)[5], int m) {
   const float fm = (float)m;
   float x = fmaf(a[3], (float)crt_pow2_sym(m, 42),
                  fmaf(a[2], (float)crt_pow2_sym(m, 28), fmaf(a[1], (float)crt_pow2_sym(m, 14), a[0])));
   if (NP > 4) x = fmaf(a[4], (float)crt_pow2_sym(m, 56), x);
-  const float r = fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
-  return fmaf(-fm, crt_rint(r * (1.0f / fm)), r);
+  return fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
 }
 
 // x mod m for an integer-valued float |x| <= 2^24 and m >= 13, inv = FP32(1 / m): congruent, and

@@ -1,5 +1,5 @@
 // Wider CRT arithmetic for residue products whose bound passes the sixteen moduli of crt.h:
-// up to 24 pairwise coprime moduli (M below 2^184.7) in six 32-bit limbs, and fixed-point rows of
+// up to 24 pairwise coprime moduli (M about 2^184.6) in six 32-bit limbs, and fixed-point rows of
 // up to 84 bits as six 14-bit parts.  The first sixteen moduli are crt.h's, in the same order,
 // so a plan of at most sixteen moduli is the same plan.  Every modulus is at most 256, so the
 // residues, the K-chunk length (1024) and the FP32 reductions are those of crt.h.
@@ -61,16 +61,15 @@ ZF_HD inline void parts(unsigned long long mag_hi, unsigned long long mag_lo, bo
   }
 }
 
-// Symmetric residue of F modulo m from its six parts: x = sum_k a_k (2^(14k) mod m) stays below
-// 6 2^21 < 2^24 in magnitude (exact in FP32); the rest is crt_residue_f's two reductions (the first
-// leaves |r| < 0.52 m, the second brings it into [-m/2, m/2]).
+// Residue of F modulo m from its six parts: x = sum_k a_k (2^(14k) mod m) has |x / m| < 6 2^13, below
+// 2^24 (exact in FP32); crt_residue_f's one reduction then errs by less than 0.0059 in the quotient, so
+// |r| <= m (1/2 + 0.0059) < 129 for m <= 255, |r| <= 128 (m = 256: exact quotient).
 ZF_HD inline float residue_f(const float (&a)[kParts], int m) {
   const float fm = (float)m;
   float x = a[kParts - 1] * (float)crt_pow2_sym(m, 14 * (kParts - 1));
   for (int k = kParts - 2; k >= 1; --k) x = fmaf(a[k], (float)crt_pow2_sym(m, 14 * k), x);
   x += a[0];
-  const float r = fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
-  return fmaf(-fm, crt_rint(r * (1.0f / fm)), r);
+  return fmaf(-fm, crt_rint(x * (1.0f / fm)), x);
 }
 
 struct Plan {

@@ -5,7 +5,7 @@
 // Every row r of an FP64 operand is scaled by 2^(T - e_r) (e_r: the row's exponent bound) and
 // rounded to an integer F with |F| <= 2^T.  The product C' = F_A F_B^T of two such integer
 // matrices is exact and bounded by K 2^(T_A + T_B).  It is formed modulo pairwise coprime
-// moduli m_i <= 256: the symmetric residues of F (|r| <= 128) are exact in BF16, a residue
+// moduli m_i <= 256: residues of F within 128 of zero (one FP32 reduction) are exact in BF16, a residue
 // product over K <= 1024 terms stays an integer of at most 2^24 (exact in the FP32 accumulator;
 // longer products are reduced modulo m_i every 1024 terms inside the product's epilogue), and
 // the Chinese remainder theorem recovers C' from its residues once M = prod m_i > 4 |C'|.  The

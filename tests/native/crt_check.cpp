@@ -94,7 +94,7 @@ int main() {
               crt_parts(b[l], pb);
               const float fa = crt_residue_f(pa, m), fb = crt_residue_f(pb, m);
               if (ra > kCrtMaxResidue || ra < -kCrtMaxResidue || rb > kCrtMaxResidue || rb < -kCrtMaxResidue ||
-                  fabsf(fa) > (float)(m / 2) || fabsf(fb) > (float)(m / 2) || fa != floorf(fa) ||
+                  fabsf(fa) > (float)kCrtMaxResidue || fabsf(fb) > (float)kCrtMaxResidue || fa != floorf(fa) ||
                   ((long long)fa - ra) % m != 0 || ((long long)fb - rb) % m != 0) {
                 printf("residue wrong or out of range (m=%d: %d %g, %d %g)\n", m, ra, fa, rb, fb);
                 return 1;
@@ -148,7 +148,7 @@ int main() {
     float pa[5];
     crt_parts(F, pa);
     const float rf = crt_residue_f(pa, m);
-    if ((F - r) % m != 0 || (F - (long long)rf) % m != 0 || fabsf(rf) > (float)(m / 2) || rf != floorf(rf)) {
+    if ((F - r) % m != 0 || (F - (long long)rf) % m != 0 || fabsf(rf) > 128.0f || rf != floorf(rf)) {
       printf("residue of %lld mod %d wrong: %d / %g\n", F, m, r, rf);
       return 1;
     }
@@ -158,7 +158,7 @@ int main() {
     crt_parts(F4, p4);
     const int r4 = ref_sym_residue((unsigned long long)(F4 < 0 ? -F4 : F4), F4 < 0, m);
     const float rf4 = crt_residue_f<4>(p4, m);
-    if ((F4 - (long long)rf4) % m != 0 || (F4 - r4) % m != 0 || fabsf(rf4) > (float)(m / 2) || rf4 != floorf(rf4)) {
+    if ((F4 - (long long)rf4) % m != 0 || (F4 - r4) % m != 0 || fabsf(rf4) > 128.0f || rf4 != floorf(rf4)) {
       printf("four-part residue of %lld mod %d wrong: %d / %g\n", F4, m, r4, rf4);
       return 1;
     }

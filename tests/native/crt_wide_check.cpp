@@ -68,8 +68,8 @@ int main(int argc, char** argv) {
           // congruence with the exact value and the symmetric range
           const long long ea = (long long)(ma[l] % (unsigned)m) * (na[l] ? -1 : 1);
           const long long eb = (long long)(mb[l] % (unsigned)m) * (nb[l] ? -1 : 1);
-          if ((((long long)ra - ea) % m) != 0 || (((long long)rb - eb) % m) != 0 || fabsf(ra) > (float)(m / 2) ||
-              fabsf(rb) > (float)(m / 2) || ra != floorf(ra) || rb != floorf(rb)) {
+          if ((((long long)ra - ea) % m) != 0 || (((long long)rb - eb) % m) != 0 || fabsf(ra) > 128.0f ||
+              fabsf(rb) > 128.0f || ra != floorf(ra) || rb != floorf(rb)) {
             printf("badresidue %d %d %d\n", T, K, m);
             return 1;
           }
