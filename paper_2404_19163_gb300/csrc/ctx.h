@@ -61,6 +61,9 @@ struct zfact_ctx {
   int oz_nmod = 0;   // > 0: those products use this many CRT residues instead of slices
   int oz_wide = 0;   // 1: those residues use the wider moduli of crt_wide.h
   double oz_rho_s = -1.0;  // largest scaled row norm of S's rows (-1: unknown), see oz_prod_bits
+  // when set, oz_residual's fused CRT reconstruction writes max|d| there (double bits) and sets oz_amax_done
+  unsigned long long* oz_amax = nullptr;
+  bool oz_amax_done = false;
   int oz_scheme = 0;  // zfact_emulation: 0 residues where they fit, 1 slices always, 2 also wide residues
   cudaStream_t lane_stream[kLanes] = {};
   int lane = -1;

@@ -188,13 +188,15 @@ __device__ __forceinline__ void combine8_tile(const uint8_t* __restrict__ G, siz
                                               const Plan& plan, const int* __restrict__ eA,
                                               const int* __restrict__ eB, int TA, int TB, int n,
                                               double* __restrict__ out, int ld64, int mode, int sym,
-                                              double* partial_out, int bi, int bj) {
+                                              double* partial_out, int bi, int bj,
+                                              unsigned long long* amax_out = nullptr) {
   __shared__ double tile[32][129];
   __shared__ double red[8];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const bool active = !sym || bj + 127 >= bi;
   const int nmod = plan.nmod;
   double ss_off = 0.0, ss_diag = 0.0;  // sums of d_ij^2 over j > i and j = i
+  unsigned long long am = 0ull;         // max |d_ij| (bits of a non-negative double) when amax_out is set
   if (active) {
     const int j0 = bj + 4 * tx;
     int eb[4];
@@ -251,6 +253,7 @@ __device__ __forceinline__ void combine8_tile(const uint8_t* __restrict__ G, siz
               v = __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
               if (j > i) ss_off = fma(v, v, ss_off);
             }
+            if (amax_out && (!sym || j >= i)) am = max_bits(am, abs_bits(v));
           }
           if (out && (!sym || j >= i)) {
             double* o = out + (size_t)i * ld64 + j;
@@ -290,6 +293,11 @@ __device__ __forceinline__ void combine8_tile(const uint8_t* __restrict__ G, siz
       for (int w = 0; w < 8; ++w) t += red[w];
       if (partial_out) *partial_out = t;
     }
+    if (amax_out) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) am = max_bits(am, __shfl_xor_sync(0xffffffffu, am, o));
+      if (tx == 0 && am) atomicMax(amax_out, am);
+    }
   }
 }
 
@@ -298,10 +306,11 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
                                                          int nch, const __grid_constant__ Plan plan,
                                                          const int* __restrict__ eA, const int* __restrict__ eB, int TA,
                                                          int TB, int n, double* __restrict__ out, int ld64, int mode,
-                                                         int sym, double* __restrict__ partials) {
+                                                         int sym, double* __restrict__ partials,
+                                                         unsigned long long* amax) {
   combine8_tile<Plan, Acc, KMAX>(G, gstride, ld8, nch, plan, eA, eB, TA, TB, n, out, ld64, mode, sym,
                                  partials ? partials + blockIdx.y * gridDim.x + blockIdx.x : nullptr, blockIdx.y * 32,
-                                 blockIdx.x * 128);
+                                 blockIdx.x * 128, amax);
 }
 
 // Every instance of a group (grid.z): its digits, exponents and output rows start at its packed row.
@@ -550,23 +559,24 @@ int ozm_combine_blocks(int n) { return ((n + 127) / 128) * ((n + 31) / 32); }
 
 cudaError_t launch_ozm_combine8(const uint8_t* G, size_t gstride, int ld8, int nch, const CrtPlan& plan, const int* eA,
                                 const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
-                                double* partials, cudaStream_t s) {
+                                double* partials, cudaStream_t s, unsigned long long* amax) {
   if (nch < 1 || nch > kCrtMaxChunks || plan.nmod < 1 || plan.nmod > kCrtMax || (ld8 % 4) != 0)
     return cudaErrorInvalidValue;
   dim3 grid((n + 127) / 128, (n + 31) / 32), block(32, 8);
   k_ozm_combine8<CrtPlan, CrtAcc, kCrtMax><<<grid, block, 0, s>>>(G, gstride, ld8, nch, plan, eA, eB, TA, TB, n, out,
-                                                                  ld64, mode, sym ? 1 : 0, partials);
+                                                                  ld64, mode, sym ? 1 : 0, partials, amax);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ozmw_combine8(const uint8_t* G, size_t gstride, int ld8, int nch, const crtw::Plan& plan,
                                  const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
-                                 bool sym, double* partials, cudaStream_t s) {
+                                 bool sym, double* partials, cudaStream_t s, unsigned long long* amax) {
   if (nch < 1 || nch > kCrtMaxChunks || plan.nmod < 1 || plan.nmod > crtw::kMax || (ld8 % 4) != 0)
     return cudaErrorInvalidValue;
   dim3 grid((n + 127) / 128, (n + 31) / 32), block(32, 8);
   k_ozm_combine8<crtw::Plan, crtw::Acc, crtw::kMax><<<grid, block, 0, s>>>(G, gstride, ld8, nch, plan, eA, eB, TA, TB,
-                                                                         n, out, ld64, mode, sym ? 1 : 0, partials);
+                                                                         n, out, ld64, mode, sym ? 1 : 0, partials,
+                                                                         amax);
   return cudaGetLastError();
 }
 

@@ -355,7 +355,8 @@ __device__ __forceinline__ void epi_chunk(const TcArgs& a, int i, int col0, floa
       for (int jj = 0; jj < 32; ++jj) {
         const int j = col0 + jj;
         if (j < n && (!a.sym || j >= i)) {
-          const double x = (double)v[jj] * (double)us;
+          double x = (double)v[jj] * (double)us;
+          if (a.f64_in) x = fma((double)a.c1, a.f64_in[(size_t)row0 * a.ld64 + (size_t)i * a.ld64 + j], (double)a.c2 * x);
           crow[j] = x;
           if (a.sym && j > i) f64[(size_t)j * a.ld64 + i] = x;
         }

@@ -114,10 +114,11 @@ cudaError_t launch_ozm_residues(const double* X, int n, int ld, bool trans, int*
 // C' from the CRT digits of the residue products (k_tc.cu epilogue kEpiCrt8: plane t * nch + c holds
 // the byte (product_t,c mod m_t) w_t mod m_t, row-major with leading dimension ld8), scaled by
 // 2^(eA_i + eB_j - TA - TB); modes as launch_oz_combine (mode 2 writes ozm_combine_blocks(n)
-// partials); sym forms i <= j and mirrors; nch <= kCrtMaxChunks.
+// partials, and with amax != null the atomic maximum of |d| as the bits of a double, which the caller
+// zeroes); sym forms i <= j and mirrors; nch <= kCrtMaxChunks.
 cudaError_t launch_ozm_combine8(const uint8_t* G, size_t gstride, int ld8, int nch, const CrtPlan& plan, const int* eA,
                                 const int* eB, int TA, int TB, int n, double* out, int ld64, int mode, bool sym,
-                                double* partials, cudaStream_t s);
+                                double* partials, cudaStream_t s, unsigned long long* amax = nullptr);
 int ozm_combine_blocks(int n);
 // max_r rho_r^2 over the rows (cols = false) or columns (cols = true) of X, rho_r^2 = sum_k (x_rk 2^-e_r)^2
 // with e_r the exponent bound of the residue kernels, as an FP32 bit pattern: atomic maximum into
@@ -133,7 +134,7 @@ cudaError_t launch_ozmw_residues(const double* X, int n, int ld, bool trans, int
                                  int ld16, int Rp, cudaStream_t s);
 cudaError_t launch_ozmw_combine8(const uint8_t* G, size_t gstride, int ld8, int nch, const crtw::Plan& plan,
                                  const int* eA, const int* eB, int TA, int TB, int n, double* out, int ld64, int mode,
-                                 bool sym, double* partials, cudaStream_t s);
+                                 bool sym, double* partials, cudaStream_t s, unsigned long long* amax = nullptr);
 
 // ---- grouped residue products (the batched mode's final residuals, batched.cu)
 // Instance i of a group: size n[i], its operand rows at packed rows row0[i] ... (one leading dimension for

@@ -255,9 +255,14 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
       rho_zt = oz_rho_from(c->st_host->rho2[1], n);
       rho_zr = -1.0;
     }
-    if ((st = oz_residual(c, Z64, D64, n, idx, o.stop_rule, o.tol, 0, rho_zt))) return st;
-    // max|d| comes back with Err: it scales d's 16-bit copy and bounds Q for the update's slices
-    if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
+    // max|d| comes back with Err (from the CRT reconstruction itself, else one pass over d): it scales
+    // d's 16-bit copy and bounds Q for the update's moduli or slices
+    c->oz_amax = reinterpret_cast<unsigned long long*>(&c->st_dev->amax[1]);
+    st = oz_residual(c, Z64, D64, n, idx, o.stop_rule, o.tol, 0, rho_zt);
+    c->oz_amax = nullptr;
+    if (st) return st;
+    if (!c->oz_amax_done &&
+        (st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
                                   [&] { return launch_amax_f64(D64, n, c->st_dev, 1, c->stream); }),
                        "amax d")))
       return st;
@@ -317,6 +322,15 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
       kp.ld64 = n;
       kp.sa_ptr = &c->st_dev->scale[k > 2 ? 4 : 0];
       kp.sb_ptr = &c->st_dev->scale[0];
+      if (ord == 2) {
+        // Q = c1 d + c2 d^2 formed in the product's epilogue (FP64), no power kept
+        kp.f64 = Q64;
+        kp.f64_in = D64;
+        kp.c1 = (float)coef[1];
+        kp.c2 = (float)coef[2];
+        if ((st = tc_product(c, kp, A, Dr, ld, bn))) return st;
+        break;
+      }
       if ((st = tc_product(c, kp, A, Dr, ld, bn))) return st;
       const double* first = (k == 2) ? D64 : Q64;
       const double a1 = (k == 2) ? coef[1] : 1.0;

@@ -228,9 +228,9 @@ int oz_product_mod(zfact_ctx* c, const OzOperand& A, const OzOperand& B, int n, 
   if ((st = ctx_cuda(c, klaunch(c, wide ? "oz_crt.wide" : "oz_crt", 0, cbytes, 1, [&] {
                        if (wide)
                          return launch_ozmw_combine8(G, (size_t)n * ld, ld, 1, wplan, A.e, B.e, A.T, B.T, n, out, ld64,
-                                                     md, sym, partials, cur_stream(c));
+                                                     md, sym, partials, cur_stream(c), md == 2 ? c->oz_amax : nullptr);
                        return launch_ozm_combine8(G, (size_t)n * ld, ld, 1, plan, A.e, B.e, A.T, B.T, n, out, ld64, md,
-                                                  sym, partials, cur_stream(c));
+                                                  sym, partials, cur_stream(c), md == 2 ? c->oz_amax : nullptr);
                      }),
                      "oz crt combine")))
     return st;
@@ -413,7 +413,10 @@ int oz_residual(zfact_ctx* c, const double* Z, double* D, int n, int idx, int ru
   // X = Z^T A = Z^T (A^T)^T, symmetric tiles; d = I - X fused into the combine when possible
   bool fused = false;
   double* Xout = X64;
+  // with residues the fused reconstruction also gives max|d| (into st->amax[1]) when the caller asks
+  if (c->oz_amax) cudaMemsetAsync(c->oz_amax, 0, sizeof(unsigned long long), cur_stream(c));
   if ((st = oz_product(c, Zt, At, n, true, D, n, 0, partials, &fused, &nb_fused, bits2))) return st;
+  c->oz_amax_done = fused && c->oz_nmod > 0 && c->oz_amax;
   if (!fused) {
     // several K-chunk batches: the combine accumulated X into D; form d = I - X from it
     if ((st = ctx_cuda(c, cudaMemcpyAsync(Xout, D, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, cur_stream(c)),

@@ -43,6 +43,7 @@ struct TcArgs {
   float* f32;  int ld32;        // kEpiResid out (d), kEpiZupd in/out (Z master)
   const float* f32_in;          // kEpiPoly: d in FP32
   double* f64; int ld64;        // kEpiF64 out / kEpiZupd64 in-out
+  const double* f64_in;         // kEpiF64: when set, out = c1 f64_in + c2 (product), in FP64 (ld64)
   uint16_t* o16h; uint16_t* o16l; int ld16;
   uint16_t* t16h; uint16_t* t16l;  // kEpiZupd: transposed copy
   float c1, c2;
