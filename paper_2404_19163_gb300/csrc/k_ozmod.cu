@@ -302,7 +302,7 @@ __device__ __forceinline__ void combine8_tile(const uint8_t* __restrict__ G, siz
 }
 
 template <class Plan, class Acc, int KMAX>
-__global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restrict__ G, size_t gstride, int ld8,
+__global__ void __launch_bounds__(256, KMAX > kCrtMax ? 2 : 3) k_ozm_combine8(const uint8_t* __restrict__ G, size_t gstride, int ld8,
                                                          int nch, const __grid_constant__ Plan plan,
                                                          const int* __restrict__ eA, const int* __restrict__ eB, int TA,
                                                          int TB, int n, double* __restrict__ out, int ld64, int mode,
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256, 2) k_ozm_combine8(const uint8_t* __restri
 
 // Every instance of a group (grid.z): its digits, exponents and output rows start at its packed row.
 template <class Plan, class Acc, int KMAX>
-__global__ void __launch_bounds__(256, 2) k_gozm_combine8(const uint8_t* __restrict__ G, size_t gstride, int ld8,
+__global__ void __launch_bounds__(256, KMAX > kCrtMax ? 2 : 3) k_gozm_combine8(const uint8_t* __restrict__ G, size_t gstride, int ld8,
                                                           const __grid_constant__ Plan plan, const GroupRes g,
                                                           const int* __restrict__ eA, const int* __restrict__ eB,
                                                           double* __restrict__ out, int ld64, int mode, int sym,
