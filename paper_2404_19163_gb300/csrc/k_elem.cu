@@ -27,12 +27,13 @@ __global__ void k_rowabs_max(const double* __restrict__ S, int n, IterState* st)
 __global__ void k_gscale(IterState* st) { st->gscale = 1.0 / sqrt(st->amax[0]); }
 __global__ void k_set_gscale(IterState* st, double s) { st->gscale = s; }
 
+// Rows i = blockIdx.y, blockIdx.y + gridDim.y, ...; columns across blockIdx.x and the threads (no
+// division per element).
 __global__ void k_scaled_identity_f64(double* Z, int n, const IterState* st) {
-  const size_t total = (size_t)n * n;
   const double s = st->gscale;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = e / n, j = e % n;
-    Z[e] = (i == j) ? s : 0.0;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    double* zr = Z + (size_t)i * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) zr[j] = (i == j) ? s : 0.0;
   }
 }
 
@@ -325,21 +326,22 @@ __global__ void k_cold_update(const float* __restrict__ Q, int n, int ld, const 
   const float s = (float)st->gscale;
   const float osc = out_scale ? *out_scale : 1.0f;
   float am = 0.0f;
-  const size_t total = (size_t)n * n;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / n), j = (int)(e % n);
-    const size_t o = (size_t)i * ld + j;
-    const float z = s * ((i == j ? 1.0f : 0.0f) + Q[o]);
-    Zm[o] = z;
-    am = fmaxf(am, fabsf(z));
-    const float y = z * osc;
-    const uint16_t h = r16(y, bf16);
-    zh[o] = h;
-    th[o] = h;
-    if (zl) {
-      const uint16_t l = r16(y - f16v(h, bf16), bf16);
-      zl[o] = l;
-      tl[o] = l;
+  // rows across blockIdx.y, columns across blockIdx.x and the threads (no division per element)
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+      const size_t o = (size_t)i * ld + j;
+      const float z = s * ((i == j ? 1.0f : 0.0f) + Q[o]);
+      Zm[o] = z;
+      am = fmaxf(am, fabsf(z));
+      const float y = z * osc;
+      const uint16_t h = r16(y, bf16);
+      zh[o] = h;
+      th[o] = h;
+      if (zl) {
+        const uint16_t l = r16(y - f16v(h, bf16), bf16);
+        zl[o] = l;
+        tl[o] = l;
+      }
     }
   }
 #pragma unroll
@@ -419,9 +421,7 @@ cudaError_t launch_set_gscale(IterState* st, double scale, cudaStream_t s) {
 }
 
 cudaError_t launch_scaled_identity_f64(double* Z, int n, const IterState* st, cudaStream_t s) {
-  const size_t total = (size_t)n * n;
-  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  k_scaled_identity_f64<<<blocks, 256, 0, s>>>(Z, n, st);
+  k_scaled_identity_f64<<<rows_grid(n), 256, 0, s>>>(Z, n, st);
   return cudaGetLastError();
 }
 
@@ -449,8 +449,7 @@ cudaError_t launch_cold_resid(const double* S, int n, const IterState* st, float
 cudaError_t launch_cold_update(const float* Q, int n, int ld, const IterState* st, float* Zm, uint16_t* zh,
                                uint16_t* zl, uint16_t* th, uint16_t* tl, const float* out_scale, bool bf16,
                                unsigned int* amax_bits, cudaStream_t s) {
-  k_cold_update<<<grid_for((size_t)n * n), 256, 0, s>>>(Q, n, ld, st, Zm, zh, zl, th, tl, out_scale, bf16 ? 1 : 0,
-                                                       amax_bits);
+  k_cold_update<<<rows_grid(n), 256, 0, s>>>(Q, n, ld, st, Zm, zh, zl, th, tl, out_scale, bf16 ? 1 : 0, amax_bits);
   return cudaGetLastError();
 }
 }  // namespace zf
