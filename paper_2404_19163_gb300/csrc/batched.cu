@@ -72,6 +72,8 @@ extern "C" int zfact_refine_batched(zfact_ctx* c, int count, const double* const
   const int limit = o.fixed_iters > 0 ? o.fixed_iters : o.nmax;
   int st = ZFACT_OK;
   c->launches = 0;
+  c->ghi_S = nullptr;
+  c->zmax_Z = nullptr;
   cudaEventRecord(c->ev0, c->stream);
 
   // ---- layout: instances stacked along rows, largest first; 256-row slots, common ld

@@ -352,6 +352,8 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
   inf.resid_f = NAN;
 
   c->launches = 0;
+  c->ghi_S = nullptr;
+  c->zmax_Z = nullptr;
   cudaEventRecord(c->ev0, c->stream);
   // ---- stage inputs (host inputs are copied in; device S is used in place)
   const double* S = S_in;
@@ -374,6 +376,7 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
                                   [&] { return launch_gershgorin(S, n, c->st_dev, c->stream); }),
                        "gershgorin")))
       return st;
+    c->ghi_S = S;  // amax[0] holds S's Gershgorin bound for the rest of the call
     if (o.start_scale > 0.0 &&
         (st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1,
                                   [&] { return launch_set_gscale(c->st_dev, o.start_scale, c->stream); }),
@@ -466,6 +469,8 @@ extern "C" int zfact_refine(zfact_ctx* c, const double* S_in, const double* Z0_i
                                     [&] { return launch_gershgorin(S, n, c->st_dev, c->stream); }),
                          "gershgorin")))
         return st;
+      c->ghi_S = S;
+      c->zmax_Z = nullptr;
       if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 8.0 * n * n, 1,
                                     [&] { return launch_scaled_identity_f64(Zcur, n, c->st_dev, c->stream); }),
                          "Z0")))

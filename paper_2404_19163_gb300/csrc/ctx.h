@@ -64,6 +64,10 @@ struct zfact_ctx {
   // when set, oz_residual's fused CRT reconstruction writes max|d| there (double bits) and sets oz_amax_done
   unsigned long long* oz_amax = nullptr;
   bool oz_amax_done = false;
+  // what the refinement's set-up would measure again, when this call already has it in the state:
+  // the Gershgorin bound of S (amax[0]) and max|Z| of the FP64 Z it starts from (amax[2])
+  const double* ghi_S = nullptr;
+  const double* zmax_Z = nullptr;
   int oz_scheme = 0;  // zfact_emulation: 0 residues where they fit, 1 slices always, 2 also wide residues
   cudaStream_t lane_stream[kLanes] = {};
   int lane = -1;

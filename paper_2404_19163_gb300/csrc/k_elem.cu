@@ -142,13 +142,24 @@ __global__ void k_f64_to_f32(const double* __restrict__ src, int n, int ld64, fl
   }
 }
 
-__global__ void k_f32_to_f64(const float* __restrict__ src, int n, int ld32, double* dst, int ld64) {
+// With amax != null also max |x| into *amax (the bits of a non-negative double; the caller zeroes it).
+__global__ void k_f32_to_f64(const float* __restrict__ src, int n, int ld32, double* dst, int ld64,
+                             unsigned long long* amax) {
+  unsigned long long m = 0ull;
   for (int i = blockIdx.y; i < n; i += gridDim.y) {
     const float* s = src + (size_t)i * ld32;
     double* d = dst + (size_t)i * ld64;
 #pragma unroll 4
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) d[j] = (double)s[j];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+      const double x = (double)s[j];
+      d[j] = x;
+      m = max_bits(m, abs_bits(x));
+    }
   }
+  if (!amax) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max_bits(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(amax, m);
 }
 
 // max |A_ij| on the integer pipes (abs_bits): a NaN orders above every number, so a NaN anywhere
@@ -361,8 +372,10 @@ cudaError_t launch_f64_to_f32(const double* src, int n, int ld64, float* dst, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_f32_to_f64(const float* src, int n, int ld32, double* dst, int ld64, cudaStream_t s) {
-  k_f32_to_f64<<<rows_grid(n), 256, 0, s>>>(src, n, ld32, dst, ld64);
+cudaError_t launch_f32_to_f64(const float* src, int n, int ld32, double* dst, int ld64, cudaStream_t s,
+                              unsigned long long* amax) {
+  if (amax) cudaMemsetAsync(amax, 0, sizeof(unsigned long long), s);
+  k_f32_to_f64<<<rows_grid(n), 256, 0, s>>>(src, n, ld32, dst, ld64, amax);
   return cudaGetLastError();
 }
 

@@ -85,7 +85,9 @@ cudaError_t launch_split_flat(const double* A, int64_t n, double scale, uint16_t
                               cudaStream_t s);
 // dst32 = (float) src64 (n x n, leading dimensions ld64 / ld32) and back.
 cudaError_t launch_f64_to_f32(const double* src, int n, int ld64, float* dst, int ld32, cudaStream_t s);
-cudaError_t launch_f32_to_f64(const float* src, int n, int ld32, double* dst, int ld64, cudaStream_t s);
+// dst = (double)src; with amax != null also max |src| into *amax (the bits of a double, zeroed first).
+cudaError_t launch_f32_to_f64(const float* src, int n, int ld32, double* dst, int ld64, cudaStream_t s,
+                              unsigned long long* amax = nullptr);
 // st->amax[slot] = max |A_ij| (FP64 bits, non-negative ordering).
 cudaError_t launch_amax_f64(const double* A, int n, IterState* st, int slot, cudaStream_t s);
 // Power-of-two scales for FP16 operands: st->scale[k] = 2^e with bound_k * 2^e in (2^13, 2^14],

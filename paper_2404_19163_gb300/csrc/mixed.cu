@@ -226,9 +226,12 @@ int refine_ozaki(zfact_ctx* c, const double* S, double* Z64, int n, int order, c
     return e;
   };
   cudaMemsetAsync(c->st_dev->rho2, 0, sizeof(c->st_dev->rho2), c->stream);
-  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 5, [&] {
-                       cudaError_t e = launch_gershgorin(S, n, c->st_dev, c->stream);
-                       if (e == cudaSuccess) e = launch_amax_f64(Z64, n, c->st_dev, 2, c->stream);
+  // S's Gershgorin bound and max|Z| unless this call's state already holds them (cold start, conversion of Z)
+  const bool have_g = c->ghi_S == S, have_z = c->zmax_Z == Z64;
+  c->zmax_Z = nullptr;
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 5 - (have_g ? 2 : 0) - (have_z ? 1 : 0), [&] {
+                       cudaError_t e = have_g ? cudaSuccess : launch_gershgorin(S, n, c->st_dev, c->stream);
+                       if (e == cudaSuccess && !have_z) e = launch_amax_f64(Z64, n, c->st_dev, 2, c->stream);
                        if (e == cudaSuccess) e = launch_ozm_rho(S, n, n, false, &c->st_dev->rho2[0], nullptr, c->stream);
                        if (e == cudaSuccess) e = z_norms();
                        return e;
@@ -529,6 +532,7 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   if (scaled) {
     if ((st = elem("scales S", 5 + (cold && o.start_scale > 0.0 ? 1 : 0), [&] {
            cudaError_t e = launch_gershgorin(S, n, sd, c->stream);  // amax[0] = max row sum of |S|
+           c->ghi_S = S;
            // (which also resets the start scale: a caller's start_scale applies again)
            if (e == cudaSuccess && cold && o.start_scale > 0.0) e = launch_set_gscale(sd, o.start_scale, c->stream);
            if (e == cudaSuccess) e = launch_amax_f64(S, n, sd, kSlotS, c->stream);
@@ -780,7 +784,13 @@ int mixed_refine(zfact_ctx* c, const double* S, double* Za64, double* Zb64, int 
   }
 
   // ---- refinement (Algorithm 3): Z = FP64[Z]; X = Z^T S Z in FP64; Z = Z p(X)
-  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] { return launch_f32_to_f64(Zm, n, ld, Za64, n, c->stream); }), "Z to FP64"))) return st;
+  if ((st = ctx_cuda(c, klaunch(c, "elementwise", 0, 0, 1, [&] {
+                       return launch_f32_to_f64(Zm, n, ld, Za64, n, c->stream,
+                                                reinterpret_cast<unsigned long long*>(&sd->amax[2]));
+                     }),
+                     "Z to FP64")))
+    return st;
+  c->zmax_Z = Za64;  // max|Z| is in the state for the refinement's set-up
   double* Z64 = Za64;
   int ridx = 0;
   if (o.refine_steps <= 0 && !o.final_residual) {
