@@ -189,6 +189,38 @@ int main() {
         return 1;
       }
   }
+  // the tables: pairwise coprime, at most 256, products within the reconstructions' limb counts
+  {
+    double lb = 0.0;
+    for (int i = 0; i < crtw::kMax; ++i) {
+      const int mi = crtw::modulus(i);
+      if (mi < 2 || mi > 256 || (i < kCrtMax && mi != crt_modulus(i))) {
+        printf("modulus %d out of range: %d\n", i, mi);
+        return 1;
+      }
+      for (int j = 0; j < i; ++j) {
+        int a = mi, b = crtw::modulus(j);
+        while (b) {
+          const int t = a % b;
+          a = b;
+          b = t;
+        }
+        if (a != 1) {
+          printf("moduli %d and %d share the factor %d\n", mi, crtw::modulus(j), a);
+          return 1;
+        }
+      }
+      lb += log2((double)mi);
+      if (i == kCrtMax - 1 && !(lb < 126.0)) {
+        printf("the regular set's product 2^%.2f passes the four-limb reconstruction\n", lb);
+        return 1;
+      }
+    }
+    if (!(lb < 190.0)) {
+      printf("the wide set's product 2^%.2f passes the six-limb reconstruction\n", lb);
+      return 1;
+    }
+  }
   CrtPlan p;
   if (crt_plan(110.0, &p) != 14 || crt_plan(117.0, &p) != 15 || crt_plan(118.0, &p) != 16 ||
       crt_plan(125.5, &p) != 0) {
