@@ -6,7 +6,9 @@
 // packed buffer (instance i at row row0[i], one leading dimension), so one tensor map covers all of them and
 // one persistent tcgen05 launch forms every instance's residue products (units: instance, modulus, tile).
 // The moduli of a product are the largest any instance of the group asks for (each instance's from its
-// measured row norms, as in the single-instance refinement).
+// measured row norms, as in the single-instance refinement).  Two buffer sets on two streams let one
+// group's residues and first product run while the host reads the previous group's A norms (which set the
+// second product's moduli).
 #include <math.h>
 #include <string.h>
 
