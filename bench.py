@@ -67,6 +67,41 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def roofline_of(dom, total_ms, reasons, peaks, peak_src):
+    """The `roofline` object of the dominant kernel family `dom` (name, launches, ms, flops, bytes from the
+    library's per-launch events) over a timed region of total_ms with the sampler's throttle reasons.
+    Tensor-core kernels: algorithmic TFLOP/s against the measured burst BF16 peak when the region lasts
+    under a second without the power cap, else the sustained one; FP64 GEMMs: against the FP64 pipe;
+    everything else: algorithmic GB/s against the measured copy bandwidth."""
+    avg_ms = dom["ms"] / max(1, dom["launches"])
+    fl = dom["flops"] / max(1, dom["launches"])
+    by = dom["bytes"] / max(1, dom["launches"])
+    capped = "sw_power_cap" in reasons
+    if dom["name"].startswith("tc_gemm"):
+        ach = fl / (avg_ms * 1e-3) / 1e12
+        # burst peak for a kernel timed in a short region without power capping; the sustained
+        # peak once the timed region lasts seconds or the sampler saw the power cap
+        sustained = total_ms * 1e-3 >= 1.0 or capped
+        key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+        peak = peaks.get(key, 1730.1 if sustained else 1889.9)
+        return {"bound": "tensor", "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": captured_traffic(dom["name"]), "kernel": dom["name"],
+                "peak_source": "%s bf16 %s (timed region %.2f s%s)" % (
+                    peak_src, "sustained" if sustained else "burst", total_ms * 1e-3,
+                    ", power cap seen" if capped else ", no power cap")}
+    if dom["name"].startswith("f64_gemm"):
+        ach = fl / (avg_ms * 1e-3) / 1e12
+        peak = 1.098
+        return {"bound": "alu", "achieved": round(ach, 3), "peak": peak, "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": None, "kernel": dom["name"],
+                "peak_source": "FP64 pipe: cuBLAS DGEMM 4096^3 measured on this GB300 (1.098 TFLOP/s)"}
+    ach = by / (avg_ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6676.8)
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4), "traffic": None, "kernel": dom["name"],
+            "peak_source": "%s hbm" % peak_src}
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
@@ -381,33 +416,7 @@ def run_ours(args, rank, ws, local):
     dom = max(stats, key=lambda s: s["ms"]) if stats else None
     roof = None
     if dom:
-        avg_ms = dom["ms"] / max(1, dom["launches"])
-        fl = dom["flops"] / max(1, dom["launches"])
-        by = dom["bytes"] / max(1, dom["launches"])
-        if dom["name"].startswith("tc_gemm"):
-            ach = fl / (avg_ms * 1e-3) / 1e12
-            # burst peak for a kernel timed in a short region without power capping; the sustained
-            # peak once the timed region lasts seconds or the sampler saw the power cap
-            sustained = total * 1e-3 >= 1.0 or "sw_power_cap" in clk.summary()["reasons"]
-            key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
-            peak = peaks.get(key, 1730.1 if sustained else 1889.9)
-            roof = {"bound": "tensor", "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
-                    "frac": round(ach / peak, 4), "traffic": captured_traffic(dom["name"]), "kernel": dom["name"],
-                    "peak_source": "%s bf16 %s (timed region %.2f s%s)" % (
-                        peak_src, "sustained" if sustained else "burst", total * 1e-3,
-                        ", power cap seen" if "sw_power_cap" in clk.summary()["reasons"] else ", no power cap")}
-        elif dom["name"].startswith("f64_gemm"):
-            ach = fl / (avg_ms * 1e-3) / 1e12
-            peak = 1.098
-            roof = {"bound": "alu", "achieved": round(ach, 3), "peak": peak, "unit": "TFLOP/s",
-                    "frac": round(ach / peak, 4), "traffic": None, "kernel": dom["name"],
-                    "peak_source": "FP64 pipe: cuBLAS DGEMM 4096^3 measured on this GB300 (1.098 TFLOP/s)"}
-        else:
-            ach = by / (avg_ms * 1e-3) / 1e9
-            peak = peaks.get("hbm_gbs", 6676.8)
-            roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(ach / peak, 4), "traffic": None, "kernel": dom["name"],
-                    "peak_source": "%s hbm" % peak_src}
+        roof = roofline_of(dom, total, clk.summary()["reasons"], peaks, peak_src)
     tc_ms = sum(s["ms"] for s in stats if s["name"].startswith("tc_gemm"))
     tc_fl = sum(s["flops"] for s in stats if s["name"].startswith("tc_gemm"))
     # the FP64-accurate products counted as the FP64 products they stand for (2 N^2 K each, half on
