@@ -142,7 +142,9 @@ const char* zfact_last_error(zfact_ctx* ctx);
  *   order   m in 2..5 (degree of p_m).
  *   precision  zfact_precision of the bulk iterations.
  *   opts    NULL = defaults.
- *   Z       output (FP64, N x N); may alias Z0.
+ *   Z       output (FP64, N x N); may alias Z0.  S, Z0 and Z may each be device or host memory
+ *           (host data are copied in and out inside the call); a pinned host Z receives the result
+ *           by a copy that starts after the last refinement update and overlaps the final residual.
  *   hist    host array of hist_cap doubles: hist[0] = Err_0, then Err after every bulk
  *           update, then after every refinement update, then the final FP64 residual
  *           (when formed).  Entries beyond hist_cap are dropped.
@@ -159,7 +161,8 @@ int zfact_refine(zfact_ctx* ctx, const double* S, const double* Z0, int64_t N, i
  * entries (may be NULL), status a host array of count ints (per-instance
  * zfact_status, may be NULL).  Every instance runs the bulk under the stop rule of opts; then, by
  * default (refine_steps < 0 or 0), the FP64-accurate residual of every returned Z is formed
- * (opts->final_residual) on concurrent streams.  With refine_steps > 0 every instance also gets
+ * (opts->final_residual) by grouped CRT launches over groups of instances (two groups in flight on
+ * two streams), or per instance on concurrent streams when the batch is outside that form.  With refine_steps > 0 every instance also gets
  * Algorithm 3's refinement (refine_mode ZFACT_R_OZAKI or ZFACT_R_FP32; ZFACT_R_NATIVE returns
  * ZFACT_ERR_UNSUPPORTED), one instance after another, its Err entries appended to its history.
  * Motivated by the warm starts of Sec. 6 (molecular-dynamics frames, geometry optimisation). */
